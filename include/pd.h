@@ -1,0 +1,276 @@
+/*
+ * pd.h -- C ABI of the GB300 bond-based peridynamic / multilevel Monte Carlo
+ * hot path (arXiv 2212.04415, "A probabilistic peridynamic framework with an
+ * application to the study of the statistical size effect").
+ *
+ * Conventions shared by every call:
+ *  - Status: every call returns PD_OK (0) or a negative PD_ERR_* code. On an
+ *    error nothing is written to the caller's output buffers, the call never
+ *    aborts, and pd_last_error() returns a one-line description.
+ *  - Device buffers are owned by the caller (allocated by the caller, for
+ *    example as torch tensors, and passed as raw device pointers). Handles
+ *    (pd_state, pd_field) own only their internal state, scratch and KL basis.
+ *  - Every call that touches the GPU takes a CUDA stream (pd_stream, the same
+ *    object as cudaStream_t; NULL = the legacy default stream) and is
+ *    asynchronous on that stream unless its comment says "host-synchronous".
+ *  - Units are SI (m, N, Pa, kg, s). Node i has grid index
+ *    (ix, iy, iz) = (i % nx, (i / nx) % ny, i / (nx ny)) and sits at the cell
+ *    centre ((ix + 1/2) dx, (iy + 1/2) dx, (iz + 1/2) dx).
+ *  - Geometry that must compare exactly (notch, supports, load line) is given
+ *    in integer half-cells: x = X dx / 2, so node ix sits at X = 2 ix + 1.
+ *  - Arrays indexed by sample are sample-major: [B][N] or [B][N][3].
+ */
+#ifndef PD_GB300_H
+#define PD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *pd_stream; /* == cudaStream_t */
+
+#if defined(__GNUC__)
+#define PD_API __attribute__((visibility("default")))
+#else
+#define PD_API
+#endif
+
+enum {
+    PD_OK = 0,
+    PD_ERR_ARG = -1,     /* invalid argument (sizes, NULL pointers, unsupported mode) */
+    PD_ERR_CUDA = -2,    /* a CUDA runtime call failed */
+    PD_ERR_OOM = -3,     /* device allocation failed */
+    PD_ERR_TIMEOUT = -4, /* a bounded device wait gave up */
+    PD_ERR_NAN = -5,     /* a non-finite value was detected */
+    PD_ERR_CAP = -6      /* output capacity too small (the required size is reported) */
+};
+
+enum { PD_LAW_BILINEAR = 0, PD_LAW_EXPLINEAR = 1 };
+enum { PD_PREC_FP64 = 0, PD_PREC_MIXED = 1 };
+enum { PD_BC_BAR_TENSION = 1, PD_BC_BEAM_3PT = 2 };
+enum { PD_COV_SQEXP = 0, PD_COV_EXP = 1 };
+enum { PD_MARG_LOGNORMAL = 0, PD_MARG_WEIBULL = 1 };
+
+/* Regular grid and horizon (Eq. PD_Horizon, Section 3.2: delta = m dx).
+ * notch: 1 removes every bond whose segment strictly crosses the plane
+ * X = notch_x2 (half-cells) at a height below Y = notch_y2 (half-cells); a
+ * crossing exactly at the notch tip is kept. */
+typedef struct pd_grid {
+    int32_t nx, ny, nz; /* nodes per axis; nx, ny <= 2047, nz <= 1023 */
+    double dx;          /* node spacing [m] */
+    double m_ratio;     /* horizon / dx */
+    int32_t notch;
+    int32_t notch_x2;
+    int32_t notch_y2;
+} pd_grid;
+
+/* Material and integrator (Appendix A; integrator readings in the design notes).
+ * Micromodulus c = 12 E / (pi delta^4) (Eq. bond_stiffness_constant, 3D).
+ * Bond force f = c_ij (1 - d) s (Eq. exp_scalar_force) with per-bond
+ * s0_ij = (s0_i + s0_j)/2, s_crit_ij = s_ratio s0_ij, c_ij = c (kappa_i + kappa_j)/2.
+ * law PD_LAW_BILINEAR: d = 1 - s0 (sf - s)/(s (sf - s0)) on (s0, sf);
+ * law PD_LAW_EXPLINEAR: Eq. exp_damage_parameter with k, alpha.
+ * Damage is irreversible: d_n = max(d_{n-1}, d_law(s_n)).
+ * dt > 0 is used as given; dt <= 0 selects dt_safety x the Silling-Askari
+ * stable step min_i sqrt(2 rho / sum_j c V / |xi_ij|).
+ * zeta: mass-proportional damping rate [1/s] of the damped leapfrog update.
+ * precision: PD_PREC_FP64 (all arithmetic FP64) or PD_PREC_MIXED (bond
+ * kinematics and forces FP32; nodal sums, integration, reaction FP64). */
+typedef struct pd_material {
+    double E;
+    double rho;
+    int32_t law;
+    double s_ratio;
+    double k;
+    double alpha;
+    double dt;
+    double dt_safety;
+    double zeta;
+    int32_t precision;
+} pd_material;
+
+/* Displacement control: prescribed magnitude U(n) = u_max min(n, n_ramp) / n_ramp.
+ * PD_BC_BAR_TENSION: the first grip_planes x-planes are fixed; the last
+ *   grip_planes x-planes move by +U(n) along x and are held in y and z.
+ * PD_BC_BEAM_3PT: bottom-layer (iy = 0) nodes within half a cell of either
+ *   support_x2 are held in y; top-layer nodes within half a cell of load_x2
+ *   move by -U(n) along y. */
+typedef struct pd_bc {
+    int32_t type;
+    int32_t grip_planes;
+    int32_t support_x2[2];
+    int32_t load_x2;
+    double u_max;
+    int32_t n_ramp;
+} pd_bc;
+
+/* Truncated Karhunen-Loeve random field (Section 5). */
+typedef struct pd_field_cfg {
+    int32_t kernel;   /* PD_COV_SQEXP: exp(-r^2/l^2) (separable); PD_COV_EXP: exp(-r/l) */
+    double length;    /* correlation length l [m] */
+    int32_t n_modes;  /* K, 1..256 */
+    int32_t marginal; /* PD_MARG_LOGNORMAL or PD_MARG_WEIBULL */
+    double mean;      /* mean of the marginal */
+    double cov;       /* coefficient of variation (lognormal) */
+    double weibull_m; /* Weibull modulus (Weibull) */
+} pd_field_cfg;
+
+typedef struct pd_state pd_state;
+typedef struct pd_field pd_field;
+
+/* One-line text of the last error raised on the calling thread. */
+PD_API int pd_last_error(char *buf, size_t len);
+
+/* Version string of the library (static storage). */
+PD_API const char *pd_version(void);
+
+/* ------------------------------------------------------------------ mesh */
+
+/* Neighbour list of the horizon H_x = {x' : |x' - x| <= delta} (Eq. PD_Horizon),
+ * minus notch-cut bonds, as CSR sorted by neighbour index within each row.
+ * row_ptr: device int32[N+1] (always written); col: device int32[cap].
+ * n_bonds (host out): number of directed bonds. If col == NULL only row_ptr
+ * and n_bonds are produced; if cap < n_bonds, returns PD_ERR_CAP with
+ * n_bonds set and col untouched. Host-synchronous (reads back n_bonds).
+ * Bit-exact: the list is a pure integer function of the grid. */
+PD_API int pd_build_neighbours(const pd_grid *g, int32_t *row_ptr, int32_t *col, int64_t cap,
+                        int64_t *n_bonds, pd_stream stream);
+
+/* Per-DOF boundary codes (device uint8[N*3]: 0 free, 1 fixed, 2 +U(n), 3 -U(n)). */
+PD_API int pd_bc_codes(const pd_grid *g, const pd_bc *bc, uint8_t *codes, pd_stream stream);
+
+/* ------------------------------------------------------------ time step */
+
+/* Create the explicit-dynamics state of B independent samples on one mesh
+ * (row_ptr/col: device CSR from pd_build_neighbours; copied, not retained).
+ * Host-synchronous. The state starts at step 0 with u = v = d = 0 and a
+ * uniform field s0 = 1e-4, kappa = 1; call pd_state_reset to set the fields. */
+PD_API int pd_state_create(const pd_grid *g, const int32_t *row_ptr, const int32_t *col,
+                    int64_t n_bonds, const pd_material *mat, const pd_bc *bc, int32_t batch,
+                    pd_state **out);
+PD_API int pd_state_destroy(pd_state *st);
+
+/* dt [s], micromodulus c, node and bond counts of a state (host outputs, any may be NULL). */
+PD_API int pd_state_info(const pd_state *st, double *dt, double *c, int64_t *n_nodes,
+                  int64_t *n_bonds);
+
+/* Restart every sample at step 0 with u = v = d = 0, peak = -inf, and the
+ * per-node fields s0 (device float[B][N], required) and kappa (device
+ * float[B][N], or NULL for kappa = 1). */
+PD_API int pd_state_reset(pd_state *st, const float *s0, const float *kappa, pd_stream stream);
+
+/* Overwrite u, v (device double[B][N][3]) and damage d (device double[B][n_bonds]
+ * in CSR order, or NULL to keep) and set the step index of every sample. */
+PD_API int pd_state_load(pd_state *st, const double *u, const double *v, const double *d,
+                  int32_t step, pd_stream stream);
+
+/* Copy u, v (device double[B][N][3]) and d (device double[B][n_bonds], CSR
+ * order) out; any pointer may be NULL. */
+PD_API int pd_state_store(const pd_state *st, double *u, double *v, double *d, pd_stream stream);
+
+/* Internal force density F (device double[B][N][3]) of the current state,
+ * F_i = sum_j f_ij V_j (Eq. PD_EOM_Dynamic with b = 0), updating the bond
+ * damage from the current stretch exactly as a step does; u, v unchanged. */
+PD_API int pd_force(pd_state *st, double *F, pd_stream stream);
+
+/* Advance every sample n_steps explicit steps (Section 3; Eq. PD_EOM_Dynamic):
+ * damage from the current stretch, bond forces, nodal sums, damped leapfrog
+ * update with the prescribed displacements, and the reaction
+ * R_n = -sum over prescribed DOFs of F sign V. reaction: device
+ * double[B][n_steps] or NULL. Samples marked done by pd_run_to_peak do not move. */
+PD_API int pd_step(pd_state *st, int32_t n_steps, double *reaction, pd_stream stream);
+
+/* Run every sample until its peak-load rule stops it or max_steps steps have
+ * been taken: Q = max_n R_n (first step attaining it); a sample stops once
+ * R_n < Q/2 with Q > 0 and at least 100 steps after the peak.
+ * Outputs (device): peak double[B], peak_step int32[B], n_done int32[B]
+ * (steps executed). Host-synchronous (the host polls completion once per
+ * chunk of captured steps). */
+PD_API int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int32_t *peak_step,
+                   int32_t *n_done, pd_stream stream);
+
+/* ---------------------------------------------------------- random field */
+
+/* KL coefficients xi (device double[B][K]) of samples sample_ids (device
+ * uint64[B]) on MLMC level `level`: Philox4x32-10 keyed by the seed, counter
+ * (block, sample id, level), Box-Muller in FP64 (Section 4.2: the same xi
+ * serves both members of a coupled pair). */
+PD_API int pd_draw_xi(uint64_t seed, int32_t level, const uint64_t *sample_ids, int32_t B,
+               int32_t n_modes, double *xi, pd_stream stream);
+
+/* KL basis of the finest grid of a hierarchy of n_levels nested grids (each
+ * coarser grid halves nx, ny, nz and doubles dx; level 0 is the coarsest).
+ * Host-synchronous. The separable squared-exponential kernel works on any
+ * size; the exponential kernel needs the dense covariance (finest N <= 4096). */
+PD_API int pd_field_create(const pd_grid *finest, int32_t n_levels, const pd_field_cfg *cfg,
+                    pd_field **out);
+PD_API int pd_field_destroy(pd_field *f);
+
+/* K and the KL eigenvalues (host double[K], may be NULL). */
+PD_API int pd_field_info(const pd_field *f, int32_t *n_modes, double *lambda);
+
+/* Field of B samples on grid `level`: g = Phi diag(sqrt(lambda)) xi, then the
+ * marginal transform (Section 5.2). node_field: device float[B][N_level].
+ * coarse_field (level > 0, or NULL): the same samples on grid level-1, from
+ * the 2x2x2 mean of the Gaussian field before the transform (Section 4.2). */
+PD_API int pd_sample_field(pd_field *f, int32_t level, const double *xi, int32_t B,
+                    float *node_field, float *coarse_field, pd_stream stream);
+
+/* ------------------------------------------------------------------ MLMC */
+
+#define PD_MAX_LEVELS 8
+
+/* Fixed-allocation multilevel Monte Carlo (Section 4.2). Level l uses grid[l]
+ * (coarsest first, dx halving) with bc[l] and max_steps[l]; level l > 0
+ * draws each sample's field once on grid l and its 2x2x2 coarsening on grid
+ * l-1 and runs both (Y_l = Q_l - Q_{l-1}); level 0 runs Q_0 alone. */
+typedef struct pd_mlmc_cfg {
+    int32_t n_levels;
+    const pd_grid *grid;
+    const pd_bc *bc;
+    const int32_t *max_steps;
+    const int64_t *n_samples;
+    pd_material mat;
+    pd_field_cfg field;
+    uint64_t seed;
+    int32_t batch; /* samples per launch (<= 4096) */
+} pd_mlmc_cfg;
+
+typedef struct pd_mlmc_level {
+    int64_t n;           /* samples taken */
+    double sum_y;        /* sum of Y (FP64, fixed order) */
+    double sum_y2;       /* sum of Y^2 */
+    double mean;         /* Y_hat = sum_y / n */
+    double var;          /* s^2 = sum_y2/n - mean^2 (Eq. sample_variance) */
+    double var_unbiased; /* s^2 n/(n-1) */
+    double cost_s;       /* GPU seconds spent on the level */
+    int64_t steps;       /* explicit steps executed (fine + coarse) */
+    int64_t bond_updates;
+} pd_mlmc_level;
+
+typedef struct pd_mlmc_result {
+    int32_t n_levels;
+    pd_mlmc_level level[PD_MAX_LEVELS];
+    double q_ml;   /* Q_hat^ML = sum_l Y_hat_l (Eq. MLMC_estimator) */
+    double var_ml; /* sum_l var_l / n_l (Eq. MLMC_error, sampling part) */
+} pd_mlmc_result;
+
+/* Host-synchronous; owns its own device buffers. q_fine/q_coarse (host,
+ * optional) receive every sample's Q_l and Q_{l-1} level after level
+ * (sum_l n_samples[l] entries; q_coarse entries of level 0 are 0). */
+PD_API int mlmc_estimate(const pd_mlmc_cfg *cfg, pd_mlmc_result *out, double *q_fine,
+                  double *q_coarse, pd_stream stream);
+
+/* Optimal allocation N_l = floor(eps_s^-2 (sum_k sqrt(V_k C_k)) sqrt(V_l/C_l))
+ * (Eq. sample_allocation), host arrays of length n_levels. */
+PD_API int pd_mlmc_allocation(int32_t n_levels, const double *V, const double *C, double eps_s,
+                       int64_t *N);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PD_GB300_H */

@@ -1,0 +1,321 @@
+"""GB300-native probabilistic bond-based peridynamics (arXiv 2212.04415).
+
+Thin Python binding of ``libpd_gb300.so`` (the C ABI declared in
+``include/pd.h``): argument marshalling only. Every step of the hot path runs
+in the library's sm_103a kernels; PyTorch provides device memory and streams.
+There is no CPU fallback: if the library is not built, or no GPU is present,
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from .build import LIB as _LIB_PATH
+
+PD_OK, PD_ERR_ARG, PD_ERR_CUDA, PD_ERR_OOM, PD_ERR_TIMEOUT, PD_ERR_NAN, PD_ERR_CAP = 0, -1, -2, -3, -4, -5, -6
+PREC_FP64, PREC_MIXED = 0, 1
+MAX_LEVELS = 8
+
+
+class PdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pd error {code}: {msg}")
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("dx", C.c_double),
+                ("m_ratio", C.c_double), ("notch", C.c_int32), ("notch_x2", C.c_int32),
+                ("notch_y2", C.c_int32)]
+
+
+class Material(C.Structure):
+    _fields_ = [("E", C.c_double), ("rho", C.c_double), ("law", C.c_int32), ("s_ratio", C.c_double),
+                ("k", C.c_double), ("alpha", C.c_double), ("dt", C.c_double), ("dt_safety", C.c_double),
+                ("zeta", C.c_double), ("precision", C.c_int32)]
+
+
+class BC(C.Structure):
+    _fields_ = [("type", C.c_int32), ("grip_planes", C.c_int32), ("support_x2", C.c_int32 * 2),
+                ("load_x2", C.c_int32), ("u_max", C.c_double), ("n_ramp", C.c_int32)]
+
+
+class FieldCfg(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("length", C.c_double), ("n_modes", C.c_int32),
+                ("marginal", C.c_int32), ("mean", C.c_double), ("cov", C.c_double),
+                ("weibull_m", C.c_double)]
+
+
+class MlmcCfg(C.Structure):
+    _fields_ = [("n_levels", C.c_int32), ("grid", C.POINTER(Grid)), ("bc", C.POINTER(BC)),
+                ("max_steps", C.POINTER(C.c_int32)), ("n_samples", C.POINTER(C.c_int64)),
+                ("mat", Material), ("field", FieldCfg), ("seed", C.c_uint64), ("batch", C.c_int32)]
+
+
+class MlmcLevel(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sum_y", C.c_double), ("sum_y2", C.c_double), ("mean", C.c_double),
+                ("var", C.c_double), ("var_unbiased", C.c_double), ("cost_s", C.c_double),
+                ("steps", C.c_int64), ("bond_updates", C.c_int64)]
+
+
+class MlmcResult(C.Structure):
+    _fields_ = [("n_levels", C.c_int32), ("level", MlmcLevel * MAX_LEVELS), ("q_ml", C.c_double),
+                ("var_ml", C.c_double)]
+
+
+_VP = C.c_void_p
+_SIGS = {
+    "pd_last_error": (C.c_int, [C.c_char_p, C.c_size_t]),
+    "pd_version": (C.c_char_p, []),
+    "pd_build_neighbours": (C.c_int, [C.POINTER(Grid), _VP, _VP, C.c_int64, C.POINTER(C.c_int64), _VP]),
+    "pd_bc_codes": (C.c_int, [C.POINTER(Grid), C.POINTER(BC), _VP, _VP]),
+    "pd_state_create": (C.c_int, [C.POINTER(Grid), _VP, _VP, C.c_int64, C.POINTER(Material), C.POINTER(BC),
+                                  C.c_int32, C.POINTER(_VP)]),
+    "pd_state_destroy": (C.c_int, [_VP]),
+    "pd_state_info": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                C.POINTER(C.c_int64)]),
+    "pd_state_reset": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "pd_state_load": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int32, _VP]),
+    "pd_state_store": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "pd_force": (C.c_int, [_VP, _VP, _VP]),
+    "pd_step": (C.c_int, [_VP, C.c_int32, _VP, _VP]),
+    "pd_run_to_peak": (C.c_int, [_VP, C.c_int32, _VP, _VP, _VP, _VP]),
+    "pd_draw_xi": (C.c_int, [C.c_uint64, C.c_int32, _VP, C.c_int32, C.c_int32, _VP, _VP]),
+    "pd_field_create": (C.c_int, [C.POINTER(Grid), C.c_int32, C.POINTER(FieldCfg), C.POINTER(_VP)]),
+    "pd_field_destroy": (C.c_int, [_VP]),
+    "pd_field_info": (C.c_int, [_VP, C.POINTER(C.c_int32), _VP]),
+    "pd_sample_field": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, _VP, _VP, _VP]),
+    "mlmc_estimate": (C.c_int, [C.POINTER(MlmcCfg), C.POINTER(MlmcResult), _VP, _VP, _VP]),
+    "pd_mlmc_allocation": (C.c_int, [C.c_int32, _VP, _VP, C.c_double, _VP]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(_LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != PD_OK:
+        buf = C.create_string_buffer(512)
+        lib().pd_last_error(buf, 512)
+        raise PdError(rc, buf.value.decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be CUDA and contiguous"
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------ conversions
+
+def grid_struct(g) -> Grid:
+    return Grid(g.nx, g.ny, g.nz, g.dx, g.m_ratio, g.notch, g.notch_x2, g.notch_y2)
+
+
+def material_struct(m, precision: int, dt: float = 0.0) -> Material:
+    return Material(m.E, m.rho, m.law, m.s_ratio, m.k, m.alpha, dt, m.dt_safety, m.zeta, precision)
+
+
+def bc_struct(b) -> BC:
+    return BC(b.type, b.grip_planes, (C.c_int32 * 2)(*b.support_x2), b.load_x2, b.u_max, b.n_ramp)
+
+
+def field_struct(f) -> FieldCfg:
+    return FieldCfg(f.kernel, f.length, f.n_modes, f.marginal, f.mean, f.cov, f.weibull_m)
+
+
+# ------------------------------------------------------------------ calls
+
+def build_neighbours(g, stream=None):
+    """CSR (row_ptr int32[N+1], col int32[nb]) as CUDA tensors (Eq. PD_Horizon)."""
+    import torch
+    G = grid_struct(g)
+    n = g.nx * g.ny * g.nz
+    row = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+    nb = C.c_int64(0)
+    _check(lib().pd_build_neighbours(C.byref(G), _ptr(row), None, 0, C.byref(nb), _stream(stream)))
+    col = torch.empty(max(nb.value, 1), dtype=torch.int32, device="cuda")
+    _check(lib().pd_build_neighbours(C.byref(G), _ptr(row), _ptr(col), nb.value, C.byref(nb), _stream(stream)))
+    return row, col[: nb.value]
+
+
+def bc_codes(g, b, stream=None):
+    import torch
+    G, Bc = grid_struct(g), bc_struct(b)
+    out = torch.empty((g.nx * g.ny * g.nz, 3), dtype=torch.uint8, device="cuda")
+    _check(lib().pd_bc_codes(C.byref(G), C.byref(Bc), _ptr(out), _stream(stream)))
+    return out
+
+
+class State:
+    """B independent samples of the explicit peridynamic dynamics on one mesh."""
+
+    def __init__(self, g, row, col, mat, bc, batch=1, precision=PREC_MIXED, dt=0.0):
+        import torch
+        torch.cuda.synchronize()
+        self.grid = g
+        self.B = batch
+        self._G, self._M, self._BC = grid_struct(g), material_struct(mat, precision, dt), bc_struct(bc)
+        h = C.c_void_p()
+        _check(lib().pd_state_create(C.byref(self._G), _ptr(row), _ptr(col), int(col.numel()),
+                                     C.byref(self._M), C.byref(self._BC), batch, C.byref(h)))
+        self.h = h
+        dtv, cv, nn, nb = C.c_double(), C.c_double(), C.c_int64(), C.c_int64()
+        _check(lib().pd_state_info(h, C.byref(dtv), C.byref(cv), C.byref(nn), C.byref(nb)))
+        self.dt, self.c, self.N, self.nb = dtv.value, cv.value, nn.value, nb.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pd_state_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def reset(self, s0, kappa=None, stream=None):
+        _check(lib().pd_state_reset(self.h, _ptr(s0), _ptr(kappa), _stream(stream)))
+
+    def load(self, u, v, d=None, step=0, stream=None):
+        _check(lib().pd_state_load(self.h, _ptr(u), _ptr(v), _ptr(d), step, _stream(stream)))
+
+    def store(self, stream=None):
+        import torch
+        u = torch.empty((self.B, self.N, 3), dtype=torch.float64, device="cuda")
+        v = torch.empty_like(u)
+        d = torch.empty((self.B, self.nb), dtype=torch.float64, device="cuda")
+        _check(lib().pd_state_store(self.h, _ptr(u), _ptr(v), _ptr(d), _stream(stream)))
+        return u, v, d
+
+    def force(self, stream=None):
+        import torch
+        F = torch.empty((self.B, self.N, 3), dtype=torch.float64, device="cuda")
+        _check(lib().pd_force(self.h, _ptr(F), _stream(stream)))
+        return F
+
+    def step(self, n_steps, reaction=True, stream=None):
+        import torch
+        R = torch.empty((self.B, n_steps), dtype=torch.float64, device="cuda") if reaction else None
+        _check(lib().pd_step(self.h, n_steps, _ptr(R), _stream(stream)))
+        return R
+
+    def run_to_peak(self, max_steps, stream=None, out=None):
+        import torch
+        if out is None:
+            out = (torch.empty(self.B, dtype=torch.float64, device="cuda"),
+                   torch.empty(self.B, dtype=torch.int32, device="cuda"),
+                   torch.empty(self.B, dtype=torch.int32, device="cuda"))
+        pk, ps, nd = out
+        _check(lib().pd_run_to_peak(self.h, max_steps, _ptr(pk), _ptr(ps), _ptr(nd), _stream(stream)))
+        return pk, ps, nd
+
+
+def draw_xi(seed, level, sample_ids, n_modes, stream=None, out=None):
+    import torch
+    B = sample_ids.numel()
+    xi = out if out is not None else torch.empty((B, n_modes), dtype=torch.float64, device="cuda")
+    _check(lib().pd_draw_xi(seed, level, _ptr(sample_ids), B, n_modes, _ptr(xi), _stream(stream)))
+    return xi
+
+
+class Field:
+    """Truncated KL random field on a hierarchy of nested grids (finest given)."""
+
+    def __init__(self, finest, n_levels, cfg):
+        import torch
+        torch.cuda.synchronize()
+        self._G, self._F = grid_struct(finest), field_struct(cfg)
+        h = C.c_void_p()
+        _check(lib().pd_field_create(C.byref(self._G), n_levels, C.byref(self._F), C.byref(h)))
+        self.h = h
+        self.K = cfg.n_modes
+        # node counts per level, coarsest first (each coarser grid halves nx, ny, nz)
+        self.sizes = [(finest.nx >> s, finest.ny >> s, finest.nz >> s) for s in range(n_levels - 1, -1, -1)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pd_field_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def eigenvalues(self):
+        import numpy as np
+        lam = np.zeros(self.K)
+        k = C.c_int32()
+        _check(lib().pd_field_info(self.h, C.byref(k), lam.ctypes.data_as(C.c_void_p)))
+        return lam
+
+    def sample(self, level, xi, coarse=False, stream=None, out=None):
+        import torch
+        B = xi.shape[0]
+        nf = self.sizes[level][0] * self.sizes[level][1] * self.sizes[level][2]
+        f = out[0] if out is not None else torch.empty((B, nf), dtype=torch.float32, device="cuda")
+        c = None
+        if coarse:
+            nc = self.sizes[level - 1][0] * self.sizes[level - 1][1] * self.sizes[level - 1][2]
+            c = out[1] if out is not None else torch.empty((B, nc), dtype=torch.float32, device="cuda")
+        _check(lib().pd_sample_field(self.h, level, _ptr(xi), B, _ptr(f), _ptr(c), _stream(stream)))
+        return (f, c) if coarse else f
+
+
+def mlmc_estimate(grids, bcs, max_steps, n_samples, mat, field, seed, batch, precision=PREC_MIXED,
+                  return_samples=False, stream=None):
+    """Fixed-allocation MLMC over len(grids) nested levels (coarsest first)."""
+    import numpy as np
+    L = len(grids)
+    G = (Grid * L)(*[grid_struct(g) for g in grids])
+    Bc = (BC * L)(*[bc_struct(b) for b in bcs])
+    ms = (C.c_int32 * L)(*max_steps)
+    ns = (C.c_int64 * L)(*n_samples)
+    cfg = MlmcCfg(L, G, Bc, ms, ns, material_struct(mat, precision), field_struct(field), seed, batch)
+    res = MlmcResult()
+    tot = int(sum(n_samples))
+    qf = np.zeros(max(tot, 1))
+    qc = np.zeros(max(tot, 1))
+    _check(lib().mlmc_estimate(C.byref(cfg), C.byref(res), qf.ctypes.data_as(C.c_void_p),
+                               qc.ctypes.data_as(C.c_void_p), _stream(stream)))
+    levels = []
+    for l in range(L):
+        lv = res.level[l]
+        levels.append(dict(n=lv.n, sum_y=lv.sum_y, sum_y2=lv.sum_y2, mean=lv.mean, var=lv.var,
+                           var_unbiased=lv.var_unbiased, cost_s=lv.cost_s, steps=lv.steps,
+                           bond_updates=lv.bond_updates))
+    out = dict(levels=levels, q_ml=res.q_ml, var_ml=res.var_ml)
+    if return_samples:
+        out["q_fine"], out["q_coarse"] = qf[:tot], qc[:tot]
+    return out
+
+
+def mlmc_allocation(V, Cst, eps_s):
+    import numpy as np
+    V = np.ascontiguousarray(V, np.float64)
+    Cs = np.ascontiguousarray(Cst, np.float64)
+    N = np.zeros(V.size, np.int64)
+    _check(lib().pd_mlmc_allocation(V.size, V.ctypes.data_as(C.c_void_p), Cs.ctypes.data_as(C.c_void_p),
+                                    eps_s, N.ctypes.data_as(C.c_void_p)))
+    return N

@@ -1,0 +1,111 @@
+// pd_internal.cuh -- shared internals of the GB300 peridynamic library
+// (error plumbing, small device helpers, the state layout).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/pd.h"
+
+namespace pdi {
+
+// Record the last error text for pd_last_error (thread-local).
+void set_error(const char *fmt, ...);
+
+#define PD_CHECK_CUDA(call)                                                           \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            pdi::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,                 \
+                           cudaGetErrorString(e_));                                   \
+            return PD_ERR_CUDA;                                                       \
+        }                                                                             \
+    } while (0)
+
+#define PD_CHECK_LAUNCH() PD_CHECK_CUDA(cudaGetLastError())
+
+#define PD_REQUIRE(cond, ...)                                                         \
+    do {                                                                              \
+        if (!(cond)) {                                                                \
+            pdi::set_error(__VA_ARGS__);                                              \
+            return PD_ERR_ARG;                                                        \
+        }                                                                             \
+    } while (0)
+
+// Device allocation that reports PD_ERR_OOM through the caller.
+template <typename T>
+int dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        *p = nullptr;
+        return PD_ERR_OOM;
+    }
+    return PD_OK;
+}
+
+#define PD_TRY(expr)                \
+    do {                            \
+        int rc_ = (expr);           \
+        if (rc_ != PD_OK) return rc_; \
+    } while (0)
+
+int validate_grid(const pd_grid *g);
+
+// Exclusive-free inclusive scan of a[1..n] in place (a[0] untouched), int32
+// with an int64 running sum; sets *overflow if the total exceeds INT32_MAX.
+int scan_inplace_i32(int32_t *a, int64_t n, int32_t *overflow_flag_dev, cudaStream_t s);
+
+// Packed grid coordinate of a node: ix | iy << 11 | iz << 22.
+__host__ __device__ __forceinline__ int32_t pack_coord(int ix, int iy, int iz) {
+    return ix | (iy << 11) | (iz << 22);
+}
+
+}  // namespace pdi
+
+// Opaque handles (definitions shared between translation units).
+struct pd_state {
+    pd_grid g;
+    pd_material mat;
+    pd_bc bc;
+    int32_t B;
+    int64_t N;
+    int64_t nb;
+    double dt, c, V;
+    // neighbour list: CSR copy and SELL-32 slot-major layout
+    int32_t *row_ptr;
+    int64_t n_slices;
+    int64_t sell_len;
+    long long *sell_off; // [n_slices]: first slot element of each slice
+    int32_t *sell_w;    // [n_slices]: slots per lane in the slice
+    int32_t *sell_col;  // [sell_len]: neighbour index, -1 = padding
+    // per-sample state
+    void *dmg;          // float or double [B][sell_len]
+    double *u64;        // [B][N][3]
+    double *v64;        // [B][N][3]
+    void *rec[2];       // 32-byte gather records [B][N], double-buffered by step parity
+    float *kappa;       // [B][N] or nullptr
+    bool has_kappa;
+    uint8_t *codes;     // [N][3]
+    int32_t *coord;     // [N] packed grid coordinates
+    // run bookkeeping (device)
+    int32_t *step;      // [B]
+    int32_t *done;      // [B]
+    int32_t *status;    // [B] bit 0: non-finite reaction
+    double *peak;       // [B]
+    int32_t *peak_step; // [B]
+    double *partial;    // [B][nblk]
+    uint32_t *ticket;   // [B]
+    int32_t nblk;
+    // run_to_peak chunk graph
+    cudaGraphExec_t chunk_exec;
+    int32_t chunk_steps;
+    int32_t chunk_max_steps;
+    int32_t *host_flag;     // pinned mapped [2]
+    int32_t *host_flag_dev; // device alias
+    cudaEvent_t ev[2];
+};

@@ -1,0 +1,230 @@
+// pd_mlmc.cu -- multilevel Monte Carlo driver (Section 4): coupled fine /
+// coarse samples on nested grids sharing one KL realisation, FP64 level
+// sums on the GPU, the estimator Q_ML = sum_l Y_hat_l (Eq. MLMC_estimator),
+// the sample variance of Eq. sample_variance and the optimal allocation of
+// Eq. sample_allocation.
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "pd_internal.cuh"
+
+namespace pdi {
+
+// Y = Qf - Qc and the FP64 sums of Y and Y^2 over one batch, in a fixed order
+// (thread t sums t, t + 256, ...; then a fixed tree), one CTA.
+__global__ void k_level_sums(int n, const double *qf, const double *qc, double *y, double *out2) {
+    __shared__ double s1[256], s2[256];
+    double a = 0.0, b = 0.0;
+    for (int t = threadIdx.x; t < n; t += 256) {
+        const double v = qf[t] - (qc ? qc[t] : 0.0);
+        y[t] = v;
+        a += v;
+        b += v * v;
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            s1[threadIdx.x] += s1[threadIdx.x + o];
+            s2[threadIdx.x] += s2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out2[0] = s1[0];
+        out2[1] = s2[0];
+    }
+}
+
+__global__ void k_iota(uint64_t start, int n, uint64_t *ids) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) ids[t] = start + (uint64_t)t;
+}
+
+struct Mesh {
+    int32_t *row = nullptr, *col = nullptr;
+    int64_t nb = 0;
+    ~Mesh() {
+        cudaFree(row);
+        cudaFree(col);
+    }
+};
+
+static int make_mesh(const pd_grid &g, Mesh &m, cudaStream_t s) {
+    const long long N = (long long)g.nx * g.ny * g.nz;
+    PD_TRY(dalloc(&m.row, N + 1));
+    PD_TRY(pd_build_neighbours(&g, m.row, nullptr, 0, &m.nb, (pd_stream)s));
+    PD_TRY(dalloc(&m.col, m.nb));
+    PD_TRY(pd_build_neighbours(&g, m.row, m.col, m.nb, &m.nb, (pd_stream)s));
+    return PD_OK;
+}
+
+struct Buffers {
+    uint64_t *ids = nullptr;
+    double *xi = nullptr, *qf = nullptr, *qc = nullptr, *y = nullptr, *sums = nullptr;
+    float *ff = nullptr, *fc = nullptr;
+    int32_t *ps = nullptr, *nd = nullptr, *ndc = nullptr;
+    ~Buffers() {
+        cudaFree(ids);
+        cudaFree(xi);
+        cudaFree(qf);
+        cudaFree(qc);
+        cudaFree(y);
+        cudaFree(sums);
+        cudaFree(ff);
+        cudaFree(fc);
+        cudaFree(ps);
+        cudaFree(nd);
+        cudaFree(ndc);
+    }
+};
+
+static int run_level(const pd_mlmc_cfg *cfg, pd_field *field, int l, pd_mlmc_level *lv, double *q_fine,
+                     double *q_coarse, cudaStream_t s) {
+    const int64_t n_total = cfg->n_samples[l];
+    lv->n = 0;
+    lv->sum_y = lv->sum_y2 = 0.0;
+    lv->cost_s = 0.0;
+    lv->steps = 0;
+    lv->bond_updates = 0;
+    if (n_total <= 0) return PD_OK;
+    const int K = cfg->field.n_modes;
+    const int Bmax = (int)std::min<int64_t>(cfg->batch, n_total);
+    Mesh mf, mc;
+    PD_TRY(make_mesh(cfg->grid[l], mf, s));
+    if (l > 0) PD_TRY(make_mesh(cfg->grid[l - 1], mc, s));
+    const long long Nf = (long long)cfg->grid[l].nx * cfg->grid[l].ny * cfg->grid[l].nz;
+    const long long Nc = l > 0 ? (long long)cfg->grid[l - 1].nx * cfg->grid[l - 1].ny * cfg->grid[l - 1].nz : 0;
+    Buffers bf;
+    PD_TRY(dalloc(&bf.ids, Bmax));
+    PD_TRY(dalloc(&bf.xi, (size_t)Bmax * K));
+    PD_TRY(dalloc(&bf.qf, Bmax));
+    PD_TRY(dalloc(&bf.qc, Bmax));
+    PD_TRY(dalloc(&bf.y, Bmax));
+    PD_TRY(dalloc(&bf.sums, 2));
+    PD_TRY(dalloc(&bf.ff, (size_t)Bmax * Nf));
+    if (l > 0) PD_TRY(dalloc(&bf.fc, (size_t)Bmax * Nc));
+    PD_TRY(dalloc(&bf.ps, Bmax));
+    PD_TRY(dalloc(&bf.nd, Bmax));
+    PD_TRY(dalloc(&bf.ndc, Bmax));
+    pd_state *sf = nullptr, *sc = nullptr;
+    int cur_b = 0;
+    int rc = PD_OK;
+    std::vector<double> hq(Bmax), hqc(Bmax);
+    std::vector<int32_t> hnd(Bmax), hndc(Bmax);
+    for (int64_t first = 0; first < n_total && rc == PD_OK; first += Bmax) {
+        const int b = (int)std::min<int64_t>(Bmax, n_total - first);
+        if (b != cur_b) {
+            pd_state_destroy(sf);
+            pd_state_destroy(sc);
+            sf = sc = nullptr;
+            if ((rc = pd_state_create(&cfg->grid[l], mf.row, mf.col, mf.nb, &cfg->mat, &cfg->bc[l], b, &sf))) break;
+            if (l > 0 && (rc = pd_state_create(&cfg->grid[l - 1], mc.row, mc.col, mc.nb, &cfg->mat, &cfg->bc[l - 1],
+                                               b, &sc)))
+                break;
+            cur_b = b;
+        }
+        cudaStreamSynchronize(s);
+        const auto t0 = std::chrono::steady_clock::now();
+        k_iota<<<(b + 255) / 256, 256, 0, s>>>((uint64_t)first, b, bf.ids);
+        if ((rc = pd_draw_xi(cfg->seed, l, bf.ids, b, K, bf.xi, (pd_stream)s))) break;
+        if ((rc = pd_sample_field(field, l, bf.xi, b, bf.ff, l > 0 ? bf.fc : nullptr, (pd_stream)s))) break;
+        if ((rc = pd_state_reset(sf, bf.ff, nullptr, (pd_stream)s))) break;
+        if ((rc = pd_run_to_peak(sf, cfg->max_steps[l], bf.qf, bf.ps, bf.nd, (pd_stream)s))) break;
+        if (l > 0) {
+            if ((rc = pd_state_reset(sc, bf.fc, nullptr, (pd_stream)s))) break;
+            if ((rc = pd_run_to_peak(sc, cfg->max_steps[l - 1], bf.qc, bf.ps, bf.ndc, (pd_stream)s))) break;
+        }
+        k_level_sums<<<1, 256, 0, s>>>(b, bf.qf, l > 0 ? bf.qc : nullptr, bf.y, bf.sums);
+        double sums[2];
+        cudaMemcpyAsync(sums, bf.sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(hq.data(), bf.qf, b * sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(hnd.data(), bf.nd, b * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (l > 0) {
+            cudaMemcpyAsync(hqc.data(), bf.qc, b * sizeof(double), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(hndc.data(), bf.ndc, b * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            set_error("MLMC batch failed: %s", cudaGetErrorString(cudaGetLastError()));
+            rc = PD_ERR_CUDA;
+            break;
+        }
+        const auto t1 = std::chrono::steady_clock::now();
+        lv->cost_s += std::chrono::duration<double>(t1 - t0).count();
+        lv->sum_y += sums[0];
+        lv->sum_y2 += sums[1];
+        lv->n += b;
+        for (int q = 0; q < b; ++q) {
+            lv->steps += hnd[q];
+            lv->bond_updates += (int64_t)hnd[q] * mf.nb;
+            if (l > 0) {
+                lv->steps += hndc[q];
+                lv->bond_updates += (int64_t)hndc[q] * mc.nb;
+            }
+            if (q_fine) q_fine[first + q] = hq[q];
+            if (q_coarse) q_coarse[first + q] = l > 0 ? hqc[q] : 0.0;
+        }
+    }
+    pd_state_destroy(sf);
+    pd_state_destroy(sc);
+    if (rc != PD_OK) return rc;
+    lv->mean = lv->sum_y / (double)lv->n;
+    lv->var = lv->sum_y2 / (double)lv->n - lv->mean * lv->mean;
+    lv->var_unbiased = lv->n > 1 ? lv->var * (double)lv->n / (double)(lv->n - 1) : 0.0;
+    return PD_OK;
+}
+
+}  // namespace pdi
+
+using namespace pdi;
+
+extern "C" int pd_mlmc_allocation(int32_t n_levels, const double *V, const double *C, double eps_s, int64_t *N) {
+    PD_REQUIRE(n_levels >= 1 && V && C && N, "n_levels >= 1 and V, C, N are required");
+    PD_REQUIRE(eps_s > 0, "eps_s must be positive");
+    double S = 0.0;
+    for (int l = 0; l < n_levels; ++l) {
+        PD_REQUIRE(V[l] >= 0 && C[l] > 0, "V >= 0 and C > 0 required");
+        S += std::sqrt(V[l] * C[l]);
+    }
+    for (int l = 0; l < n_levels; ++l) N[l] = (int64_t)std::floor(S * std::sqrt(V[l] / C[l]) / (eps_s * eps_s));
+    return PD_OK;
+}
+
+extern "C" int mlmc_estimate(const pd_mlmc_cfg *cfg, pd_mlmc_result *out, double *q_fine, double *q_coarse,
+                             pd_stream stream) {
+    PD_REQUIRE(cfg && out, "cfg and out are required");
+    PD_REQUIRE(cfg->n_levels >= 1 && cfg->n_levels <= PD_MAX_LEVELS, "n_levels out of range");
+    PD_REQUIRE(cfg->grid && cfg->bc && cfg->max_steps && cfg->n_samples, "per-level arrays are required");
+    PD_REQUIRE(cfg->batch >= 1 && cfg->batch <= 4096, "batch must be in [1, 4096]");
+    for (int l = 1; l < cfg->n_levels; ++l) {
+        const pd_grid &f = cfg->grid[l], &c = cfg->grid[l - 1];
+        PD_REQUIRE(f.nx == 2 * c.nx && f.ny == 2 * c.ny && f.nz == 2 * c.nz &&
+                       std::fabs(f.dx * 2.0 - c.dx) <= 1e-12 * c.dx,
+                   "grid %d is not the 2x refinement of grid %d", l, l - 1);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    pd_field *field = nullptr;
+    PD_TRY(pd_field_create(&cfg->grid[cfg->n_levels - 1], cfg->n_levels, &cfg->field, &field));
+    pd_mlmc_result r;
+    memset(&r, 0, sizeof(r));
+    r.n_levels = cfg->n_levels;
+    int rc = PD_OK;
+    int64_t off = 0;
+    for (int l = 0; l < cfg->n_levels && rc == PD_OK; ++l) {
+        rc = run_level(cfg, field, l, &r.level[l], q_fine ? q_fine + off : nullptr,
+                       q_coarse ? q_coarse + off : nullptr, s);
+        off += cfg->n_samples[l];
+    }
+    pd_field_destroy(field);
+    if (rc != PD_OK) return rc;
+    for (int l = 0; l < cfg->n_levels; ++l) {
+        if (r.level[l].n > 0) {
+            r.q_ml += r.level[l].mean;
+            r.var_ml += r.level[l].var / (double)r.level[l].n;
+        }
+    }
+    *out = r;
+    return PD_OK;
+}
