@@ -76,18 +76,25 @@ struct pd_state {
     int64_t N;
     int64_t nb;
     double dt, c, V;
-    // neighbour list: CSR copy and SELL-32 slot-major layout
+    // neighbour list: CSR copy and a SELL-C layout of stencil ids
     int32_t *row_ptr;
+    int32_t lanes;          // T lanes per node; C = 32 / T nodes per slice
     int64_t n_slices;
     int64_t sell_len;
-    long long *sell_off; // [n_slices]: first slot element of each slice
-    int32_t *sell_w;    // [n_slices]: slots per lane in the slice
-    int32_t *sell_col;  // [sell_len]: neighbour index, -1 = padding
+    long long *sell_off;    // [n_slices]: first element of each slice
+    int32_t *sell_m;        // [n_slices]: 32-wide rounds per slice (slots / T)
+    uint8_t *ids;           // [sell_len]: stencil id of each slot, 0xFF = padding
+    int32_t n_off;          // stencil size
+    float4 *xi_tab;         // [n_off]: xi (x, y, z) and |xi| in FP32
+    double4_32a *xid_tab;       // [n_off]: the same in FP64
+    int32_t *off_tab;       // [n_off]: linear index offset j - i
     // per-sample state
     void *dmg;          // float or double [B][sell_len]
-    double *u64;        // [B][N][3]
-    double *v64;        // [B][N][3]
-    void *rec[2];       // 32-byte gather records [B][N], double-buffered by step parity
+    double *u64;        // fp64 path: [B][N][3]
+    double *v64;        // fp64 path: [B][N][3]
+    float4 *vdf;        // mixed path: v as double-float, float4 hi[B][N] then float4 lo[B][N]
+    void *rec[2];       // gather records, double-buffered by step parity:
+                        // mixed: float4 hi[B][N] then float4 lo[B][N]; fp64: double4_32a [B][N]
     float *kappa;       // [B][N] or nullptr
     bool has_kappa;
     uint8_t *codes;     // [N][3]

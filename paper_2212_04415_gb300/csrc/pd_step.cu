@@ -4,51 +4,62 @@
 // control, and the FP64 reaction / peak-load reduction.
 //
 // Layout (per state; B samples share one mesh):
-//   * neighbour list as SELL-32: slices of 32 consecutive nodes, slot-major
-//     inside a slice, so lane l of a warp reads slot k of node 32 s + l at
-//     element off[s] + 32 k + l (one 128-byte line per warp per slot).
-//     Padding slots hold -1 and trail each row.
-//   * damage per directed bond in the same SELL order, per sample. Both
-//     directed copies of a bond evolve identically: the stretch, the per-bond
+//   * The grid is regular, so every bond of node i is one of the n_off
+//     stencil offsets (|k|^2 <= m^2): j = i + off[id], xi = dx k. The CSR
+//     neighbour list is stored as one byte per directed bond (the stencil
+//     id), in a SELL-C layout: slices of C = 32 / T consecutive nodes,
+//     slot-major inside a slice, rows padded (0xFF) to a multiple of T slots.
+//     Lane L of a warp serves node c = L % C of the slice and sub-lane
+//     t = L / C, which takes slots t, t + T, t + 2T, ...; round m of the warp
+//     reads the 32 consecutive elements off[s] + 32 m + L (one id byte and one
+//     damage word per lane: fully coalesced).
+//   * Damage per directed bond in the same order, per sample. Both directed
+//     copies of a bond evolve identically: the stretch, the per-bond
 //     properties and the law are symmetric in (i, j) bit for bit.
-//   * a 32-byte gather record per node (double-buffered by step parity):
-//       mixed: float4 (u_hi xyz, s0), float4 (u_lo xyz, packed grid coordinate)
-//              where u = u_hi + u_lo (double-float), so u_j - u_i keeps FP64-like
-//              accuracy with FP32 arithmetic;
-//       fp64:  double u xyz, float s0, packed coordinate.
-//   * FP64 u, v per node for the integrator (owner thread only).
-// One thread owns one (sample, node) pair and walks its row in CSR order, so
-// the nodal sum has a fixed order and needs no atomics. Blocks are ordered
-// sample-fastest so that all samples of a batch stream the shared neighbour
-// index through L2 together.
+//   * Gather records per node, double-buffered by step parity:
+//       mixed: float4 hi = (u_hi, s0), float4 lo = (u_lo, kappa), u = u_hi + u_lo
+//              (double-float), so u_j - u_i keeps FP64-like accuracy in FP32;
+//       fp64:  double4_32a (u, s0).
+//   * velocities: mixed path double-float float4 hi/lo pairs, fp64 path FP64
+//     (the fp64 path also keeps FP64 u next to its records).
+// Arithmetic: GB300 runs FP64 at about 1/64 of the FP32 rate, so the mixed
+// path issues no FP64 instruction per bond or per node. Each lane sums its
+// bonds in compensated FP32 (TwoSum pairs), the T lane partials are added in
+// double-float along a fixed xor tree (TwoSum is exact, so every sub-lane
+// ends with the same total), and sub-lane t integrates component t of its
+// node in double-float arithmetic (about 48 significant bits). FP64 is used
+// for the reaction of prescribed DOFs and its reduction only. The fp64 path
+// does everything in FP64. Order is fixed everywhere, so results are
+// deterministic with no atomics. Blocks are ordered sample-fastest so that the
+// samples of a batch stream the shared stencil ids through L2 together.
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "pd_internal.cuh"
 
 namespace pdi {
 
-struct RecMixed {
-    float4 hi;  // u_hi.x, u_hi.y, u_hi.z, s0
-    float4 lo;  // u_lo.x, u_lo.y, u_lo.z, coord bits
-};
-struct RecF64 {
-    double ux, uy, uz;
-    float s0;
-    int32_t coord;
-};
-static_assert(sizeof(RecMixed) == 32 && sizeof(RecF64) == 32, "records are 32 bytes");
-
 constexpr int kThreads = 256;
-constexpr int kMaxQ = 64;  // largest squared stencil radius in cells (m <= 8)
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxOff = 255;  // stencil ids fit a byte; 0xFF marks padding
+
+struct df {
+    float hi, lo;
+};
 
 struct StepArgs {
     long long N;
+    long long n_slices;
     int nblk;
     int B;
     const long long *sell_off;
-    const int32_t *sell_w;
-    const int32_t *sell_col;
+    const int32_t *sell_m;
+    const uint8_t *ids;
+    const float4 *xi_tab;
+    const double4_32a *xid_tab;
+    const int32_t *off_tab;
+    int n_off;
     void *dmg;
     long long sell_len;
     double *u64;
@@ -69,12 +80,14 @@ struct StepArgs {
     int k_local;
     double *F_out;
     double dt, rho, zeta, u_max;
+    double ca, dtr, icb, idt;  // 1 - zeta dt/2, dt/rho, 1/(1 + zeta dt/2), 1/dt
+    df ca_df, dtr_df, icb_df, dt_df;
+    float4 *vdf;
     int n_ramp;
     int max_steps;
     int use_stop;
     double cV;  // micromodulus x node volume
     double V;
-    double dx;
     double s_ratio, k, alpha, inv_1mek, inv_1pa;
 };
 
@@ -84,13 +97,55 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// ---- double-float arithmetic (an unevaluated pair hi + lo of FP32 numbers;
+// Dekker 1971, Knuth TAOCP vol. 2, 4.2.2): about 48 significant bits with
+// FP32 instructions only.
+
+// s + e = a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = a + b;
+    const float z = s - a;
+    const float e = (a - (s - z)) + (b - z);
+    return {s, e};
+}
+
+// s + e = a + b exactly when |a| >= |b| (Dekker's FastTwoSum).
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ df df_add(df x, df y) {
+    const df s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+
+__device__ __forceinline__ df df_mul(df x, df y) {
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return fast_two_sum(p, e);
+}
+
+__host__ __device__ __forceinline__ df df_split(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+// s + x with the rounding error carried in c (accumulation by TwoSum).
+__device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
+    const df t = two_sum(s, x);
+    s = t.hi;
+    c += t.lo;
+}
+
 template <typename T>
-__device__ __forceinline__ T law_damage(int law, T s, T s0, T sc, T k, T alpha, T inv_1mek,
-                                        T inv_1pa);
+__device__ __forceinline__ T law_damage(int law, T s, T s0, T sc, T k, T alpha, T inv_1mek, T inv_1pa);
 
 template <>
-__device__ __forceinline__ float law_damage<float>(int law, float s, float s0, float sc, float k,
-                                                   float alpha, float inv_1mek, float inv_1pa) {
+__device__ __forceinline__ float law_damage<float>(int law, float s, float s0, float sc, float k, float alpha,
+                                                   float inv_1mek, float inv_1pa) {
     if (s >= sc) return 1.0f;
     if (law == PD_LAW_BILINEAR) return 1.0f - s0 * (sc - s) / (s * (sc - s0));
     const float t = (s - s0) / (sc - s0);
@@ -99,9 +154,8 @@ __device__ __forceinline__ float law_damage<float>(int law, float s, float s0, f
 }
 
 template <>
-__device__ __forceinline__ double law_damage<double>(int law, double s, double s0, double sc,
-                                                     double k, double alpha, double inv_1mek,
-                                                     double inv_1pa) {
+__device__ __forceinline__ double law_damage<double>(int law, double s, double s0, double sc, double k,
+                                                     double alpha, double inv_1mek, double inv_1pa) {
     if (s >= sc) return 1.0;
     if (law == PD_LAW_BILINEAR) return 1.0 - s0 * (sc - s) / (s * (sc - s0));
     const double t = (s - s0) / (sc - s0);
@@ -114,197 +168,236 @@ __device__ __forceinline__ double ramp(const StepArgs &a, int n) {
     return a.u_max * (double)m / (double)a.n_ramp;
 }
 
-// One explicit step (or, with FORCE_ONLY, one force evaluation) of every
-// (sample, node) pair. Grid: nblk * B blocks, sample index fastest.
-template <bool F64, int LAW, bool KAPPA, bool FORCE_ONLY>
-__global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
-    __shared__ float sL0f[kMaxQ + 1];
-    __shared__ double sL0d[kMaxQ + 1];
-    __shared__ double red[kThreads / 32];
-    __shared__ int last_flag;
+__device__ __forceinline__ float pick3(float a, float b, float c, int q) { return q == 0 ? a : (q == 1 ? b : c); }
+__device__ __forceinline__ double pick3(double a, double b, double c, int q) { return q == 0 ? a : (q == 1 ? b : c); }
 
-    for (int t = threadIdx.x; t <= kMaxQ; t += blockDim.x) {
-        const double L0 = sqrt((double)t) * a.dx;
-        sL0d[t] = L0;
-        sL0f[t] = (float)L0;
-    }
-    __syncthreads();
+// One explicit step (or, with FORCE_ONLY, one force evaluation) of every
+// (sample, node) pair. Grid: ceil(n_slices / 8) * B blocks, sample fastest;
+// warp w of a block serves one slice. After the bond loop every sub-lane of a
+// node holds the node's total force; sub-lane t then integrates component t.
+template <int T, bool F64, int LAW, bool KAPPA, bool FORCE_ONLY>
+__global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
+    static_assert(T >= 2 && T <= 8, "2 to 8 lanes per node");
+    constexpr int C = 32 / T;
+    __shared__ float4 s_xi[kMaxOff];
+    __shared__ int s_off[kMaxOff];
+    __shared__ double4_32a s_xid[F64 ? kMaxOff : 1];
+    __shared__ double red[kWarps];
+    __shared__ double s_U[2];
+    __shared__ int last_flag;
 
     const int b = blockIdx.x % a.B;
     const int xb = blockIdx.x / a.B;
-    const long long i = (long long)xb * kThreads + threadIdx.x;
     const bool done = FORCE_ONLY ? false : (a.done[b] != 0);
     const int n = a.step[b];
+    for (int t = threadIdx.x; t < a.n_off; t += kThreads) {
+        s_xi[t] = a.xi_tab[t];
+        s_off[t] = a.off_tab[t];
+        if (F64) s_xid[t] = a.xid_tab[t];
+    }
+    if (threadIdx.x == 0) {
+        s_U[0] = ramp(a, n);
+        s_U[1] = ramp(a, n + 1);
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long sl = (long long)xb * kWarps + warp;
+    const int c = lane % C, t = lane / C;
+    const long long i = sl * C + c;
     double Rloc = 0.0;
 
-    if (!done && i < a.N) {
+    if (!done && sl < a.n_slices) {  // warp-uniform
+        const bool own = i < a.N;
         const size_t node = (size_t)b * a.N + i;
-        const long long sl = i >> 5;
-        const int lane = (int)(i & 31);
-        const int w = a.sell_w[sl];
-        const long long base = a.sell_off[sl] + lane;
-        const size_t dbase = (size_t)b * a.sell_len;
-        double Fx = 0.0, Fy = 0.0, Fz = 0.0;
-        int32_t ci;
-        float kap_i = 1.0f;
-        if (KAPPA) kap_i = a.kappa[node];
-
+        const size_t BN = (size_t)a.B * a.N;
         if (F64) {
-            const RecF64 *rin = (const RecF64 *)((n & 1) ? a.rec1 : a.rec0) + (size_t)b * a.N;
-            double *dm = (double *)a.dmg + dbase;
-            const RecF64 me = rin[i];
-            ci = me.coord;
-            const int ix = ci & 2047, iy = (ci >> 11) & 2047, iz = ci >> 22;
-            const double s0i = me.s0;
-            for (int kk = 0; kk < w; ++kk) {
-                const long long e = base + 32ll * kk;
-                const int j = __ldg(a.sell_col + e);
-                if (j < 0) break;
-                const RecF64 rj = rin[j];
-                const int cj = rj.coord;
-                const int ddx = (cj & 2047) - ix, ddy = ((cj >> 11) & 2047) - iy, ddz = (cj >> 22) - iz;
-                const int q = ddx * ddx + ddy * ddy + ddz * ddz;
-                const double L0 = sL0d[q];
-                const double xx = ddx * a.dx, xy = ddy * a.dx, xz = ddz * a.dx;
-                const double ex = rj.ux - me.ux, ey = rj.uy - me.uy, ez = rj.uz - me.uz;
-                const double yx = xx + ex, yy = xy + ey, yz = xz + ez;
-                const double L = sqrt(yx * yx + yy * yy + yz * yz);
-                const double s = (2.0 * (xx * ex + xy * ey + xz * ez) + (ex * ex + ey * ey + ez * ez)) /
-                                 (L0 * (L + L0));
-                const double s0 = 0.5 * (s0i + (double)rj.s0);
-                double d = dm[e];
-                if (s > s0) {
-                    const double dl = law_damage<double>(LAW, s, s0, a.s_ratio * s0, a.k, a.alpha,
-                                                         a.inv_1mek, a.inv_1pa);
-                    if (dl > d) {
-                        d = dl;
-                        dm[e] = d;
+            double Fx = 0.0, Fy = 0.0, Fz = 0.0;
+            const double4_32a *rin = (const double4_32a *)((n & 1) ? a.rec1 : a.rec0) + (size_t)b * a.N;
+            if (own) {
+                const int M = a.sell_m[sl];
+                const long long e0 = a.sell_off[sl] + lane;
+                double *dm = (double *)a.dmg + (size_t)b * a.sell_len;
+                const double4_32a me = rin[i];
+                const double kap_i = KAPPA ? (double)a.kappa[node] : 1.0;
+                for (int m = 0; m < M; ++m) {
+                    const long long e = e0 + 32ll * m;
+                    const int id = a.ids[e];
+                    if (id == 0xFF) break;
+                    const long long j = i + s_off[id];
+                    const double4_32a xl = s_xid[id];
+                    const double4_32a rj = rin[j];
+                    const double ex = rj.x - me.x, ey = rj.y - me.y, ez = rj.z - me.z;
+                    const double yx = xl.x + ex, yy = xl.y + ey, yz = xl.z + ez;
+                    const double L = sqrt(yx * yx + yy * yy + yz * yz);
+                    const double s =
+                        (2.0 * (xl.x * ex + xl.y * ey + xl.z * ez) + (ex * ex + ey * ey + ez * ez)) / (xl.w * (L + xl.w));
+                    const double s0 = 0.5 * (me.w + rj.w);
+                    double d = dm[e];
+                    if (s > s0) {
+                        const double dl =
+                            law_damage<double>(LAW, s, s0, a.s_ratio * s0, a.k, a.alpha, a.inv_1mek, a.inv_1pa);
+                        if (dl > d) {
+                            d = dl;
+                            dm[e] = d;
+                        }
                     }
+                    double cv = a.cV;
+                    if (KAPPA) cv = a.cV * 0.5 * (kap_i + (double)a.kappa[(size_t)b * a.N + j]);
+                    const double g = cv * (1.0 - d) * s / L;
+                    Fx += g * yx;
+                    Fy += g * yy;
+                    Fz += g * yz;
                 }
-                double cv = a.cV;
-                if (KAPPA) cv = a.cV * 0.5 * ((double)kap_i + (double)a.kappa[(size_t)b * a.N + j]);
-                const double g = cv * (1.0 - d) * s / L;
-                Fx += g * yx;
-                Fy += g * yy;
-                Fz += g * yz;
             }
-        } else {
-            const RecMixed *rin = (const RecMixed *)((n & 1) ? a.rec1 : a.rec0) + (size_t)b * a.N;
-            float *dm = (float *)a.dmg + dbase;
-            const float4 hi = __ldg(&rin[i].hi);
-            const float4 lo = __ldg(&rin[i].lo);
-            ci = __float_as_int(lo.w);
-            const int ix = ci & 2047, iy = (ci >> 11) & 2047, iz = ci >> 22;
-            const float dxf = (float)a.dx;
-            const float cVf = (float)a.cV;
-            const float sr = (float)a.s_ratio, kf = (float)a.k, af = (float)a.alpha;
-            const float i1 = (float)a.inv_1mek, i2 = (float)a.inv_1pa;
-            for (int kk = 0; kk < w; ++kk) {
-                const long long e = base + 32ll * kk;
-                const int j = __ldg(a.sell_col + e);
-                if (j < 0) break;
-                const float4 hj = __ldg(&rin[j].hi);
-                const float4 lj = __ldg(&rin[j].lo);
-                const int cj = __float_as_int(lj.w);
-                const int ddx = (cj & 2047) - ix, ddy = ((cj >> 11) & 2047) - iy, ddz = (cj >> 22) - iz;
-                const int q = ddx * ddx + ddy * ddy + ddz * ddz;
-                const float L0 = sL0f[q];
-                const float xx = (float)ddx * dxf, xy = (float)ddy * dxf, xz = (float)ddz * dxf;
-                const float ex = (hj.x - hi.x) + (lj.x - lo.x);
-                const float ey = (hj.y - hi.y) + (lj.y - lo.y);
-                const float ez = (hj.z - hi.z) + (lj.z - lo.z);
-                const float yx = xx + ex, yy = xy + ey, yz = xz + ez;
-                const float L = sqrtf(yx * yx + yy * yy + yz * yz);
-                const float s = (2.0f * (xx * ex + xy * ey + xz * ez) + (ex * ex + ey * ey + ez * ez)) /
-                                (L0 * (L + L0));
-                const float s0 = 0.5f * (hi.w + hj.w);
-                float d = dm[e];
-                if (s > s0) {
-                    const float dl = law_damage<float>(LAW, s, s0, sr * s0, kf, af, i1, i2);
-                    if (dl > d) {
-                        d = dl;
-                        dm[e] = d;
-                    }
-                }
-                float cv = cVf;
-                if (KAPPA) cv = cVf * 0.5f * (kap_i + a.kappa[(size_t)b * a.N + j]);
-                const float g = cv * (1.0f - d) * s / L;
-                Fx += (double)(g * yx);
-                Fy += (double)(g * yy);
-                Fz += (double)(g * yz);
-            }
-        }
-
-        if (FORCE_ONLY) {
-            a.F_out[3 * node + 0] = Fx;
-            a.F_out[3 * node + 1] = Fy;
-            a.F_out[3 * node + 2] = Fz;
-        } else {
-            const double F[3] = {Fx, Fy, Fz};
-            const double U0 = ramp(a, n), U1 = ramp(a, n + 1);
-            const double ca = 1.0 - 0.5 * a.zeta * a.dt;
-            const double cb = 1.0 + 0.5 * a.zeta * a.dt;
-            double un[3];
-            double *u = a.u64 + 3 * node;
-            double *v = a.v64 + 3 * node;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const uint8_t code = a.codes[3 * i + c];
-                double uc = u[c], vc = v[c];
-                if (code == 0) {
-                    vc = (ca * vc + a.dt * F[c] / a.rho) / cb;
-                    uc = uc + a.dt * vc;
-                } else if (code == 1) {
-                    uc = 0.0;
-                    vc = 0.0;
-                } else {
-                    const double sg = code == 2 ? 1.0 : -1.0;
-                    Rloc += (code == 2 ? -F[c] : F[c]) * a.V;
-                    vc = sg * (U1 - U0) / a.dt;
-                    uc = sg * U1;
-                }
-                u[c] = uc;
-                v[c] = vc;
-                un[c] = uc;
+            for (int o = C; o < 32; o <<= 1) {
+                Fx += __shfl_xor_sync(0xffffffffu, Fx, o);
+                Fy += __shfl_xor_sync(0xffffffffu, Fy, o);
+                Fz += __shfl_xor_sync(0xffffffffu, Fz, o);
             }
-            if (F64) {
-                RecF64 *rout = (RecF64 *)((n & 1) ? a.rec0 : a.rec1) + (size_t)b * a.N;
-                const RecF64 *rin = (const RecF64 *)((n & 1) ? a.rec1 : a.rec0) + (size_t)b * a.N;
-                RecF64 r;
-                r.ux = un[0];
-                r.uy = un[1];
-                r.uz = un[2];
-                r.s0 = rin[i].s0;
-                r.coord = ci;
-                rout[i] = r;
-            } else {
-                RecMixed *rout = (RecMixed *)((n & 1) ? a.rec0 : a.rec1) + (size_t)b * a.N;
-                const RecMixed *rin = (const RecMixed *)((n & 1) ? a.rec1 : a.rec0) + (size_t)b * a.N;
-                const float hx = (float)un[0], hy = (float)un[1], hz = (float)un[2];
-                RecMixed r;
-                r.hi = make_float4(hx, hy, hz, rin[i].hi.w);
-                r.lo = make_float4((float)(un[0] - (double)hx), (float)(un[1] - (double)hy),
-                                   (float)(un[2] - (double)hz), __int_as_float(ci));
-                rout[i] = r;
+            if (own) {
+                for (int q = t; q < 3; q += T) {
+                    const double F = pick3(Fx, Fy, Fz, q);
+                    if (FORCE_ONLY) {
+                        a.F_out[3 * node + q] = F;
+                        continue;
+                    }
+                    const uint8_t code = a.codes[3 * i + q];
+                    double uc = a.u64[3 * node + q], vc = a.v64[3 * node + q];
+                    if (code == 0) {
+                        vc = (a.ca * vc + a.dtr * F) * a.icb;
+                        uc = uc + a.dt * vc;
+                    } else if (code == 1) {
+                        uc = 0.0;
+                        vc = 0.0;
+                    } else {
+                        const double sg = code == 2 ? 1.0 : -1.0;
+                        Rloc -= sg * F * a.V;
+                        vc = sg * (s_U[1] - s_U[0]) * a.idt;
+                        uc = sg * s_U[1];
+                    }
+                    a.u64[3 * node + q] = uc;
+                    a.v64[3 * node + q] = vc;
+                    double *ro = (double *)((double4_32a *)((n & 1) ? a.rec0 : a.rec1) + node);
+                    ro[q] = uc;
+                }
+            }
+        } else {
+            const float4 *rhi = (const float4 *)((n & 1) ? a.rec1 : a.rec0) + (size_t)b * a.N;
+            const float4 *rlo = rhi + BN;
+            float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+            float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
+            if (own) {
+                const int M = a.sell_m[sl];
+                const long long e0 = a.sell_off[sl] + lane;
+                float *dm = (float *)a.dmg + (size_t)b * a.sell_len;
+                hi = __ldg(rhi + i);
+                lo = __ldg(rlo + i);
+                const float cVf = (float)a.cV;
+                const float sr = (float)a.s_ratio, kf = (float)a.k, af = (float)a.alpha;
+                const float i1 = (float)a.inv_1mek, i2 = (float)a.inv_1pa;
+                for (int m = 0; m < M; ++m) {
+                    const long long e = e0 + 32ll * m;
+                    const int id = __ldg(a.ids + e);
+                    if (id == 0xFF) break;
+                    const long long j = i + s_off[id];
+                    const float4 xl = s_xi[id];
+                    const float4 hj = __ldg(rhi + j);
+                    const float4 lj = __ldg(rlo + j);
+                    const float ex = (hj.x - hi.x) + (lj.x - lo.x);
+                    const float ey = (hj.y - hi.y) + (lj.y - lo.y);
+                    const float ez = (hj.z - hi.z) + (lj.z - lo.z);
+                    const float yx = xl.x + ex, yy = xl.y + ey, yz = xl.z + ez;
+                    const float y2 = yx * yx + yy * yy + yz * yz;
+                    const float rL = rsqrtf(y2);
+                    const float L = y2 * rL;
+                    const float s = __fdividef(2.0f * (xl.x * ex + xl.y * ey + xl.z * ez) + (ex * ex + ey * ey + ez * ez),
+                                               xl.w * (L + xl.w));
+                    const float s0 = 0.5f * (hi.w + hj.w);
+                    float d = dm[e];
+                    if (s > s0) {
+                        const float dl = law_damage<float>(LAW, s, s0, sr * s0, kf, af, i1, i2);
+                        if (dl > d) {
+                            d = dl;
+                            dm[e] = d;
+                        }
+                    }
+                    float cv = cVf;
+                    if (KAPPA) cv = cVf * 0.5f * (lo.w + lj.w);
+                    const float g = cv * (1.0f - d) * s * rL;
+                    two_sum_acc(sx, cx, g * yx);
+                    two_sum_acc(sy, cy, g * yy);
+                    two_sum_acc(sz, cz, g * yz);
+                }
+            }
+            // add the T sub-lane partials of each node in double-float (fixed
+            // xor tree; TwoSum is exact, so partners get identical totals)
+#pragma unroll
+            for (int o = C; o < 32; o <<= 1) {
+                const float px = __shfl_xor_sync(0xffffffffu, sx, o), qx = __shfl_xor_sync(0xffffffffu, cx, o);
+                const float py = __shfl_xor_sync(0xffffffffu, sy, o), qy = __shfl_xor_sync(0xffffffffu, cy, o);
+                const float pz = __shfl_xor_sync(0xffffffffu, sz, o), qz = __shfl_xor_sync(0xffffffffu, cz, o);
+                df r = two_sum(sx, px);
+                sx = r.hi;
+                cx = r.lo + (cx + qx);
+                r = two_sum(sy, py);
+                sy = r.hi;
+                cy = r.lo + (cy + qy);
+                r = two_sum(sz, pz);
+                sz = r.hi;
+                cz = r.lo + (cz + qz);
+            }
+            if (own) {
+                for (int q = t; q < 3; q += T) {
+                    const df F = two_sum(pick3(sx, sy, sz, q), pick3(cx, cy, cz, q));
+                    if (FORCE_ONLY) {
+                        a.F_out[3 * node + q] = (double)F.hi + (double)F.lo;
+                        continue;
+                    }
+                    const uint8_t code = a.codes[3 * i + q];
+                    df u = {pick3(hi.x, hi.y, hi.z, q), pick3(lo.x, lo.y, lo.z, q)};
+                    float *vh = (float *)(a.vdf + node);
+                    float *vl = (float *)(a.vdf + BN + node);
+                    df v = {vh[q], vl[q]};
+                    if (code == 0) {
+                        v = df_mul(df_add(df_mul(a.ca_df, v), df_mul(a.dtr_df, F)), a.icb_df);
+                        u = df_add(u, df_mul(a.dt_df, v));
+                    } else if (code == 1) {
+                        u = {0.f, 0.f};
+                        v = {0.f, 0.f};
+                    } else {
+                        const double sg = code == 2 ? 1.0 : -1.0;
+                        Rloc -= sg * ((double)F.hi + (double)F.lo) * a.V;
+                        v = df_split(sg * (s_U[1] - s_U[0]) * a.idt);
+                        u = df_split(sg * s_U[1]);
+                    }
+                    vh[q] = v.hi;
+                    vl[q] = v.lo;
+                    float *oh = (float *)((float4 *)((n & 1) ? a.rec0 : a.rec1) + node);
+                    float *ol = (float *)((float4 *)((n & 1) ? a.rec0 : a.rec1) + BN + node);
+                    oh[q] = u.hi;
+                    ol[q] = u.lo;
+                }
             }
         }
     }
 
     if (FORCE_ONLY || done) return;  // uniform per block
 
-    // deterministic reaction reduction: warp tree, then warps in order
-    Rloc = warp_sum(Rloc);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // deterministic reaction reduction: warp tree (skipped by warps without a
+    // prescribed DOF, whose sum is exactly 0), warps in order, blocks in order
+    if (__any_sync(0xffffffffu, Rloc != 0.0)) Rloc = warp_sum(Rloc);
     if (lane == 0) red[warp] = Rloc;
     __syncthreads();
     if (warp == 0) {
-        double v = lane < kThreads / 32 ? red[lane] : 0.0;
-        v = warp_sum(v);
+        double v = lane < kWarps ? red[lane] : 0.0;
+        if (__any_sync(0xffffffffu, v != 0.0)) v = warp_sum(v);
         if (lane == 0) {
             a.partial[(size_t)b * a.nblk + xb] = v;
             __threadfence();
-            const unsigned t = atomicAdd(&a.ticket[b], 1u);
-            last_flag = (t == (unsigned)(a.nblk - 1));
+            const unsigned tk = atomicAdd(&a.ticket[b], 1u);
+            last_flag = (tk == (unsigned)(a.nblk - 1));
         }
     }
     __syncthreads();
@@ -313,7 +406,7 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
         __threadfence();
         const volatile double *p = a.partial + (size_t)b * a.nblk;
         double v = 0.0;
-        for (int t = lane; t < a.nblk; t += 32) v += p[t];
+        for (int q = lane; q < a.nblk; q += 32) v += p[q];
         v = warp_sum(v);
         if (lane == 0) {
             const double R = v;
@@ -339,28 +432,47 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
 
 // ---------------------------------------------------------------- set-up
 
-__global__ void k_slice_width(const int32_t *row_ptr, long long N, long long n_slices, int32_t *w) {
+// Rounds per slice: ceil(max row length / T).
+__global__ void k_slice_rounds(const int32_t *row_ptr, long long N, long long n_slices, int C, int T, int32_t *m) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_slices) return;
-    int m = 0;
-    for (int l = 0; l < 32; ++l) {
-        const long long i = s * 32 + l;
-        if (i < N) m = max(m, row_ptr[i + 1] - row_ptr[i]);
+    int w = 0;
+    for (int l = 0; l < C; ++l) {
+        const long long i = s * C + l;
+        if (i < N) w = max(w, row_ptr[i + 1] - row_ptr[i]);
     }
-    w[s] = m;
+    m[s] = (w + T - 1) / T;
 }
 
-__global__ void k_fill_sell(const int32_t *row_ptr, const int32_t *col, long long N,
-                            long long n_slices, const long long *off, const int32_t *w,
-                            int32_t *sell_col) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_slices * 32) return;
-    const long long s = t >> 5;
-    const int lane = (int)(t & 31);
-    const long long i = s * 32 + lane;
+// Stencil id of every slot; flags neighbours that are not stencil offsets.
+__global__ void k_fill_ids(const int32_t *row_ptr, const int32_t *col, const int32_t *coord, long long N,
+                           long long n_slices, int C, int T, const long long *off, const int32_t *m,
+                           const int16_t *box, int R, uint8_t *ids, int32_t *bad) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_slices * C) return;
+    const long long s = q / C;
+    const int c = (int)(q % C);
+    const long long i = s * C + c;
     const int len = i < N ? row_ptr[i + 1] - row_ptr[i] : 0;
-    const long long r0 = i < N ? row_ptr[i] : 0;
-    for (int k = 0; k < w[s]; ++k) sell_col[off[s] + 32ll * k + lane] = k < len ? col[r0 + k] : -1;
+    const int W = T * m[s];
+    const int ci = i < N ? coord[i] : 0;
+    const int D = 2 * R + 1;
+    for (int k = 0; k < W; ++k) {
+        uint8_t id = 0xFF;
+        if (k < len) {
+            const int cj = coord[col[row_ptr[i] + k]];
+            const int dx = (cj & 2047) - (ci & 2047), dy = ((cj >> 11) & 2047) - ((ci >> 11) & 2047),
+                      dz = (cj >> 22) - (ci >> 22);
+            int v = -1;
+            if (abs(dx) <= R && abs(dy) <= R && abs(dz) <= R) v = box[(dz + R) * D * D + (dy + R) * D + (dx + R)];
+            if (v < 0) {
+                *bad = 1;
+                v = 0xFF;
+            }
+            id = (uint8_t)v;
+        }
+        ids[off[s] + (long long)k * C + c] = id;
+    }
 }
 
 __global__ void k_coords(int nx, int ny, long long N, int32_t *coord) {
@@ -371,8 +483,8 @@ __global__ void k_coords(int nx, int ny, long long N, int32_t *coord) {
 }
 
 // Per-node Silling-Askari stable step sqrt(2 rho / sum_j c V / |xi_ij|), sum in CSR order.
-__global__ void k_dt_sum(const int32_t *row_ptr, const int32_t *col, const int32_t *coord,
-                         long long N, double cV, double dx, double rho, double *dti) {
+__global__ void k_dt_sum(const int32_t *row_ptr, const int32_t *col, const int32_t *coord, long long N, double cV,
+                         double dx, double rho, double *dti) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int ci = coord[i];
@@ -401,33 +513,35 @@ __global__ void k_min(const double *x, long long n, double *out) {
 }
 
 template <bool F64>
-__global__ void k_reset(long long N, int B, const float *s0, const int32_t *coord, double *u64,
-                        double *v64, void *rec0, void *rec1) {
+__global__ void k_reset(long long N, int B, const float *s0, const float *kappa, double *u64, double *v64,
+                        float4 *vdf, void *rec0, void *rec1) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N * B) return;
-    const long long i = t % N;
-    for (int c = 0; c < 3; ++c) {
-        u64[3 * t + c] = 0.0;
-        v64[3 * t + c] = 0.0;
-    }
+    const float s = s0 ? s0[t] : 1e-4f;
     if (F64) {
-        RecF64 r;
-        r.ux = r.uy = r.uz = 0.0;
-        r.s0 = s0 ? s0[t] : 1e-4f;
-        r.coord = coord[i];
-        ((RecF64 *)rec0)[t] = r;
-        ((RecF64 *)rec1)[t] = r;
+        for (int c = 0; c < 3; ++c) {
+            u64[3 * t + c] = 0.0;
+            v64[3 * t + c] = 0.0;
+        }
+        const double4_32a r = make_double4_32a(0.0, 0.0, 0.0, (double)s);
+        ((double4_32a *)rec0)[t] = r;
+        ((double4_32a *)rec1)[t] = r;
     } else {
-        RecMixed r;
-        r.hi = make_float4(0.f, 0.f, 0.f, s0 ? s0[t] : 1e-4f);
-        r.lo = make_float4(0.f, 0.f, 0.f, __int_as_float(coord[i]));
-        ((RecMixed *)rec0)[t] = r;
-        ((RecMixed *)rec1)[t] = r;
+        const size_t BN = (size_t)N * B;
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 hi = make_float4(0.f, 0.f, 0.f, s);
+        const float4 lo = make_float4(0.f, 0.f, 0.f, kappa ? kappa[t] : 1.0f);
+        vdf[t] = z;
+        vdf[BN + t] = z;
+        ((float4 *)rec0)[t] = hi;
+        ((float4 *)rec1)[t] = hi;
+        ((float4 *)rec0)[BN + t] = lo;
+        ((float4 *)rec1)[BN + t] = lo;
     }
 }
 
-__global__ void k_reset_run(int B, int32_t *step, int32_t *done, int32_t *status, double *peak,
-                            int32_t *peak_step, unsigned *ticket, int step0) {
+__global__ void k_reset_run(int B, int32_t *step, int32_t *done, int32_t *status, double *peak, int32_t *peak_step,
+                            unsigned *ticket, int step0) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     step[b] = step0;
@@ -438,85 +552,104 @@ __global__ void k_reset_run(int B, int32_t *step, int32_t *done, int32_t *status
     ticket[b] = 0u;
 }
 
-// Load u (and the gather record of the current parity) from caller arrays.
+// Load u, v from caller arrays (NULL keeps the current values) and refresh
+// both parities of the gather records; mixed path splits into double-float.
 template <bool F64>
-__global__ void k_load_u(long long N, int B, const double *u, const double *v, double *u64,
-                         double *v64, const int32_t *step, void *rec0, void *rec1) {
+__global__ void k_load_u(long long N, int B, const double *u, const double *v, double *u64, double *v64,
+                         float4 *vdf, const int32_t *step, void *rec0, void *rec1) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N * B) return;
-    const int b = (int)(t / N);
-    const int par = step[b] & 1;
-    double uu[3];
-    for (int c = 0; c < 3; ++c) {
-        uu[c] = u ? u[3 * t + c] : u64[3 * t + c];
-        u64[3 * t + c] = uu[c];
-        if (v) v64[3 * t + c] = v[3 * t + c];
-    }
+    const size_t BN = (size_t)N * B;
     if (F64) {
-        RecF64 *r = (RecF64 *)(par ? rec1 : rec0) + t;
-        r->ux = uu[0];
-        r->uy = uu[1];
-        r->uz = uu[2];
+        double uu[3];
+        for (int c = 0; c < 3; ++c) {
+            uu[c] = u ? u[3 * t + c] : u64[3 * t + c];
+            u64[3 * t + c] = uu[c];
+            if (v) v64[3 * t + c] = v[3 * t + c];
+        }
+        for (int p = 0; p < 2; ++p) {
+            double4_32a *r = (double4_32a *)(p ? rec1 : rec0) + t;
+            r->x = uu[0];
+            r->y = uu[1];
+            r->z = uu[2];
+        }
     } else {
-        RecMixed *r = (RecMixed *)(par ? rec1 : rec0) + t;
-        const float hx = (float)uu[0], hy = (float)uu[1], hz = (float)uu[2];
-        float4 hi = r->hi, lo = r->lo;
-        hi.x = hx;
-        hi.y = hy;
-        hi.z = hz;
-        lo.x = (float)(uu[0] - (double)hx);
-        lo.y = (float)(uu[1] - (double)hy);
-        lo.z = (float)(uu[2] - (double)hz);
-        r->hi = hi;
-        r->lo = lo;
-    }
-}
-
-// Copy the s0 field into both parities of the record (after a load).
-template <bool F64>
-__global__ void k_copy_s0_other(long long N, int B, const int32_t *step, void *rec0, void *rec1) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= N * B) return;
-    const int b = (int)(t / N);
-    const int par = step[b] & 1;
-    if (F64) {
-        RecF64 *src = (RecF64 *)(par ? rec1 : rec0) + t;
-        RecF64 *dst = (RecF64 *)(par ? rec0 : rec1) + t;
-        *dst = *src;
-    } else {
-        RecMixed *src = (RecMixed *)(par ? rec1 : rec0) + t;
-        RecMixed *dst = (RecMixed *)(par ? rec0 : rec1) + t;
-        *dst = *src;
+        const int par = step[t / N] & 1;
+        const float4 *cur_h = (const float4 *)(par ? rec1 : rec0) + t;
+        const float4 *cur_l = (const float4 *)(par ? rec1 : rec0) + BN + t;
+        float hx[3], lx[3];
+        for (int c = 0; c < 3; ++c) {
+            if (u) {
+                const df d = df_split(u[3 * t + c]);
+                hx[c] = d.hi;
+                lx[c] = d.lo;
+            } else {
+                hx[c] = ((const float *)cur_h)[c];
+                lx[c] = ((const float *)cur_l)[c];
+            }
+        }
+        for (int p = 0; p < 2; ++p) {
+            float4 *h = (float4 *)(p ? rec1 : rec0) + t;
+            float4 *l = (float4 *)(p ? rec1 : rec0) + BN + t;
+            h->x = hx[0];
+            h->y = hx[1];
+            h->z = hx[2];
+            l->x = lx[0];
+            l->y = lx[1];
+            l->z = lx[2];
+        }
+        if (v) {
+            const df a = df_split(v[3 * t + 0]), b = df_split(v[3 * t + 1]), c = df_split(v[3 * t + 2]);
+            vdf[t] = make_float4(a.hi, b.hi, c.hi, 0.f);
+            vdf[BN + t] = make_float4(a.lo, b.lo, c.lo, 0.f);
+        }
     }
 }
 
 // CSR-ordered damage <-> SELL-ordered damage.
 template <typename T, bool TO_SELL>
-__global__ void k_dmg_map(const int32_t *row_ptr, long long N, int B, long long nb,
-                          const long long *off, long long sell_len, T *sell, double *csr) {
+__global__ void k_dmg_map(const int32_t *row_ptr, long long N, int B, long long nb, int C, const long long *off,
+                          long long sell_len, T *sell, double *csr) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N * B) return;
     const int b = (int)(t / N);
     const long long i = t % N;
-    const long long s = i >> 5;
-    const int lane = (int)(i & 31);
+    const long long s = i / C;
+    const int c = (int)(i % C);
     const int r0 = row_ptr[i], len = row_ptr[i + 1] - r0;
     for (int k = 0; k < len; ++k) {
-        const long long e = (size_t)b * sell_len + off[s] + 32ll * k + lane;
-        const long long c = (size_t)b * nb + r0 + k;
+        const long long e = (long long)b * sell_len + off[s] + (long long)k * C + c;
+        const long long q = (long long)b * nb + r0 + k;
         if (TO_SELL)
-            sell[e] = (T)csr[c];
+            sell[e] = (T)csr[q];
         else
-            csr[c] = (double)sell[e];
+            csr[q] = (double)sell[e];
     }
 }
 
-__global__ void k_store_u(long long N, int B, const double *u64, const double *v64, double *u,
-                          double *v) {
+// Copy u, v out as FP64 (the mixed path adds its double-float pairs).
+template <bool F64>
+__global__ void k_store_u(long long N, int B, const double *u64, const double *v64, const float4 *vdf,
+                          const int32_t *step, const void *rec0, const void *rec1, double *u, double *v) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 3 * N * B) return;
-    if (u) u[t] = u64[t];
-    if (v) v[t] = v64[t];
+    if (t >= N * B) return;
+    const size_t BN = (size_t)N * B;
+    if (F64) {
+        for (int c = 0; c < 3; ++c) {
+            if (u) u[3 * t + c] = u64[3 * t + c];
+            if (v) v[3 * t + c] = v64[3 * t + c];
+        }
+    } else {
+        const int par = step[t / N] & 1;
+        const float *h = (const float *)((const float4 *)(par ? rec1 : rec0) + t);
+        const float *l = (const float *)((const float4 *)(par ? rec1 : rec0) + BN + t);
+        const float *vh = (const float *)(vdf + t);
+        const float *vl = (const float *)(vdf + BN + t);
+        for (int c = 0; c < 3; ++c) {
+            if (u) u[3 * t + c] = (double)h[c] + (double)l[c];
+            if (v) v[3 * t + c] = (double)vh[c] + (double)vl[c];
+        }
+    }
 }
 
 __global__ void k_run_init(int B, const int32_t *step, int32_t *done, int max_steps) {
@@ -536,8 +669,8 @@ __global__ void k_count_active(int B, const int32_t *done, int32_t *host_flag) {
     if (threadIdx.x == 0) *(volatile int32_t *)host_flag = cnt;
 }
 
-__global__ void k_copy_out(int B, const double *peak, const int32_t *peak_step,
-                           const int32_t *step, double *o_peak, int32_t *o_ps, int32_t *o_nd) {
+__global__ void k_copy_out(int B, const double *peak, const int32_t *peak_step, const int32_t *step,
+                           double *o_peak, int32_t *o_ps, int32_t *o_nd) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     if (o_peak) o_peak[b] = peak[b];
@@ -549,30 +682,43 @@ __global__ void k_copy_out(int B, const double *peak, const int32_t *peak_step,
 
 typedef void (*StepKernel)(const StepArgs);
 
-template <bool F64, bool FO>
-static StepKernel pick3(int law, bool kappa) {
-    if (law == PD_LAW_BILINEAR)
-        return kappa ? k_step<F64, 0, true, FO> : k_step<F64, 0, false, FO>;
-    return kappa ? k_step<F64, 1, true, FO> : k_step<F64, 1, false, FO>;
+template <int T, bool F64, bool FO>
+static StepKernel pick_law(int law, bool kappa) {
+    if (law == PD_LAW_BILINEAR) return kappa ? k_step<T, F64, 0, true, FO> : k_step<T, F64, 0, false, FO>;
+    return kappa ? k_step<T, F64, 1, true, FO> : k_step<T, F64, 1, false, FO>;
+}
+
+template <int T>
+static StepKernel pick_t(const pd_state *st, bool fo) {
+    const bool f64 = st->mat.precision == PD_PREC_FP64;
+    if (f64) return fo ? pick_law<T, true, true>(st->mat.law, st->has_kappa)
+                       : pick_law<T, true, false>(st->mat.law, st->has_kappa);
+    return fo ? pick_law<T, false, true>(st->mat.law, st->has_kappa)
+              : pick_law<T, false, false>(st->mat.law, st->has_kappa);
 }
 
 static StepKernel pick(const pd_state *st, bool force_only) {
-    const bool f64 = st->mat.precision == PD_PREC_FP64;
-    if (f64) return force_only ? pick3<true, true>(st->mat.law, st->has_kappa)
-                               : pick3<true, false>(st->mat.law, st->has_kappa);
-    return force_only ? pick3<false, true>(st->mat.law, st->has_kappa)
-                      : pick3<false, false>(st->mat.law, st->has_kappa);
+    switch (st->lanes) {
+        case 2: return pick_t<2>(st, force_only);
+        case 8: return pick_t<8>(st, force_only);
+        default: return pick_t<4>(st, force_only);
+    }
 }
 
 static StepArgs make_args(const pd_state *st) {
     StepArgs a;
     memset(&a, 0, sizeof(a));
     a.N = st->N;
+    a.n_slices = st->n_slices;
     a.nblk = st->nblk;
     a.B = st->B;
     a.sell_off = st->sell_off;
-    a.sell_w = st->sell_w;
-    a.sell_col = st->sell_col;
+    a.sell_m = st->sell_m;
+    a.ids = st->ids;
+    a.xi_tab = st->xi_tab;
+    a.xid_tab = st->xid_tab;
+    a.off_tab = st->off_tab;
+    a.n_off = st->n_off;
     a.dmg = st->dmg;
     a.sell_len = st->sell_len;
     a.u64 = st->u64;
@@ -591,13 +737,21 @@ static StepArgs make_args(const pd_state *st) {
     a.dt = st->dt;
     a.rho = st->mat.rho;
     a.zeta = st->mat.zeta;
+    a.ca = 1.0 - 0.5 * st->mat.zeta * st->dt;
+    a.dtr = st->dt / st->mat.rho;
+    a.icb = 1.0 / (1.0 + 0.5 * st->mat.zeta * st->dt);
+    a.idt = 1.0 / st->dt;
+    a.ca_df = df_split(a.ca);
+    a.dtr_df = df_split(a.dtr);
+    a.icb_df = df_split(a.icb);
+    a.dt_df = df_split(a.dt);
+    a.vdf = st->vdf;
     a.u_max = st->bc.u_max;
     a.n_ramp = st->bc.n_ramp;
     a.max_steps = 0x7fffffff;
     a.use_stop = 0;
     a.cV = st->c * st->V;
     a.V = st->V;
-    a.dx = st->g.dx;
     a.s_ratio = st->mat.s_ratio;
     a.k = st->mat.k;
     a.alpha = st->mat.alpha;
@@ -620,11 +774,15 @@ static void free_state(pd_state *st) {
     if (!st) return;
     cudaFree(st->row_ptr);
     cudaFree(st->sell_off);
-    cudaFree(st->sell_w);
-    cudaFree(st->sell_col);
+    cudaFree(st->sell_m);
+    cudaFree(st->ids);
+    cudaFree(st->xi_tab);
+    cudaFree(st->xid_tab);
+    cudaFree(st->off_tab);
     cudaFree(st->dmg);
     cudaFree(st->u64);
     cudaFree(st->v64);
+    cudaFree(st->vdf);
     cudaFree(st->rec[0]);
     cudaFree(st->rec[1]);
     cudaFree(st->kappa);
@@ -644,6 +802,45 @@ static void free_state(pd_state *st) {
     delete st;
 }
 
+// Stencil of the horizon: integer offsets with 0 < |k|^2 <= m^2, ordered by
+// ascending linear index offset (z, then y, then x), so a CSR row (sorted by
+// neighbour index) visits ids in ascending order.
+static int build_stencil(pd_state *st, int16_t **box_dev, int *R_out) {
+    const pd_grid &g = st->g;
+    const double m2 = g.m_ratio * g.m_ratio;
+    const int R = (int)std::ceil(g.m_ratio);
+    const int D = 2 * R + 1;
+    std::vector<int16_t> box((size_t)D * D * D, -1);
+    std::vector<float4> xt;
+    std::vector<double4_32a> xd;
+    std::vector<int32_t> ot;
+    for (int dz = -R; dz <= R; ++dz)
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx) {
+                const int q = dx * dx + dy * dy + dz * dz;
+                if (q == 0 || (double)q > m2) continue;
+                const double L0 = std::sqrt((double)q) * g.dx;
+                box[(size_t)(dz + R) * D * D + (dy + R) * D + (dx + R)] = (int16_t)xt.size();
+                xt.push_back(make_float4((float)dx * (float)g.dx, (float)dy * (float)g.dx, (float)dz * (float)g.dx,
+                                         (float)L0));
+                xd.push_back(make_double4_32a(dx * g.dx, dy * g.dx, dz * g.dx, L0));
+                ot.push_back(dx + g.nx * (dy + g.ny * dz));
+            }
+    PD_REQUIRE(xt.size() <= (size_t)kMaxOff - 1, "horizon stencil has %zu offsets (at most 254 supported)",
+               xt.size());
+    st->n_off = (int32_t)xt.size();
+    PD_TRY(dalloc(&st->xi_tab, xt.size()));
+    PD_TRY(dalloc(&st->xid_tab, xd.size()));
+    PD_TRY(dalloc(&st->off_tab, ot.size()));
+    PD_TRY(dalloc(box_dev, box.size()));
+    PD_CHECK_CUDA(cudaMemcpy(st->xi_tab, xt.data(), xt.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    PD_CHECK_CUDA(cudaMemcpy(st->xid_tab, xd.data(), xd.size() * sizeof(double4_32a), cudaMemcpyHostToDevice));
+    PD_CHECK_CUDA(cudaMemcpy(st->off_tab, ot.data(), ot.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    PD_CHECK_CUDA(cudaMemcpy(*box_dev, box.data(), box.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+    *R_out = R;
+    return PD_OK;
+}
+
 static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col) {
     const long long N = st->N;
     const int B = st->B;
@@ -652,32 +849,49 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
     PD_CHECK_CUDA(cudaMemcpy(st->row_ptr, row_ptr, (N + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice));
     int32_t last = 0;
     PD_CHECK_CUDA(cudaMemcpy(&last, st->row_ptr + N, sizeof(int32_t), cudaMemcpyDeviceToHost));
-    PD_REQUIRE((long long)last == st->nb, "row_ptr[N] = %d does not match n_bonds = %lld", last,
-               (long long)st->nb);
-    // SELL-32 layout
-    st->n_slices = (N + 31) / 32;
-    PD_TRY(dalloc(&st->sell_w, st->n_slices));
-    PD_TRY(dalloc(&st->sell_off, st->n_slices));
-    k_slice_width<<<blocks_for(st->n_slices), 256, 0, s>>>(st->row_ptr, N, st->n_slices, st->sell_w);
-    PD_CHECK_LAUNCH();
-    std::vector<int32_t> w(st->n_slices);
-    std::vector<long long> off(st->n_slices);
-    PD_CHECK_CUDA(cudaMemcpy(w.data(), st->sell_w, w.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
-    long long acc = 0;
-    for (long long q = 0; q < st->n_slices; ++q) {
-        off[q] = acc;
-        acc += 32ll * w[q];
-    }
-    st->sell_len = acc;
-    PD_CHECK_CUDA(cudaMemcpy(st->sell_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice));
-    PD_TRY(dalloc(&st->sell_col, st->sell_len));
-    k_fill_sell<<<blocks_for(st->n_slices * 32), 256, 0, s>>>(st->row_ptr, col, N, st->n_slices,
-                                                               st->sell_off, st->sell_w, st->sell_col);
-    PD_CHECK_LAUNCH();
-    // per-node constants
+    PD_REQUIRE((long long)last == st->nb, "row_ptr[N] = %d does not match n_bonds = %lld", last, (long long)st->nb);
     PD_TRY(dalloc(&st->coord, N));
     k_coords<<<blocks_for(N), 256, 0, s>>>(st->g.nx, st->g.ny, N, st->coord);
     PD_CHECK_LAUNCH();
+    // SELL-C layout of stencil ids
+    const int T = st->lanes, C = 32 / st->lanes;
+    st->n_slices = (N + C - 1) / C;
+    PD_TRY(dalloc(&st->sell_m, st->n_slices));
+    PD_TRY(dalloc(&st->sell_off, st->n_slices));
+    k_slice_rounds<<<blocks_for(st->n_slices), 256, 0, s>>>(st->row_ptr, N, st->n_slices, C, T, st->sell_m);
+    PD_CHECK_LAUNCH();
+    std::vector<int32_t> m(st->n_slices);
+    std::vector<long long> off(st->n_slices);
+    PD_CHECK_CUDA(cudaMemcpy(m.data(), st->sell_m, m.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    long long acc = 0;
+    for (long long q = 0; q < st->n_slices; ++q) {
+        off[q] = acc;
+        acc += 32ll * m[q];
+    }
+    st->sell_len = acc;
+    PD_CHECK_CUDA(cudaMemcpy(st->sell_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    int16_t *box = nullptr;
+    int R = 0;
+    int rc = build_stencil(st, &box, &R);
+    if (rc != PD_OK) {
+        cudaFree(box);
+        return rc;
+    }
+    int32_t *bad = nullptr;
+    if ((rc = dalloc(&st->ids, st->sell_len)) != PD_OK || (rc = dalloc(&bad, 1)) != PD_OK) {
+        cudaFree(box);
+        cudaFree(bad);
+        return rc;
+    }
+    cudaMemset(bad, 0, sizeof(int32_t));
+    k_fill_ids<<<blocks_for(st->n_slices * C), 256, 0, s>>>(st->row_ptr, col, st->coord, N, st->n_slices, C, T,
+                                                           st->sell_off, st->sell_m, box, R, st->ids, bad);
+    int32_t hbad = 0;
+    cudaError_t e = cudaMemcpy(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    cudaFree(box);
+    cudaFree(bad);
+    PD_CHECK_CUDA(e);
+    PD_REQUIRE(!hbad, "a CSR neighbour is not a horizon stencil offset of the grid");
     PD_TRY(dalloc(&st->codes, 3 * N));
     PD_TRY(pd_bc_codes(&st->g, &st->bc, st->codes, (pd_stream)s));
     // time step
@@ -687,11 +901,11 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
         double *dti = nullptr, *dmin = nullptr;
         PD_TRY(dalloc(&dti, N));
         PD_TRY(dalloc(&dmin, 1));
-        k_dt_sum<<<blocks_for(N), 256, 0, s>>>(st->row_ptr, col, st->coord, N, st->c * st->V, st->g.dx,
-                                               st->mat.rho, dti);
+        k_dt_sum<<<blocks_for(N), 256, 0, s>>>(st->row_ptr, col, st->coord, N, st->c * st->V, st->g.dx, st->mat.rho,
+                                               dti);
         k_min<<<1, 1024, 0, s>>>(dti, N, dmin);
         double h = 0.0;
-        cudaError_t e = cudaMemcpy(&h, dmin, sizeof(double), cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(&h, dmin, sizeof(double), cudaMemcpyDeviceToHost);
         cudaFree(dti);
         cudaFree(dmin);
         PD_CHECK_CUDA(e);
@@ -702,11 +916,15 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
     const bool f64 = st->mat.precision == PD_PREC_FP64;
     const size_t dsz = f64 ? sizeof(double) : sizeof(float);
     PD_CHECK_CUDA(cudaMalloc(&st->dmg, (size_t)B * st->sell_len * dsz));
-    PD_TRY(dalloc(&st->u64, 3 * N * B));
-    PD_TRY(dalloc(&st->v64, 3 * N * B));
+    if (f64) {
+        PD_TRY(dalloc(&st->u64, 3 * N * B));
+        PD_TRY(dalloc(&st->v64, 3 * N * B));
+    } else {
+        PD_TRY(dalloc(&st->vdf, 2 * N * B));
+    }
     PD_CHECK_CUDA(cudaMalloc(&st->rec[0], (size_t)B * N * 32));
     PD_CHECK_CUDA(cudaMalloc(&st->rec[1], (size_t)B * N * 32));
-    st->nblk = (int)((N + kThreads - 1) / kThreads);
+    st->nblk = (int)((st->n_slices + kWarps - 1) / kWarps);
     PD_TRY(dalloc(&st->step, B));
     PD_TRY(dalloc(&st->done, B));
     PD_TRY(dalloc(&st->status, B));
@@ -727,9 +945,8 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
 
 using namespace pdi;
 
-extern "C" int pd_state_create(const pd_grid *g, const int32_t *row_ptr, const int32_t *col,
-                               int64_t n_bonds, const pd_material *mat, const pd_bc *bc,
-                               int32_t batch, pd_state **out) {
+extern "C" int pd_state_create(const pd_grid *g, const int32_t *row_ptr, const int32_t *col, int64_t n_bonds,
+                               const pd_material *mat, const pd_bc *bc, int32_t batch, pd_state **out) {
     PD_REQUIRE(out != nullptr, "out is NULL");
     *out = nullptr;
     PD_TRY(validate_grid(g));
@@ -743,7 +960,8 @@ extern "C" int pd_state_create(const pd_grid *g, const int32_t *row_ptr, const i
     PD_REQUIRE(mat->zeta >= 0, "zeta must be >= 0");
     PD_REQUIRE(bc->type == PD_BC_BAR_TENSION || bc->type == PD_BC_BEAM_3PT, "unknown bc type");
     PD_REQUIRE(bc->n_ramp >= 1, "n_ramp must be >= 1");
-    PD_REQUIRE(g->m_ratio * g->m_ratio <= 64.0, "m_ratio^2 must be <= 64");
+    const long long NB = (long long)g->nx * g->ny * g->nz * batch;
+    PD_REQUIRE(NB < (1ll << 31), "nodes x batch must be below 2^31");
     pd_state *st = new pd_state();
     memset(st, 0, sizeof(*st));
     st->g = *g;
@@ -752,6 +970,11 @@ extern "C" int pd_state_create(const pd_grid *g, const int32_t *row_ptr, const i
     st->B = batch;
     st->N = (int64_t)g->nx * g->ny * g->nz;
     st->nb = n_bonds;
+    st->lanes = 4;
+    if (const char *e = std::getenv("PD_LANES")) {
+        const int v = std::atoi(e);
+        if (v == 2 || v == 4 || v == 8) st->lanes = v;
+    }
     const double delta = g->m_ratio * g->dx;
     st->c = 12.0 * mat->E / (M_PI * delta * delta * delta * delta);
     st->V = g->dx * g->dx * g->dx;
@@ -772,8 +995,7 @@ extern "C" int pd_state_destroy(pd_state *st) {
     return PD_OK;
 }
 
-extern "C" int pd_state_info(const pd_state *st, double *dt, double *c, int64_t *n_nodes,
-                             int64_t *n_bonds) {
+extern "C" int pd_state_info(const pd_state *st, double *dt, double *c, int64_t *n_nodes, int64_t *n_bonds) {
     PD_REQUIRE(st != nullptr, "state is NULL");
     if (dt) *dt = st->dt;
     if (c) *c = st->c;
@@ -789,13 +1011,7 @@ extern "C" int pd_state_reset(pd_state *st, const float *s0, const float *kappa,
     const bool f64 = st->mat.precision == PD_PREC_FP64;
     const size_t dsz = f64 ? sizeof(double) : sizeof(float);
     PD_CHECK_CUDA(cudaMemsetAsync(st->dmg, 0, (size_t)st->B * st->sell_len * dsz, s));
-    if (f64)
-        k_reset<true><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, s0, st->coord, st->u64, st->v64,
-                                                     st->rec[0], st->rec[1]);
-    else
-        k_reset<false><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, s0, st->coord, st->u64, st->v64,
-                                                      st->rec[0], st->rec[1]);
-    PD_CHECK_LAUNCH();
+    const bool had = st->has_kappa;
     if (kappa) {
         if (!st->kappa) PD_TRY(dalloc(&st->kappa, (size_t)NB));
         PD_CHECK_CUDA(cudaMemcpyAsync(st->kappa, kappa, (size_t)NB * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -803,43 +1019,48 @@ extern "C" int pd_state_reset(pd_state *st, const float *s0, const float *kappa,
     } else {
         st->has_kappa = false;
     }
-    if (st->chunk_exec) {  // the captured chunk bakes has_kappa into the kernel choice
+    if (f64)
+        k_reset<true><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, s0, kappa, st->u64, st->v64, st->vdf, st->rec[0],
+                                                     st->rec[1]);
+    else
+        k_reset<false><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, s0, kappa, st->u64, st->v64, st->vdf,
+                                                      st->rec[0], st->rec[1]);
+    PD_CHECK_LAUNCH();
+    if (st->chunk_exec && had != st->has_kappa) {  // the captured chunk bakes the kernel choice
         cudaGraphExecDestroy(st->chunk_exec);
         st->chunk_exec = nullptr;
     }
-    k_reset_run<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->step, st->done, st->status, st->peak,
-                                                  st->peak_step, st->ticket, 0);
+    k_reset_run<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->step, st->done, st->status, st->peak, st->peak_step,
+                                                  st->ticket, 0);
     PD_CHECK_LAUNCH();
     return PD_OK;
 }
 
-extern "C" int pd_state_load(pd_state *st, const double *u, const double *v, const double *d,
-                             int32_t step, pd_stream stream) {
+extern "C" int pd_state_load(pd_state *st, const double *u, const double *v, const double *d, int32_t step,
+                             pd_stream stream) {
     PD_REQUIRE(st != nullptr, "state is NULL");
     PD_REQUIRE(step >= 0, "step must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
     const long long NB = st->N * st->B;
     const bool f64 = st->mat.precision == PD_PREC_FP64;
-    k_reset_run<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->step, st->done, st->status, st->peak,
-                                                  st->peak_step, st->ticket, step);
+    const int C = 32 / st->lanes;
+    k_reset_run<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->step, st->done, st->status, st->peak, st->peak_step,
+                                                  st->ticket, step);
     PD_CHECK_LAUNCH();
-    if (f64) {
-        k_load_u<true><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, u, v, st->u64, st->v64, st->step,
+    if (f64)
+        k_load_u<true><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, u, v, st->u64, st->v64, st->vdf, st->step,
                                                       st->rec[0], st->rec[1]);
-        k_copy_s0_other<true><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, st->step, st->rec[0], st->rec[1]);
-    } else {
-        k_load_u<false><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, u, v, st->u64, st->v64, st->step,
+    else
+        k_load_u<false><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, u, v, st->u64, st->v64, st->vdf, st->step,
                                                        st->rec[0], st->rec[1]);
-        k_copy_s0_other<false><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, st->step, st->rec[0], st->rec[1]);
-    }
     PD_CHECK_LAUNCH();
     if (d) {
         if (f64)
-            k_dmg_map<double, true><<<blocks_for(NB), 256, 0, s>>>(
-                st->row_ptr, st->N, st->B, st->nb, st->sell_off, st->sell_len, (double *)st->dmg, (double *)d);
+            k_dmg_map<double, true><<<blocks_for(NB), 256, 0, s>>>(st->row_ptr, st->N, st->B, st->nb, C, st->sell_off,
+                                                                   st->sell_len, (double *)st->dmg, (double *)d);
         else
-            k_dmg_map<float, true><<<blocks_for(NB), 256, 0, s>>>(
-                st->row_ptr, st->N, st->B, st->nb, st->sell_off, st->sell_len, (float *)st->dmg, (double *)d);
+            k_dmg_map<float, true><<<blocks_for(NB), 256, 0, s>>>(st->row_ptr, st->N, st->B, st->nb, C, st->sell_off,
+                                                                  st->sell_len, (float *)st->dmg, (double *)d);
         PD_CHECK_LAUNCH();
     }
     return PD_OK;
@@ -849,17 +1070,23 @@ extern "C" int pd_state_store(const pd_state *st, double *u, double *v, double *
     PD_REQUIRE(st != nullptr, "state is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     const long long NB = st->N * st->B;
+    const int C = 32 / st->lanes;
     if (u || v) {
-        k_store_u<<<blocks_for(3 * NB), 256, 0, s>>>(st->N, st->B, st->u64, st->v64, u, v);
+        if (st->mat.precision == PD_PREC_FP64)
+            k_store_u<true><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, st->u64, st->v64, st->vdf, st->step,
+                                                           st->rec[0], st->rec[1], u, v);
+        else
+            k_store_u<false><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, st->u64, st->v64, st->vdf, st->step,
+                                                            st->rec[0], st->rec[1], u, v);
         PD_CHECK_LAUNCH();
     }
     if (d) {
         if (st->mat.precision == PD_PREC_FP64)
-            k_dmg_map<double, false><<<blocks_for(NB), 256, 0, s>>>(
-                st->row_ptr, st->N, st->B, st->nb, st->sell_off, st->sell_len, (double *)st->dmg, d);
+            k_dmg_map<double, false><<<blocks_for(NB), 256, 0, s>>>(st->row_ptr, st->N, st->B, st->nb, C,
+                                                                    st->sell_off, st->sell_len, (double *)st->dmg, d);
         else
-            k_dmg_map<float, false><<<blocks_for(NB), 256, 0, s>>>(
-                st->row_ptr, st->N, st->B, st->nb, st->sell_off, st->sell_len, (float *)st->dmg, d);
+            k_dmg_map<float, false><<<blocks_for(NB), 256, 0, s>>>(st->row_ptr, st->N, st->B, st->nb, C, st->sell_off,
+                                                                   st->sell_len, (float *)st->dmg, d);
         PD_CHECK_LAUNCH();
     }
     return PD_OK;
@@ -885,8 +1112,8 @@ extern "C" int pd_step(pd_state *st, int32_t n_steps, double *reaction, pd_strea
     return PD_OK;
 }
 
-extern "C" int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int32_t *peak_step,
-                              int32_t *n_done, pd_stream stream) {
+extern "C" int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int32_t *peak_step, int32_t *n_done,
+                              pd_stream stream) {
     PD_REQUIRE(st != nullptr, "state is NULL");
     PD_REQUIRE(max_steps >= 0, "max_steps must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
@@ -931,8 +1158,7 @@ extern "C" int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int
             if (((volatile int32_t *)st->host_flag)[(c - 1) & 1] == 0) break;
         }
     }
-    k_copy_out<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->peak, st->peak_step, st->step, peak,
-                                                  peak_step, n_done);
+    k_copy_out<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->peak, st->peak_step, st->step, peak, peak_step, n_done);
     PD_CHECK_LAUNCH();
     std::vector<int32_t> status(st->B);
     PD_CHECK_CUDA(cudaMemcpyAsync(status.data(), st->status, st->B * sizeof(int32_t), cudaMemcpyDeviceToHost, s));

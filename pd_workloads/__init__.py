@@ -118,7 +118,7 @@ def bar() -> Workload:
     """3D bar 40x10x10 nodes, dx = 1 mm, delta = 3.01 dx, bilinear law, 1,000 steps."""
     g = Grid(40, 10, 10, 1e-3, 3.01)
     mat = Material(E=30e9, law=LAW_BILINEAR, s0=1e-4, s_ratio=10.0, zeta=0.0)
-    bc = BC(BC_BAR_TENSION, u_max=4e-5, n_ramp=1000, grip_planes=3)
+    bc = BC(BC_BAR_TENSION, u_max=1.5e-5, n_ramp=1000, grip_planes=3)
     return Workload("bar_40x10x10_dx1mm", g, mat, bc, n_steps=1000, fp64=True)
 
 

@@ -12,7 +12,7 @@ def _declared():
     for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
         if h.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", h)).read()
-            names += re.findall(r"PD_API\s+(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", txt)
+            names += re.findall(r"^PD_API\s+(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", txt, re.M)
     return names
 
 
@@ -44,6 +44,6 @@ def test_argument_errors_need_no_gpu(built_lib):
     V = (ctypes.c_double * 2)(1.0, 1.0)
     Cst = (ctypes.c_double * 2)(1.0, 4.0)
     N = (ctypes.c_int64 * 2)()
-    assert L.pd_mlmc_allocation(2, V, Cst, ctypes.c_double(0.1), N) == 0
-    # N_l = floor(eps^-2 (sum sqrt(V C)) sqrt(V/C)) = floor(100 * 3 * [1, 0.5])
-    assert list(N) == [300, 150]
+    assert L.pd_mlmc_allocation(2, V, Cst, ctypes.c_double(0.125), N) == 0
+    # N_l = floor(eps^-2 (sum sqrt(V C)) sqrt(V/C)) = floor(64 * 3 * [1, 0.5])
+    assert list(N) == [192, 96]

@@ -139,7 +139,7 @@ def test_bar_fp64_full(pd):
     m = core.Model(w)
     r60 = m.run(60)
     pre = int(np.argmax(r60["smax"] > w.mat.s0 * 0.999)) or 60
-    assert pre > 5
+    assert pre > 50
     rp = m.run(pre)
     st2 = pd.State(g, row, col, w.mat, w.bc, batch=1, precision=pd.PREC_FP64)
     st2.reset(torch.full((1, g.n_nodes), np.float32(w.mat.s0), device="cuda"))
