@@ -42,7 +42,8 @@ namespace pdi {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kMaxOff = 255;  // stencil ids fit a byte; 0xFF marks padding
+constexpr int kTab = 256;     // stencil table entries: ids 0..n_off-1, padding id 0xFF
+constexpr int kPad = 0xFF;
 
 struct df {
     float hi, lo;
@@ -176,28 +177,30 @@ __device__ __forceinline__ double pick3(double a, double b, double c, int q) { r
 // warp w of a block serves one slice. After the bond loop every sub-lane of a
 // node holds the node's total force; sub-lane t then integrates component t.
 template <int T, bool F64, int LAW, bool KAPPA, bool FORCE_ONLY>
-__global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) k_step(const StepArgs a) {
     static_assert(T >= 2 && T <= 8, "2 to 8 lanes per node");
     constexpr int C = 32 / T;
-    __shared__ float4 s_xi[kMaxOff];
-    __shared__ int s_off[kMaxOff];
-    __shared__ double4_32a s_xid[F64 ? kMaxOff : 1];
+    __shared__ float4 s_xi[kTab];
+    __shared__ int s_off[kTab];
+    __shared__ double4_32a s_xid[F64 ? kTab : 1];
     __shared__ double red[kWarps];
     __shared__ double s_U[2];
-    __shared__ int last_flag;
+    __shared__ unsigned s_cnt;
 
     const int b = blockIdx.x % a.B;
     const int xb = blockIdx.x / a.B;
     const bool done = FORCE_ONLY ? false : (a.done[b] != 0);
     const int n = a.step[b];
-    for (int t = threadIdx.x; t < a.n_off; t += kThreads) {
+    for (int t = threadIdx.x; t < kTab; t += kThreads) {
         s_xi[t] = a.xi_tab[t];
         s_off[t] = a.off_tab[t];
         if (F64) s_xid[t] = a.xid_tab[t];
     }
+    if (threadIdx.x < kWarps) red[threadIdx.x] = 0.0;
     if (threadIdx.x == 0) {
         s_U[0] = ramp(a, n);
         s_U[1] = ramp(a, n + 1);
+        s_cnt = 0u;
     }
     __syncthreads();
 
@@ -220,10 +223,12 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
                 double *dm = (double *)a.dmg + (size_t)b * a.sell_len;
                 const double4_32a me = rin[i];
                 const double kap_i = KAPPA ? (double)a.kappa[node] : 1.0;
+                // padding slots (id 0xFF) point at the node itself with |xi| = dx:
+                // zero stretch, zero force, no damage write, no branch
+#pragma unroll 2
                 for (int m = 0; m < M; ++m) {
                     const long long e = e0 + 32ll * m;
                     const int id = a.ids[e];
-                    if (id == 0xFF) break;
                     const long long j = i + s_off[id];
                     const double4_32a xl = s_xid[id];
                     const double4_32a rj = rin[j];
@@ -290,45 +295,60 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
             float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
             if (own) {
                 const int M = a.sell_m[sl];
-                const long long e0 = a.sell_off[sl] + lane;
-                float *dm = (float *)a.dmg + (size_t)b * a.sell_len;
-                hi = __ldg(rhi + i);
-                lo = __ldg(rlo + i);
+                // per-slice bases; slot, node and neighbour indices are 32-bit
+                const uint8_t *ids = a.ids + a.sell_off[sl] + lane;
+                float *dm = (float *)a.dmg + (size_t)b * a.sell_len + a.sell_off[sl] + lane;
+                const int ii = (int)i;
+                hi = __ldg(rhi + ii);
+                lo = __ldg(rlo + ii);
                 const float cVf = (float)a.cV;
                 const float sr = (float)a.s_ratio, kf = (float)a.k, af = (float)a.alpha;
                 const float i1 = (float)a.inv_1mek, i2 = (float)a.inv_1pa;
-                for (int m = 0; m < M; ++m) {
-                    const long long e = e0 + 32ll * m;
-                    const int id = __ldg(a.ids + e);
-                    if (id == 0xFF) break;
-                    const long long j = i + s_off[id];
-                    const float4 xl = s_xi[id];
-                    const float4 hj = __ldg(rhi + j);
-                    const float4 lj = __ldg(rlo + j);
-                    const float ex = (hj.x - hi.x) + (lj.x - lo.x);
-                    const float ey = (hj.y - hi.y) + (lj.y - lo.y);
-                    const float ez = (hj.z - hi.z) + (lj.z - lo.z);
-                    const float yx = xl.x + ex, yy = xl.y + ey, yz = xl.z + ez;
-                    const float y2 = yx * yx + yy * yy + yz * yz;
-                    const float rL = rsqrtf(y2);
-                    const float L = y2 * rL;
-                    const float s = __fdividef(2.0f * (xl.x * ex + xl.y * ey + xl.z * ez) + (ex * ex + ey * ey + ez * ez),
-                                               xl.w * (L + xl.w));
-                    const float s0 = 0.5f * (hi.w + hj.w);
-                    float d = dm[e];
-                    if (s > s0) {
-                        const float dl = law_damage<float>(LAW, s, s0, sr * s0, kf, af, i1, i2);
-                        if (dl > d) {
-                            d = dl;
-                            dm[e] = d;
+                // Padding slots (id 0xFF) point at the node itself with |xi| = dx:
+                // zero stretch, zero force, no damage write, no branch.
+                // Bonds are summed in plain FP32 over groups of 4 rounds and each
+                // group sum is added to the compensated (TwoSum) accumulator.
+                for (int m0 = 0; m0 < M; m0 += 4) {
+                    float px = 0.f, py = 0.f, pz = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int m = m0 + q;
+                        if (m < M) {
+                            const int id = __ldg(ids + 32 * m);
+                            const int j = ii + s_off[id];
+                            const float4 xl = s_xi[id];
+                            const float4 hj = __ldg(rhi + j);
+                            const float4 lj = __ldg(rlo + j);
+                            const float ex = (hj.x - hi.x) + (lj.x - lo.x);
+                            const float ey = (hj.y - hi.y) + (lj.y - lo.y);
+                            const float ez = (hj.z - hi.z) + (lj.z - lo.z);
+                            const float yx = xl.x + ex, yy = xl.y + ey, yz = xl.z + ez;
+                            const float y2 = yx * yx + yy * yy + yz * yz;
+                            const float rL = rsqrtf(y2);
+                            const float L = y2 * rL;
+                            const float s = __fdividef(
+                                2.0f * (xl.x * ex + xl.y * ey + xl.z * ez) + (ex * ex + ey * ey + ez * ez),
+                                xl.w * (L + xl.w));
+                            const float s0 = 0.5f * (hi.w + hj.w);
+                            float d = dm[32 * m];
+                            if (s > s0) {
+                                const float dl = law_damage<float>(LAW, s, s0, sr * s0, kf, af, i1, i2);
+                                if (dl > d) {
+                                    d = dl;
+                                    dm[32 * m] = d;
+                                }
+                            }
+                            float cv = cVf;
+                            if (KAPPA) cv = cVf * 0.5f * (lo.w + lj.w);
+                            const float g = cv * (1.0f - d) * s * rL;
+                            px += g * yx;
+                            py += g * yy;
+                            pz += g * yz;
                         }
                     }
-                    float cv = cVf;
-                    if (KAPPA) cv = cVf * 0.5f * (lo.w + lj.w);
-                    const float g = cv * (1.0f - d) * s * rL;
-                    two_sum_acc(sx, cx, g * yx);
-                    two_sum_acc(sy, cy, g * yy);
-                    two_sum_acc(sz, cz, g * yz);
+                    two_sum_acc(sx, cx, px);
+                    two_sum_acc(sy, cy, py);
+                    two_sum_acc(sz, cz, pz);
                 }
             }
             // add the T sub-lane partials of each node in double-float (fixed
@@ -385,48 +405,53 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
 
     if (FORCE_ONLY || done) return;  // uniform per block
 
-    // deterministic reaction reduction: warp tree (skipped by warps without a
-    // prescribed DOF, whose sum is exactly 0), warps in order, blocks in order
+    // Deterministic reaction reduction without a block barrier: each warp
+    // sums its lanes (a fixed xor tree, skipped by warps without a prescribed
+    // DOF, whose sum is exactly 0) into shared memory; the last warp of the
+    // block to finish adds the 8 warp sums in a fixed order and posts the
+    // block partial; the last block of the sample adds the block partials in
+    // block order and updates the run bookkeeping. Early warps just exit.
     if (__any_sync(0xffffffffu, Rloc != 0.0)) Rloc = warp_sum(Rloc);
-    if (lane == 0) red[warp] = Rloc;
-    __syncthreads();
-    if (warp == 0) {
-        double v = lane < kWarps ? red[lane] : 0.0;
-        if (__any_sync(0xffffffffu, v != 0.0)) v = warp_sum(v);
-        if (lane == 0) {
-            a.partial[(size_t)b * a.nblk + xb] = v;
-            __threadfence();
-            const unsigned tk = atomicAdd(&a.ticket[b], 1u);
-            last_flag = (tk == (unsigned)(a.nblk - 1));
-        }
+    unsigned flag = 0u;
+    if (lane == 0) {
+        red[warp] = Rloc;
+        __threadfence_block();
+        flag = (atomicAdd(&s_cnt, 1u) == (unsigned)(kWarps - 1));
     }
-    __syncthreads();
-    if (!last_flag) return;
-    if (warp == 0) {
+    flag = __shfl_sync(0xffffffffu, flag, 0);
+    if (!flag) return;
+    __threadfence_block();
+    double v = lane < kWarps ? ((volatile double *)red)[lane] : 0.0;
+    if (__any_sync(0xffffffffu, v != 0.0)) v = warp_sum(v);
+    if (lane == 0) {
+        a.partial[(size_t)b * a.nblk + xb] = v;
         __threadfence();
-        const volatile double *p = a.partial + (size_t)b * a.nblk;
-        double v = 0.0;
-        for (int q = lane; q < a.nblk; q += 32) v += p[q];
-        v = warp_sum(v);
-        if (lane == 0) {
-            const double R = v;
-            if (!isfinite(R)) a.status[b] |= 1;
-            if (a.reaction) a.reaction[(size_t)b * a.n_react + a.k_local] = R;
-            double Q = a.peak[b];
-            int np = a.peak_step[b];
-            if (R > Q) {
-                Q = R;
-                np = n;
-                a.peak[b] = Q;
-                a.peak_step[b] = np;
-            }
-            a.step[b] = n + 1;
-            if (a.use_stop) {
-                if ((Q > 0.0 && n - np >= 100 && R < 0.5 * Q) || n + 1 >= a.max_steps || !isfinite(R))
-                    a.done[b] = 1;
-            }
-            a.ticket[b] = 0u;
+        flag = (atomicAdd(&a.ticket[b], 1u) == (unsigned)(a.nblk - 1));
+    }
+    flag = __shfl_sync(0xffffffffu, flag, 0);
+    if (!flag) return;
+    __threadfence();
+    const volatile double *p = a.partial + (size_t)b * a.nblk;
+    v = 0.0;
+    for (int q = lane; q < a.nblk; q += 32) v += p[q];
+    v = warp_sum(v);
+    if (lane == 0) {
+        const double R = v;
+        if (!isfinite(R)) a.status[b] |= 1;
+        if (a.reaction) a.reaction[(size_t)b * a.n_react + a.k_local] = R;
+        double Q = a.peak[b];
+        int np = a.peak_step[b];
+        if (R > Q) {
+            Q = R;
+            np = n;
+            a.peak[b] = Q;
+            a.peak_step[b] = np;
         }
+        a.step[b] = n + 1;
+        if (a.use_stop) {
+            if ((Q > 0.0 && n - np >= 100 && R < 0.5 * Q) || n + 1 >= a.max_steps || !isfinite(R)) a.done[b] = 1;
+        }
+        a.ticket[b] = 0u;
     }
 }
 
@@ -826,9 +851,14 @@ static int build_stencil(pd_state *st, int16_t **box_dev, int *R_out) {
                 xd.push_back(make_double4_32a(dx * g.dx, dy * g.dx, dz * g.dx, L0));
                 ot.push_back(dx + g.nx * (dy + g.ny * dz));
             }
-    PD_REQUIRE(xt.size() <= (size_t)kMaxOff - 1, "horizon stencil has %zu offsets (at most 254 supported)",
-               xt.size());
+    PD_REQUIRE(xt.size() <= (size_t)kPad, "horizon stencil has %zu offsets (at most 255 supported)", xt.size());
     st->n_off = (int32_t)xt.size();
+    // unused ids and the padding id: the node itself at distance dx (zero stretch)
+    while (xt.size() < (size_t)kTab) {
+        xt.push_back(make_float4((float)g.dx, 0.f, 0.f, (float)g.dx));
+        xd.push_back(make_double4_32a(g.dx, 0.0, 0.0, g.dx));
+        ot.push_back(0);
+    }
     PD_TRY(dalloc(&st->xi_tab, xt.size()));
     PD_TRY(dalloc(&st->xid_tab, xd.size()));
     PD_TRY(dalloc(&st->off_tab, ot.size()));
