@@ -1,0 +1,324 @@
+#!/usr/bin/env python3
+"""Benchmark of the probabilistic peridynamic hot path on GB300.
+
+One bench step = one pass of the whole per-sample hot path over one batch of
+synthetic input: KL coefficients drawn from (seed, sample id) (Philox), the
+truncated-KL strength field (a2), the explicit bond-based steps run to the
+peak-load stop rule (a3-a7: kinematics, softening law with irreversible
+damage, nodal sums, damped leapfrog under displacement control, FP64
+reaction), and the level sums of the estimator (a8). The neighbour list (a1)
+is built once per mesh before timing.
+
+Workload (N = 1): the notched three-point-bending beam 175 x 50 x 50 mm at
+dx = 2.5 mm (28,000 nodes, 2,975,344 directed bonds), one random lognormal
+strength sample per step (mean 1e-4, COV 0.1, squared-exponential covariance,
+l = 10 mm, 64 KL modes), FP32 bond arithmetic with compensated / double-float
+sums, up to 5,000 steps. Metric: bond-updates/s = sum over samples of
+(steps executed x directed bonds) / device time. Under torchrun each rank
+runs its own samples (ids offset by rank): weak scaling, no data-path
+collective.
+
+--impl reference times the FP64 CPU oracle on the same workload (a bounded
+sample of explicit steps per bench step) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "bond-updates/s"
+WORKLOAD = ("notched 3-point-bending beam 175x50x50 mm, dx 2.5 mm (28,000 nodes, 2,975,344 directed bonds), "
+            "lognormal KL strength field (64 modes, l = 10 mm), one sample per step, run to peak (<= 5,000 steps)")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline_leg(n_steps: int = 300):
+    """The FP64 oracle as it stands, on the same beam and field recipe, for a
+    bounded number of explicit steps on one host core."""
+    import pd_workloads as W
+    from oracle import core, field
+    w = W.beam()
+    Phi, lam = field.kl_separable(w.grid, w.field.length, w.field.n_modes)
+    s0 = field.sample_field(w, Phi, lam, w.seed, 0, [0])[0]
+    m = core.Model(w, s0=s0)
+    t0 = time.perf_counter()
+    r = m.run(n_steps)
+    el = time.perf_counter() - t0
+    bu = r["n_done"] * m.nb
+    return {"value": bu / el, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"first {n_steps} explicit steps of sample 0 (seed {w.seed}) of the {w.grid.nx}x{w.grid.ny}x"
+                      f"{w.grid.nz} notched beam, FP64, single thread ({el:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import pd_workloads as W
+    from oracle import core, field
+    w = W.beam()
+    Phi, lam = field.kl_separable(w.grid, w.field.length, w.field.n_modes)
+    per_step = 40
+    total_bu, total_t = 0, 0.0
+    for k in range(args.warmup + args.steps):
+        s0 = field.sample_field(w, Phi, lam, w.seed, 0, [k])[0]
+        m = core.Model(w, s0=s0)
+        t0 = time.perf_counter()
+        r = m.run(per_step)
+        el = time.perf_counter() - t0
+        if k >= args.warmup:
+            total_bu += r["n_done"] * m.nb
+            total_t += el
+    val = total_bu / total_t
+    line = {"metric": METRIC, "value": val, "unit": METRIC, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": f"{per_step} explicit steps of each sample"},
+            "cpu_baseline": {"value": val, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} explicit steps per bench step, FP64 oracle, one thread"},
+            "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--batched", type=int, default=32, help="samples per launch for the batched comparison (0: skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2212_04415_gb300 as pd
+    import pd_workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+
+    w = W.beam()
+    g = w.grid
+    row, col = pd.build_neighbours(g)
+    nb = int(col.numel())
+    fld = pd.Field(g, 1, w.field)
+    st = pd.State(g, row, col, w.mat, w.bc, batch=1, precision=pd.PREC_MIXED)
+    K = w.field.n_modes
+    xi = torch.empty((1, K), dtype=torch.float64, device="cuda")
+    s0 = torch.empty((1, g.n_nodes), dtype=torch.float32, device="cuda")
+    ids = torch.empty(1, dtype=torch.int64, device="cuda")
+    outs = (torch.empty(1, dtype=torch.float64, device="cuda"), torch.empty(1, dtype=torch.int32, device="cuda"),
+            torch.empty(1, dtype=torch.int32, device="cuda"))
+    qsum = torch.zeros(2, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def one(sample_id):
+        ids.fill_(sample_id)
+        pd.draw_xi(w.seed, 0, ids, K, out=xi)
+        fld.sample(0, xi, out=(s0,))
+        st.reset(s0)
+        st.run_to_peak(w.n_steps, out=outs)
+        qsum[0] += outs[0][0]          # level sums of the estimator (one sample, level 0)
+        qsum[1] += outs[0][0] * outs[0][0]
+
+    base = rank * 1_000_000
+    for k in range(args.warmup):
+        one(base + 10_000 + k)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    nd_list = []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))                      # L2 flush between timed steps (outside the events)
+        ev[k][0].record(stream)
+        one(base + k)
+        ev[k][1].record(stream)
+        nd_list.append(int(outs[2].item()))
+    torch.cuda.synchronize()
+    nd_tot = sum(nd_list)
+    clk = clocks.stop()
+    dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    units = float(nd_tot) * nb
+    t_max = dev_s
+    if dist:
+        t = torch.tensor([dev_s, units], dtype=torch.float64, device="cuda")
+        tm = t.clone()
+        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        t_max, units = float(tm[0]), float(t[1])
+    value = units / t_max
+    per_launch_ms = 1e3 * dev_s / max(nd_tot, 1)  # run_to_peak time per explicit step (graph replays)
+
+    # end to end through the public API with host buffers: H2D of the step's
+    # inputs (sample id) from pinned memory, D2H of the result (peak, step, n)
+    h_ids = torch.empty(1, dtype=torch.int64).pin_memory()
+    h_out = torch.empty(2, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_units = 0
+    for k in range(args.steps):
+        h_ids.fill_(base + 500_000 + k)
+        ids.copy_(h_ids, non_blocking=True)
+        pd.draw_xi(w.seed, 0, ids, K, out=xi)
+        fld.sample(0, xi, out=(s0,))
+        st.reset(s0)
+        st.run_to_peak(w.n_steps, out=outs)
+        h_out[0:1].copy_(outs[0], non_blocking=True)
+        h_out[1:2].copy_(outs[2].to(torch.float64), non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_units += int(h_out[1].item()) * nb
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": e2e_units / e2e_s, "unit": METRIC, "h2d_bytes_per_step": 8, "d2h_bytes_per_step": 16}
+
+    # batched comparison: the same beam, many samples in one launch
+    batched = None
+    if args.batched > 0:
+        Bb = args.batched
+        stb = pd.State(g, row, col, w.mat, w.bc, batch=Bb, precision=pd.PREC_MIXED)
+        idb = torch.arange(Bb, dtype=torch.int64, device="cuda") + base + 200_000
+        xib = pd.draw_xi(w.seed, 0, idb, K)
+        s0b = fld.sample(0, xib)
+        stb.reset(s0b)
+        stb.run_to_peak(w.n_steps)
+        stb.reset(s0b)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, ndb = stb.run_to_peak(w.n_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bs = e0.elapsed_time(e1) / 1e3
+        bu = float(ndb.sum().item()) * nb
+        batched = {"samples_per_launch": Bb, "value": bu / bs, "unit": METRIC, "samples_per_s": Bb / bs,
+                   "plain_samples_per_s": args.steps / dev_s, "ms": 1e3 * bs}
+        stb.close()
+
+    hbm, peak_kind = _peaks()
+    alg_bytes = nb * (4.0 + 4.0) + g.n_nodes * 108.0  # per launch, one sample (index + history, node state)
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    # our kernels per bench step: draw_xi, sample, reset (2), run init, copy-out,
+    # and graph chunks of 64 steps + 1 poll kernel (one chunk beyond the stop)
+    launches = sum(6 + 65 * (int(np.ceil(n / 64.0)) + 1) for n in nd_list)
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "samples_per_step": 1, "mean_explicit_steps": nd_tot / args.steps,
+                   "l2": "flushed between timed steps (256 MB write outside the events)",
+                   "precision": "FP32 bond arithmetic; compensated FP32 / double-float nodal sums and integration; "
+                                "FP64 reaction and estimator sums",
+                   "mesh": "neighbour list built once before timing"},
+        "samples_per_s": ws * args.steps / t_max,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "peak_kind": peak_kind, "kernel": "k_step",
+                     "algorithmic_bytes_per_launch": alg_bytes, "launch_us": per_launch_ms * 1e3},
+        "batched": batched,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_leg()
+    if rank == 0:
+        print(json.dumps(line))
+    st.close()
+    fld.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
