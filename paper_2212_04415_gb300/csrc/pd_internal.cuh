@@ -76,18 +76,24 @@ struct pd_state {
     int64_t N;
     int64_t nb;
     double dt, c, V;
-    // neighbour list: CSR copy and a SELL-C layout of stencil ids
+    // neighbour list: CSR copy and a brick-ordered SELL-8 layout of stencil ids
     int32_t *row_ptr;
-    int32_t lanes;          // T lanes per node; C = 32 / T nodes per slice
-    int64_t n_slices;
+    int32_t by, bz;         // brick = 8 x by x bz nodes; one slice = 8 x-consecutive nodes
+    int32_t nbx, nby, nbz;  // bricks per axis
+    int32_t halo;           // largest stencil offset component
+    int64_t n_bricks;
+    int64_t n_slices;       // n_bricks * by * bz (rows outside the grid are empty slices)
     int64_t sell_len;
     long long *sell_off;    // [n_slices]: first element of each slice
-    int32_t *sell_m;        // [n_slices]: 32-wide rounds per slice (slots / T)
+    int32_t *sell_m;        // [n_slices]: 32-wide rounds per slice (slots / 4)
+    int32_t *slice_i0;      // [n_slices]: node of lane 0
+    int32_t *slice_nv;      // [n_slices]: valid lanes (0..8)
     uint8_t *ids;           // [sell_len]: stencil id of each slot, 0xFF = padding
     int32_t n_off;          // stencil size
-    float4 *xi_tab;         // [n_off]: xi (x, y, z) and |xi| in FP32
-    double4_32a *xid_tab;       // [n_off]: the same in FP64
-    int32_t *off_tab;       // [n_off]: linear index offset j - i
+    float4 *xi_tab;         // [256]: xi (x, y, z) and |xi| in FP32
+    double4_32a *xid_tab;   // [256]: the same in FP64
+    int32_t *off_tab;       // [256]: neighbour offset (fp64 path: global j - i; mixed: brick-local)
+    size_t smem_bytes;      // staged brick records (mixed path)
     // per-sample state
     void *dmg;          // float or double [B][sell_len]
     double *u64;        // fp64 path: [B][N][3]

@@ -5,33 +5,41 @@
 //
 // Layout (per state; B samples share one mesh):
 //   * The grid is regular, so every bond of node i is one of the n_off
-//     stencil offsets (|k|^2 <= m^2): j = i + off[id], xi = dx k. The CSR
-//     neighbour list is stored as one byte per directed bond (the stencil
-//     id), in a SELL-C layout: slices of C = 32 / T consecutive nodes,
-//     slot-major inside a slice, rows padded (0xFF) to a multiple of T slots.
-//     Lane L of a warp serves node c = L % C of the slice and sub-lane
-//     t = L / C, which takes slots t, t + T, t + 2T, ...; round m of the warp
+//     stencil offsets k (|k|^2 <= m^2, xi = dx k). The CSR neighbour list is
+//     stored as one byte per directed bond (the stencil id).
+//   * Nodes are grouped in bricks of 8 x BY x BZ; a slice is the 8
+//     x-consecutive nodes of one brick row. Slots are slot-major inside a
+//     slice (SELL-8) and rows are padded with id 0xFF to a multiple of 4.
+//     A warp serves one slice at a time: lane L takes node c = L % 8 and
+//     sub-lane t = L / 8, i.e. slots t, t + 4, t + 8, ...; round m of the warp
 //     reads the 32 consecutive elements off[s] + 32 m + L (one id byte and one
-//     damage word per lane: fully coalesced).
+//     damage word per lane: coalesced).
 //   * Damage per directed bond in the same order, per sample. Both directed
 //     copies of a bond evolve identically: the stretch, the per-bond
 //     properties and the law are symmetric in (i, j) bit for bit.
 //   * Gather records per node, double-buffered by step parity:
 //       mixed: float4 hi = (u_hi, s0), float4 lo = (u_lo, kappa), u = u_hi + u_lo
 //              (double-float), so u_j - u_i keeps FP64-like accuracy in FP32;
-//       fp64:  double4_32a (u, s0).
+//       fp64:  double4 (u, s0).
+//   * Mixed path: one block per (brick, sample) stages the brick's records
+//     and a halo of the stencil radius in shared memory, so every bond
+//     gathers from shared memory (brick-local stencil offsets); only the id
+//     and damage streams and the owner's update touch global memory.
 //   * velocities: mixed path double-float float4 hi/lo pairs, fp64 path FP64
 //     (the fp64 path also keeps FP64 u next to its records).
 // Arithmetic: GB300 runs FP64 at about 1/64 of the FP32 rate, so the mixed
 // path issues no FP64 instruction per bond or per node. Each lane sums its
-// bonds in compensated FP32 (TwoSum pairs), the T lane partials are added in
-// double-float along a fixed xor tree (TwoSum is exact, so every sub-lane
-// ends with the same total), and sub-lane t integrates component t of its
-// node in double-float arithmetic (about 48 significant bits). FP64 is used
-// for the reaction of prescribed DOFs and its reduction only. The fp64 path
-// does everything in FP64. Order is fixed everywhere, so results are
-// deterministic with no atomics. Blocks are ordered sample-fastest so that the
-// samples of a batch stream the shared stencil ids through L2 together.
+// bonds in FP32 over groups of 4 rounds and adds each group to a compensated
+// (TwoSum) accumulator, the 4 lane partials are added in double-float along a
+// fixed xor tree (TwoSum is exact, so every sub-lane ends with the same
+// total), and sub-lane t integrates component t of its node in double-float
+// arithmetic (about 48 significant bits). FP64 is used for the reaction of
+// prescribed DOFs and its reduction only. The fp64 path does everything in
+// FP64 with global gathers. Order is fixed everywhere, so results are
+// deterministic with no atomics. Blocks are ordered sample-fastest so that
+// the samples of a batch stream the shared stencil ids through L2 together.
+#include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdlib>
 #include <vector>
@@ -42,6 +50,8 @@ namespace pdi {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kLanes = 4;   // sub-lanes per node (T)
+constexpr int kSlice = 8;   // nodes per slice (C = 32 / T)
 constexpr int kTab = 256;     // stencil table entries: ids 0..n_off-1, padding id 0xFF
 constexpr int kPad = 0xFF;
 
@@ -52,10 +62,13 @@ struct df {
 struct StepArgs {
     long long N;
     long long n_slices;
-    int nblk;
+    int nblk;  // bricks per sample
     int B;
+    int nx, ny, nz, BY, BZ, nbx, nby, H, Wx, Wy, Wz;
     const long long *sell_off;
     const int32_t *sell_m;
+    const int32_t *slice_i0;
+    const int32_t *slice_nv;
     const uint8_t *ids;
     const float4 *xi_tab;
     const double4_32a *xid_tab;
@@ -173,13 +186,13 @@ __device__ __forceinline__ float pick3(float a, float b, float c, int q) { retur
 __device__ __forceinline__ double pick3(double a, double b, double c, int q) { return q == 0 ? a : (q == 1 ? b : c); }
 
 // One explicit step (or, with FORCE_ONLY, one force evaluation) of every
-// (sample, node) pair. Grid: ceil(n_slices / 8) * B blocks, sample fastest;
-// warp w of a block serves one slice. After the bond loop every sub-lane of a
-// node holds the node's total force; sub-lane t then integrates component t.
-template <int T, bool F64, int LAW, bool KAPPA, bool FORCE_ONLY>
-__global__ void __launch_bounds__(kThreads, 4) k_step(const StepArgs a) {
-    static_assert(T >= 2 && T <= 8, "2 to 8 lanes per node");
-    constexpr int C = 32 / T;
+// (sample, node) pair. Grid: n_bricks * B blocks, sample fastest; the warps of
+// a block take the brick's slices in turn. After the bond loop every sub-lane
+// of a node holds the node's total force; sub-lane t integrates component t.
+template <bool F64, int LAW, bool KAPPA, bool FORCE_ONLY>
+__global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
+    constexpr int T = kLanes, C = kSlice;
+    extern __shared__ float4 s_rec[];  // mixed: staged hi[Wtot] then lo[Wtot]
     __shared__ float4 s_xi[kTab];
     __shared__ int s_off[kTab];
     __shared__ double4_32a s_xid[F64 ? kTab : 1];
@@ -188,13 +201,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_step(const StepArgs a) {
     __shared__ unsigned s_cnt;
 
     const int b = blockIdx.x % a.B;
-    const int xb = blockIdx.x / a.B;
+    const int brick = blockIdx.x / a.B;
     const bool done = FORCE_ONLY ? false : (a.done[b] != 0);
     const int n = a.step[b];
-    for (int t = threadIdx.x; t < kTab; t += kThreads) {
-        s_xi[t] = a.xi_tab[t];
-        s_off[t] = a.off_tab[t];
-        if (F64) s_xid[t] = a.xid_tab[t];
+    for (int q = threadIdx.x; q < kTab; q += kThreads) {
+        s_xi[q] = a.xi_tab[q];
+        s_off[q] = a.off_tab[q];
+        if (F64) s_xid[q] = a.xid_tab[q];
     }
     if (threadIdx.x < kWarps) red[threadIdx.x] = 0.0;
     if (threadIdx.x == 0) {
@@ -202,202 +215,217 @@ __global__ void __launch_bounds__(kThreads, 4) k_step(const StepArgs a) {
         s_U[1] = ramp(a, n + 1);
         s_cnt = 0u;
     }
+    const int bx = brick % a.nbx, by = (brick / a.nbx) % a.nby, bz = brick / (a.nbx * a.nby);
+    const int x0 = kSlice * bx, y0 = a.BY * by, z0 = a.BZ * bz;
+    const size_t BN = (size_t)a.B * a.N;
+    const int Wtot = a.Wx * a.Wy * a.Wz;
+    float4 *s_hi = s_rec, *s_lo = s_rec + Wtot;
+    if (!F64 && !done) {
+        // stage the brick and its halo (cells outside the grid are never read)
+        const float4 *rhi = (const float4 *)((n & 1) ? a.rec1 : a.rec0) + (size_t)b * a.N;
+        const float4 *rlo = rhi + BN;
+        for (int q = threadIdx.x; q < Wtot; q += kThreads) {
+            const int lx = q % a.Wx, ly = (q / a.Wx) % a.Wy, lz = q / (a.Wx * a.Wy);
+            const int gx = x0 - a.H + lx, gy = y0 - a.H + ly, gz = z0 - a.H + lz;
+            float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+            if (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz) {
+                const int gi = gx + a.nx * (gy + a.ny * gz);
+                h = __ldg(rhi + gi);
+                l = __ldg(rlo + gi);
+            }
+            s_hi[q] = h;
+            s_lo[q] = l;
+        }
+    }
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long sl = (long long)xb * kWarps + warp;
     const int c = lane % C, t = lane / C;
-    const long long i = sl * C + c;
     double Rloc = 0.0;
 
-    if (!done && sl < a.n_slices) {  // warp-uniform
-        const bool own = i < a.N;
-        const size_t node = (size_t)b * a.N + i;
-        const size_t BN = (size_t)a.B * a.N;
-        if (F64) {
-            double Fx = 0.0, Fy = 0.0, Fz = 0.0;
-            const double4_32a *rin = (const double4_32a *)((n & 1) ? a.rec1 : a.rec0) + (size_t)b * a.N;
-            if (own) {
-                const int M = a.sell_m[sl];
-                const long long e0 = a.sell_off[sl] + lane;
-                double *dm = (double *)a.dmg + (size_t)b * a.sell_len;
-                const double4_32a me = rin[i];
-                const double kap_i = KAPPA ? (double)a.kappa[node] : 1.0;
-                // padding slots (id 0xFF) point at the node itself with |xi| = dx:
-                // zero stretch, zero force, no damage write, no branch
-#pragma unroll 2
-                for (int m = 0; m < M; ++m) {
-                    const long long e = e0 + 32ll * m;
-                    const int id = a.ids[e];
-                    const long long j = i + s_off[id];
-                    const double4_32a xl = s_xid[id];
-                    const double4_32a rj = rin[j];
-                    const double ex = rj.x - me.x, ey = rj.y - me.y, ez = rj.z - me.z;
-                    const double yx = xl.x + ex, yy = xl.y + ey, yz = xl.z + ez;
-                    const double L = sqrt(yx * yx + yy * yy + yz * yz);
-                    const double s =
-                        (2.0 * (xl.x * ex + xl.y * ey + xl.z * ez) + (ex * ex + ey * ey + ez * ez)) / (xl.w * (L + xl.w));
-                    const double s0 = 0.5 * (me.w + rj.w);
-                    double d = dm[e];
-                    if (s > s0) {
-                        const double dl =
-                            law_damage<double>(LAW, s, s0, a.s_ratio * s0, a.k, a.alpha, a.inv_1mek, a.inv_1pa);
-                        if (dl > d) {
-                            d = dl;
-                            dm[e] = d;
-                        }
-                    }
-                    double cv = a.cV;
-                    if (KAPPA) cv = a.cV * 0.5 * (kap_i + (double)a.kappa[(size_t)b * a.N + j]);
-                    const double g = cv * (1.0 - d) * s / L;
-                    Fx += g * yx;
-                    Fy += g * yy;
-                    Fz += g * yz;
-                }
-            }
-#pragma unroll
-            for (int o = C; o < 32; o <<= 1) {
-                Fx += __shfl_xor_sync(0xffffffffu, Fx, o);
-                Fy += __shfl_xor_sync(0xffffffffu, Fy, o);
-                Fz += __shfl_xor_sync(0xffffffffu, Fz, o);
-            }
-            if (own) {
-                for (int q = t; q < 3; q += T) {
-                    const double F = pick3(Fx, Fy, Fz, q);
-                    if (FORCE_ONLY) {
-                        a.F_out[3 * node + q] = F;
-                        continue;
-                    }
-                    const uint8_t code = a.codes[3 * i + q];
-                    double uc = a.u64[3 * node + q], vc = a.v64[3 * node + q];
-                    if (code == 0) {
-                        vc = (a.ca * vc + a.dtr * F) * a.icb;
-                        uc = uc + a.dt * vc;
-                    } else if (code == 1) {
-                        uc = 0.0;
-                        vc = 0.0;
-                    } else {
-                        const double sg = code == 2 ? 1.0 : -1.0;
-                        Rloc -= sg * F * a.V;
-                        vc = sg * (s_U[1] - s_U[0]) * a.idt;
-                        uc = sg * s_U[1];
-                    }
-                    a.u64[3 * node + q] = uc;
-                    a.v64[3 * node + q] = vc;
-                    double *ro = (double *)((double4_32a *)((n & 1) ? a.rec0 : a.rec1) + node);
-                    ro[q] = uc;
-                }
-            }
-        } else {
-            const float4 *rhi = (const float4 *)((n & 1) ? a.rec1 : a.rec0) + (size_t)b * a.N;
-            const float4 *rlo = rhi + BN;
-            float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-            float4 hi = make_float4(0.f, 0.f, 0.f, 0.f), lo = hi;
-            if (own) {
-                const int M = a.sell_m[sl];
-                // per-slice bases; slot, node and neighbour indices are 32-bit
-                const uint8_t *ids = a.ids + a.sell_off[sl] + lane;
-                float *dm = (float *)a.dmg + (size_t)b * a.sell_len + a.sell_off[sl] + lane;
-                const int ii = (int)i;
-                hi = __ldg(rhi + ii);
-                lo = __ldg(rlo + ii);
-                const float cVf = (float)a.cV;
-                const float sr = (float)a.s_ratio, kf = (float)a.k, af = (float)a.alpha;
-                const float i1 = (float)a.inv_1mek, i2 = (float)a.inv_1pa;
-                // Padding slots (id 0xFF) point at the node itself with |xi| = dx:
-                // zero stretch, zero force, no damage write, no branch.
-                // Bonds are summed in plain FP32 over groups of 4 rounds and each
-                // group sum is added to the compensated (TwoSum) accumulator.
-                for (int m0 = 0; m0 < M; m0 += 4) {
-                    float px = 0.f, py = 0.f, pz = 0.f;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int m = m0 + q;
-                        if (m < M) {
-                            const int id = __ldg(ids + 32 * m);
-                            const int j = ii + s_off[id];
-                            const float4 xl = s_xi[id];
-                            const float4 hj = __ldg(rhi + j);
-                            const float4 lj = __ldg(rlo + j);
-                            const float ex = (hj.x - hi.x) + (lj.x - lo.x);
-                            const float ey = (hj.y - hi.y) + (lj.y - lo.y);
-                            const float ez = (hj.z - hi.z) + (lj.z - lo.z);
-                            const float yx = xl.x + ex, yy = xl.y + ey, yz = xl.z + ez;
-                            const float y2 = yx * yx + yy * yy + yz * yz;
-                            const float rL = rsqrtf(y2);
-                            const float L = y2 * rL;
-                            const float s = __fdividef(
-                                2.0f * (xl.x * ex + xl.y * ey + xl.z * ez) + (ex * ex + ey * ey + ez * ez),
-                                xl.w * (L + xl.w));
-                            const float s0 = 0.5f * (hi.w + hj.w);
-                            float d = dm[32 * m];
-                            if (s > s0) {
-                                const float dl = law_damage<float>(LAW, s, s0, sr * s0, kf, af, i1, i2);
-                                if (dl > d) {
-                                    d = dl;
-                                    dm[32 * m] = d;
-                                }
+    if (!done) {
+        for (int r = warp; r < a.BY * a.BZ; r += kWarps) {
+            const long long sl = (long long)brick * (a.BY * a.BZ) + r;
+            const int nv = a.slice_nv[sl];
+            if (nv == 0) continue;  // warp-uniform: a brick row outside the grid
+            const bool own = c < nv;
+            const int ii = a.slice_i0[sl] + c;
+            const size_t node = (size_t)b * a.N + ii;
+            const int M = a.sell_m[sl];
+            const uint8_t *ids = a.ids + a.sell_off[sl] + lane;
+            if (F64) {
+                double Fx = 0.0, Fy = 0.0, Fz = 0.0;
+                const double4_32a *rin = (const double4_32a *)((n & 1) ? a.rec1 : a.rec0) + (size_t)b * a.N;
+                if (own) {
+                    double *dm = (double *)a.dmg + (size_t)b * a.sell_len + a.sell_off[sl] + lane;
+                    const double4_32a me = rin[ii];
+                    const double kap_i = KAPPA ? (double)a.kappa[node] : 1.0;
+                    for (int m = 0; m < M; ++m) {
+                        const int id = ids[32 * m];
+                        const int j = ii + s_off[id];
+                        const double4_32a xl = s_xid[id];
+                        const double4_32a rj = rin[j];
+                        const double ex = rj.x - me.x, ey = rj.y - me.y, ez = rj.z - me.z;
+                        const double yx = xl.x + ex, yy = xl.y + ey, yz = xl.z + ez;
+                        const double L = sqrt(yx * yx + yy * yy + yz * yz);
+                        const double s = (2.0 * (xl.x * ex + xl.y * ey + xl.z * ez) + (ex * ex + ey * ey + ez * ez)) /
+                                         (xl.w * (L + xl.w));
+                        const double s0 = 0.5 * (me.w + rj.w);
+                        double d = dm[32 * m];
+                        if (s > s0) {
+                            const double dl =
+                                law_damage<double>(LAW, s, s0, a.s_ratio * s0, a.k, a.alpha, a.inv_1mek, a.inv_1pa);
+                            if (dl > d) {
+                                d = dl;
+                                dm[32 * m] = d;
                             }
-                            float cv = cVf;
-                            if (KAPPA) cv = cVf * 0.5f * (lo.w + lj.w);
-                            const float g = cv * (1.0f - d) * s * rL;
-                            px += g * yx;
-                            py += g * yy;
-                            pz += g * yz;
                         }
+                        double cv = a.cV;
+                        if (KAPPA) cv = a.cV * 0.5 * (kap_i + (double)a.kappa[(size_t)b * a.N + j]);
+                        const double g = cv * (1.0 - d) * s / L;
+                        Fx += g * yx;
+                        Fy += g * yy;
+                        Fz += g * yz;
                     }
-                    two_sum_acc(sx, cx, px);
-                    two_sum_acc(sy, cy, py);
-                    two_sum_acc(sz, cz, pz);
                 }
-            }
-            // add the T sub-lane partials of each node in double-float (fixed
-            // xor tree; TwoSum is exact, so partners get identical totals)
 #pragma unroll
-            for (int o = C; o < 32; o <<= 1) {
-                const float px = __shfl_xor_sync(0xffffffffu, sx, o), qx = __shfl_xor_sync(0xffffffffu, cx, o);
-                const float py = __shfl_xor_sync(0xffffffffu, sy, o), qy = __shfl_xor_sync(0xffffffffu, cy, o);
-                const float pz = __shfl_xor_sync(0xffffffffu, sz, o), qz = __shfl_xor_sync(0xffffffffu, cz, o);
-                df r = two_sum(sx, px);
-                sx = r.hi;
-                cx = r.lo + (cx + qx);
-                r = two_sum(sy, py);
-                sy = r.hi;
-                cy = r.lo + (cy + qy);
-                r = two_sum(sz, pz);
-                sz = r.hi;
-                cz = r.lo + (cz + qz);
-            }
-            if (own) {
-                for (int q = t; q < 3; q += T) {
-                    const df F = two_sum(pick3(sx, sy, sz, q), pick3(cx, cy, cz, q));
-                    if (FORCE_ONLY) {
-                        a.F_out[3 * node + q] = (double)F.hi + (double)F.lo;
-                        continue;
+                for (int o = C; o < 32; o <<= 1) {
+                    Fx += __shfl_xor_sync(0xffffffffu, Fx, o);
+                    Fy += __shfl_xor_sync(0xffffffffu, Fy, o);
+                    Fz += __shfl_xor_sync(0xffffffffu, Fz, o);
+                }
+                if (own) {
+                    for (int q = t; q < 3; q += T) {
+                        const double F = pick3(Fx, Fy, Fz, q);
+                        if (FORCE_ONLY) {
+                            a.F_out[3 * node + q] = F;
+                            continue;
+                        }
+                        const uint8_t code = a.codes[3 * (size_t)ii + q];
+                        double uc = a.u64[3 * node + q], vc = a.v64[3 * node + q];
+                        if (code == 0) {
+                            vc = (a.ca * vc + a.dtr * F) * a.icb;
+                            uc = uc + a.dt * vc;
+                        } else if (code == 1) {
+                            uc = 0.0;
+                            vc = 0.0;
+                        } else {
+                            const double sg = code == 2 ? 1.0 : -1.0;
+                            Rloc -= sg * F * a.V;
+                            vc = sg * (s_U[1] - s_U[0]) * a.idt;
+                            uc = sg * s_U[1];
+                        }
+                        a.u64[3 * node + q] = uc;
+                        a.v64[3 * node + q] = vc;
+                        double *ro = (double *)((double4_32a *)((n & 1) ? a.rec0 : a.rec1) + node);
+                        ro[q] = uc;
                     }
-                    const uint8_t code = a.codes[3 * i + q];
-                    df u = {pick3(hi.x, hi.y, hi.z, q), pick3(lo.x, lo.y, lo.z, q)};
-                    float *vh = (float *)(a.vdf + node);
-                    float *vl = (float *)(a.vdf + BN + node);
-                    df v = {vh[q], vl[q]};
-                    if (code == 0) {
-                        v = df_mul(df_add(df_mul(a.ca_df, v), df_mul(a.dtr_df, F)), a.icb_df);
-                        u = df_add(u, df_mul(a.dt_df, v));
-                    } else if (code == 1) {
-                        u = {0.f, 0.f};
-                        v = {0.f, 0.f};
-                    } else {
-                        const double sg = code == 2 ? 1.0 : -1.0;
-                        Rloc -= sg * ((double)F.hi + (double)F.lo) * a.V;
-                        v = df_split(sg * (s_U[1] - s_U[0]) * a.idt);
-                        u = df_split(sg * s_U[1]);
+                }
+            } else {
+                float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+                const int ly = r % a.BY, lz = r / a.BY;
+                const int il = (a.H + c) + a.Wx * ((a.H + ly) + a.Wy * (a.H + lz));
+                const float4 hi = s_hi[il], lo = s_lo[il];
+                if (own) {
+                    float *dm = (float *)a.dmg + (size_t)b * a.sell_len + a.sell_off[sl] + lane;
+                    const float cVf = (float)a.cV;
+                    const float sr = (float)a.s_ratio, kf = (float)a.k, af = (float)a.alpha;
+                    const float i1 = (float)a.inv_1mek, i2 = (float)a.inv_1pa;
+                    // Padding slots (id 0xFF) point at the node itself with |xi| = dx:
+                    // zero stretch, zero force, no damage write, no branch.
+                    // Bonds are summed in plain FP32 over groups of 4 rounds and each
+                    // group sum is added to the compensated (TwoSum) accumulator.
+                    for (int m0 = 0; m0 < M; m0 += 4) {
+                        float px = 0.f, py = 0.f, pz = 0.f;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int m = m0 + q;
+                            if (m < M) {
+                                const int id = __ldg(ids + 32 * m);
+                                const int jl = il + s_off[id];
+                                const float4 xl = s_xi[id];
+                                const float4 hj = s_hi[jl];
+                                const float4 lj = s_lo[jl];
+                                const float ex = (hj.x - hi.x) + (lj.x - lo.x);
+                                const float ey = (hj.y - hi.y) + (lj.y - lo.y);
+                                const float ez = (hj.z - hi.z) + (lj.z - lo.z);
+                                const float yx = xl.x + ex, yy = xl.y + ey, yz = xl.z + ez;
+                                const float y2 = yx * yx + yy * yy + yz * yz;
+                                const float rL = rsqrtf(y2);
+                                const float L = y2 * rL;
+                                const float s = __fdividef(
+                                    2.0f * (xl.x * ex + xl.y * ey + xl.z * ez) + (ex * ex + ey * ey + ez * ez),
+                                    xl.w * (L + xl.w));
+                                const float s0 = 0.5f * (hi.w + hj.w);
+                                float d = dm[32 * m];
+                                if (s > s0) {
+                                    const float dl = law_damage<float>(LAW, s, s0, sr * s0, kf, af, i1, i2);
+                                    if (dl > d) {
+                                        d = dl;
+                                        dm[32 * m] = d;
+                                    }
+                                }
+                                float cv = cVf;
+                                if (KAPPA) cv = cVf * 0.5f * (lo.w + lj.w);
+                                const float g = cv * (1.0f - d) * s * rL;
+                                px += g * yx;
+                                py += g * yy;
+                                pz += g * yz;
+                            }
+                        }
+                        two_sum_acc(sx, cx, px);
+                        two_sum_acc(sy, cy, py);
+                        two_sum_acc(sz, cz, pz);
                     }
-                    vh[q] = v.hi;
-                    vl[q] = v.lo;
-                    float *oh = (float *)((float4 *)((n & 1) ? a.rec0 : a.rec1) + node);
-                    float *ol = (float *)((float4 *)((n & 1) ? a.rec0 : a.rec1) + BN + node);
-                    oh[q] = u.hi;
-                    ol[q] = u.lo;
+                }
+                // add the 4 sub-lane partials of each node in double-float (fixed
+                // xor tree; TwoSum is exact, so partners get identical totals)
+#pragma unroll
+                for (int o = C; o < 32; o <<= 1) {
+                    const float px = __shfl_xor_sync(0xffffffffu, sx, o), qx = __shfl_xor_sync(0xffffffffu, cx, o);
+                    const float py = __shfl_xor_sync(0xffffffffu, sy, o), qy = __shfl_xor_sync(0xffffffffu, cy, o);
+                    const float pz = __shfl_xor_sync(0xffffffffu, sz, o), qz = __shfl_xor_sync(0xffffffffu, cz, o);
+                    df rr = two_sum(sx, px);
+                    sx = rr.hi;
+                    cx = rr.lo + (cx + qx);
+                    rr = two_sum(sy, py);
+                    sy = rr.hi;
+                    cy = rr.lo + (cy + qy);
+                    rr = two_sum(sz, pz);
+                    sz = rr.hi;
+                    cz = rr.lo + (cz + qz);
+                }
+                if (own) {
+                    for (int q = t; q < 3; q += T) {
+                        const df F = two_sum(pick3(sx, sy, sz, q), pick3(cx, cy, cz, q));
+                        if (FORCE_ONLY) {
+                            a.F_out[3 * node + q] = (double)F.hi + (double)F.lo;
+                            continue;
+                        }
+                        const uint8_t code = a.codes[3 * (size_t)ii + q];
+                        df u = {pick3(hi.x, hi.y, hi.z, q), pick3(lo.x, lo.y, lo.z, q)};
+                        float *vh = (float *)(a.vdf + node);
+                        float *vl = (float *)(a.vdf + BN + node);
+                        df v = {vh[q], vl[q]};
+                        if (code == 0) {
+                            v = df_mul(df_add(df_mul(a.ca_df, v), df_mul(a.dtr_df, F)), a.icb_df);
+                            u = df_add(u, df_mul(a.dt_df, v));
+                        } else if (code == 1) {
+                            u = {0.f, 0.f};
+                            v = {0.f, 0.f};
+                        } else {
+                            const double sg = code == 2 ? 1.0 : -1.0;
+                            Rloc -= sg * ((double)F.hi + (double)F.lo) * a.V;
+                            v = df_split(sg * (s_U[1] - s_U[0]) * a.idt);
+                            u = df_split(sg * s_U[1]);
+                        }
+                        vh[q] = v.hi;
+                        vl[q] = v.lo;
+                        float *oh = (float *)((float4 *)((n & 1) ? a.rec0 : a.rec1) + node);
+                        float *ol = (float *)((float4 *)((n & 1) ? a.rec0 : a.rec1) + BN + node);
+                        oh[q] = u.hi;
+                        ol[q] = u.lo;
+                    }
                 }
             }
         }
@@ -424,7 +452,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_step(const StepArgs a) {
     double v = lane < kWarps ? ((volatile double *)red)[lane] : 0.0;
     if (__any_sync(0xffffffffu, v != 0.0)) v = warp_sum(v);
     if (lane == 0) {
-        a.partial[(size_t)b * a.nblk + xb] = v;
+        a.partial[(size_t)b * a.nblk + brick] = v;
         __threadfence();
         flag = (atomicAdd(&a.ticket[b], 1u) == (unsigned)(a.nblk - 1));
     }
@@ -457,33 +485,35 @@ __global__ void __launch_bounds__(kThreads, 4) k_step(const StepArgs a) {
 
 // ---------------------------------------------------------------- set-up
 
-// Rounds per slice: ceil(max row length / T).
-__global__ void k_slice_rounds(const int32_t *row_ptr, long long N, long long n_slices, int C, int T, int32_t *m) {
+// Rounds per slice: ceil(max row length / 4).
+__global__ void k_slice_rounds(const int32_t *row_ptr, const int32_t *i0, const int32_t *nv, long long n_slices,
+                               int32_t *m) {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_slices) return;
     int w = 0;
-    for (int l = 0; l < C; ++l) {
-        const long long i = s * C + l;
-        if (i < N) w = max(w, row_ptr[i + 1] - row_ptr[i]);
+    for (int l = 0; l < nv[s]; ++l) {
+        const int i = i0[s] + l;
+        w = max(w, row_ptr[i + 1] - row_ptr[i]);
     }
-    m[s] = (w + T - 1) / T;
+    m[s] = (w + kLanes - 1) / kLanes;
 }
 
 // Stencil id of every slot; flags neighbours that are not stencil offsets.
-__global__ void k_fill_ids(const int32_t *row_ptr, const int32_t *col, const int32_t *coord, long long N,
-                           long long n_slices, int C, int T, const long long *off, const int32_t *m,
+__global__ void k_fill_ids(const int32_t *row_ptr, const int32_t *col, const int32_t *coord, const int32_t *i0,
+                           const int32_t *nv, long long n_slices, const long long *off, const int32_t *m,
                            const int16_t *box, int R, uint8_t *ids, int32_t *bad) {
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n_slices * C) return;
-    const long long s = q / C;
-    const int c = (int)(q % C);
-    const long long i = s * C + c;
-    const int len = i < N ? row_ptr[i + 1] - row_ptr[i] : 0;
-    const int W = T * m[s];
-    const int ci = i < N ? coord[i] : 0;
+    if (q >= n_slices * kSlice) return;
+    const long long s = q / kSlice;
+    const int c = (int)(q % kSlice);
+    const bool valid = c < nv[s];
+    const int i = i0[s] + c;
+    const int len = valid ? row_ptr[i + 1] - row_ptr[i] : 0;
+    const int W = kLanes * m[s];
+    const int ci = valid ? coord[i] : 0;
     const int D = 2 * R + 1;
     for (int k = 0; k < W; ++k) {
-        uint8_t id = 0xFF;
+        uint8_t id = kPad;
         if (k < len) {
             const int cj = coord[col[row_ptr[i] + k]];
             const int dx = (cj & 2047) - (ci & 2047), dy = ((cj >> 11) & 2047) - ((ci >> 11) & 2047),
@@ -492,11 +522,11 @@ __global__ void k_fill_ids(const int32_t *row_ptr, const int32_t *col, const int
             if (abs(dx) <= R && abs(dy) <= R && abs(dz) <= R) v = box[(dz + R) * D * D + (dy + R) * D + (dx + R)];
             if (v < 0) {
                 *bad = 1;
-                v = 0xFF;
+                v = kPad;
             }
             id = (uint8_t)v;
         }
-        ids[off[s] + (long long)k * C + c] = id;
+        ids[off[s] + (long long)k * kSlice + c] = id;
     }
 }
 
@@ -631,19 +661,27 @@ __global__ void k_load_u(long long N, int B, const double *u, const double *v, d
     }
 }
 
+// Slice and lane of node i in the brick layout.
+__device__ __forceinline__ long long slice_of(int i, int nx, int ny, int BY, int BZ, int nbx, int nby, int *lane) {
+    const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+    const long long brick = (ix / kSlice) + (long long)nbx * ((iy / BY) + (long long)nby * (iz / BZ));
+    *lane = ix % kSlice;
+    return brick * (BY * BZ) + (iy % BY) + BY * (iz % BZ);
+}
+
 // CSR-ordered damage <-> SELL-ordered damage.
 template <typename T, bool TO_SELL>
-__global__ void k_dmg_map(const int32_t *row_ptr, long long N, int B, long long nb, int C, const long long *off,
-                          long long sell_len, T *sell, double *csr) {
+__global__ void k_dmg_map(const int32_t *row_ptr, long long N, int B, long long nb, int nx, int ny, int BY, int BZ,
+                          int nbx, int nby, const long long *off, long long sell_len, T *sell, double *csr) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N * B) return;
     const int b = (int)(t / N);
-    const long long i = t % N;
-    const long long s = i / C;
-    const int c = (int)(i % C);
+    const int i = (int)(t % N);
+    int c;
+    const long long s = slice_of(i, nx, ny, BY, BZ, nbx, nby, &c);
     const int r0 = row_ptr[i], len = row_ptr[i + 1] - r0;
     for (int k = 0; k < len; ++k) {
-        const long long e = (long long)b * sell_len + off[s] + (long long)k * C + c;
+        const long long e = (long long)b * sell_len + off[s] + (long long)k * kSlice + c;
         const long long q = (long long)b * nb + r0 + k;
         if (TO_SELL)
             sell[e] = (T)csr[q];
@@ -707,27 +745,17 @@ __global__ void k_copy_out(int B, const double *peak, const int32_t *peak_step, 
 
 typedef void (*StepKernel)(const StepArgs);
 
-template <int T, bool F64, bool FO>
+template <bool F64, bool FO>
 static StepKernel pick_law(int law, bool kappa) {
-    if (law == PD_LAW_BILINEAR) return kappa ? k_step<T, F64, 0, true, FO> : k_step<T, F64, 0, false, FO>;
-    return kappa ? k_step<T, F64, 1, true, FO> : k_step<T, F64, 1, false, FO>;
+    if (law == PD_LAW_BILINEAR) return kappa ? k_step<F64, 0, true, FO> : k_step<F64, 0, false, FO>;
+    return kappa ? k_step<F64, 1, true, FO> : k_step<F64, 1, false, FO>;
 }
 
-template <int T>
-static StepKernel pick_t(const pd_state *st, bool fo) {
+static StepKernel pick(const pd_state *st, bool fo) {
     const bool f64 = st->mat.precision == PD_PREC_FP64;
-    if (f64) return fo ? pick_law<T, true, true>(st->mat.law, st->has_kappa)
-                       : pick_law<T, true, false>(st->mat.law, st->has_kappa);
-    return fo ? pick_law<T, false, true>(st->mat.law, st->has_kappa)
-              : pick_law<T, false, false>(st->mat.law, st->has_kappa);
-}
-
-static StepKernel pick(const pd_state *st, bool force_only) {
-    switch (st->lanes) {
-        case 2: return pick_t<2>(st, force_only);
-        case 8: return pick_t<8>(st, force_only);
-        default: return pick_t<4>(st, force_only);
-    }
+    if (f64) return fo ? pick_law<true, true>(st->mat.law, st->has_kappa)
+                       : pick_law<true, false>(st->mat.law, st->has_kappa);
+    return fo ? pick_law<false, true>(st->mat.law, st->has_kappa) : pick_law<false, false>(st->mat.law, st->has_kappa);
 }
 
 static StepArgs make_args(const pd_state *st) {
@@ -739,6 +767,19 @@ static StepArgs make_args(const pd_state *st) {
     a.B = st->B;
     a.sell_off = st->sell_off;
     a.sell_m = st->sell_m;
+    a.slice_i0 = st->slice_i0;
+    a.slice_nv = st->slice_nv;
+    a.nx = st->g.nx;
+    a.ny = st->g.ny;
+    a.nz = st->g.nz;
+    a.BY = st->by;
+    a.BZ = st->bz;
+    a.nbx = st->nbx;
+    a.nby = st->nby;
+    a.H = st->halo;
+    a.Wx = kSlice + 2 * st->halo;
+    a.Wy = st->by + 2 * st->halo;
+    a.Wz = st->bz + 2 * st->halo;
     a.ids = st->ids;
     a.xi_tab = st->xi_tab;
     a.xid_tab = st->xid_tab;
@@ -788,7 +829,9 @@ static StepArgs make_args(const pd_state *st) {
 static int launch_step(const pd_state *st, const StepArgs &a, bool force_only, cudaStream_t s) {
     StepKernel k = pick(st, force_only);
     const unsigned grid = (unsigned)st->nblk * (unsigned)st->B;
-    k<<<grid, kThreads, 0, s>>>(a);
+    PD_CHECK_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)st->smem_bytes));
+    k<<<grid, kThreads, st->smem_bytes, s>>>(a);
     PD_CHECK_LAUNCH();
     return PD_OK;
 }
@@ -800,6 +843,8 @@ static void free_state(pd_state *st) {
     cudaFree(st->row_ptr);
     cudaFree(st->sell_off);
     cudaFree(st->sell_m);
+    cudaFree(st->slice_i0);
+    cudaFree(st->slice_nv);
     cudaFree(st->ids);
     cudaFree(st->xi_tab);
     cudaFree(st->xid_tab);
@@ -839,6 +884,8 @@ static int build_stencil(pd_state *st, int16_t **box_dev, int *R_out) {
     std::vector<float4> xt;
     std::vector<double4_32a> xd;
     std::vector<int32_t> ot;
+    std::vector<std::array<int, 3>> off_comp;
+    int halo = 0;
     for (int dz = -R; dz <= R; ++dz)
         for (int dy = -R; dy <= R; ++dy)
             for (int dx = -R; dx <= R; ++dx) {
@@ -849,10 +896,18 @@ static int build_stencil(pd_state *st, int16_t **box_dev, int *R_out) {
                 xt.push_back(make_float4((float)dx * (float)g.dx, (float)dy * (float)g.dx, (float)dz * (float)g.dx,
                                          (float)L0));
                 xd.push_back(make_double4_32a(dx * g.dx, dy * g.dx, dz * g.dx, L0));
-                ot.push_back(dx + g.nx * (dy + g.ny * dz));
+                off_comp.push_back({dx, dy, dz});
+                halo = std::max(halo, std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))));
             }
     PD_REQUIRE(xt.size() <= (size_t)kPad, "horizon stencil has %zu offsets (at most 255 supported)", xt.size());
     st->n_off = (int32_t)xt.size();
+    st->halo = halo;
+    // neighbour offsets: global linear index (fp64 path) or index inside the
+    // staged brick of (8 + 2 halo) x (by + 2 halo) x (bz + 2 halo) records (mixed)
+    const bool f64 = st->mat.precision == PD_PREC_FP64;
+    const int Wx = kSlice + 2 * halo, Wy = st->by + 2 * halo;
+    for (const auto &k : off_comp)
+        ot.push_back(f64 ? k[0] + g.nx * (k[1] + g.ny * k[2]) : k[0] + Wx * (k[1] + Wy * k[2]));
     // unused ids and the padding id: the node itself at distance dx (zero stretch)
     while (xt.size() < (size_t)kTab) {
         xt.push_back(make_float4((float)g.dx, 0.f, 0.f, (float)g.dx));
@@ -883,12 +938,35 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
     PD_TRY(dalloc(&st->coord, N));
     k_coords<<<blocks_for(N), 256, 0, s>>>(st->g.nx, st->g.ny, N, st->coord);
     PD_CHECK_LAUNCH();
-    // SELL-C layout of stencil ids
-    const int T = st->lanes, C = 32 / st->lanes;
-    st->n_slices = (N + C - 1) / C;
+    // brick-ordered SELL-8 layout of stencil ids
+    const pd_grid &g = st->g;
+    st->nbx = (g.nx + kSlice - 1) / kSlice;
+    st->nby = (g.ny + st->by - 1) / st->by;
+    st->nbz = (g.nz + st->bz - 1) / st->bz;
+    st->n_bricks = (long long)st->nbx * st->nby * st->nbz;
+    st->n_slices = st->n_bricks * st->by * st->bz;
+    PD_REQUIRE(st->n_bricks * st->B < (1ll << 31), "too many blocks");
+    {
+        std::vector<int32_t> i0(st->n_slices), nv(st->n_slices);
+        for (long long br = 0; br < st->n_bricks; ++br) {
+            const int bx = (int)(br % st->nbx), by = (int)((br / st->nbx) % st->nby), bz = (int)(br / ((long long)st->nbx * st->nby));
+            for (int r = 0; r < st->by * st->bz; ++r) {
+                const int y = by * st->by + r % st->by, z = bz * st->bz + r / st->by, x0 = bx * kSlice;
+                const long long sidx = br * st->by * st->bz + r;
+                const bool in = y < g.ny && z < g.nz;
+                i0[sidx] = in ? x0 + g.nx * (y + g.ny * z) : 0;
+                nv[sidx] = in ? std::min(kSlice, g.nx - x0) : 0;
+            }
+        }
+        PD_TRY(dalloc(&st->slice_i0, st->n_slices));
+        PD_TRY(dalloc(&st->slice_nv, st->n_slices));
+        PD_CHECK_CUDA(cudaMemcpy(st->slice_i0, i0.data(), i0.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        PD_CHECK_CUDA(cudaMemcpy(st->slice_nv, nv.data(), nv.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     PD_TRY(dalloc(&st->sell_m, st->n_slices));
     PD_TRY(dalloc(&st->sell_off, st->n_slices));
-    k_slice_rounds<<<blocks_for(st->n_slices), 256, 0, s>>>(st->row_ptr, N, st->n_slices, C, T, st->sell_m);
+    k_slice_rounds<<<blocks_for(st->n_slices), 256, 0, s>>>(st->row_ptr, st->slice_i0, st->slice_nv, st->n_slices,
+                                                            st->sell_m);
     PD_CHECK_LAUNCH();
     std::vector<int32_t> m(st->n_slices);
     std::vector<long long> off(st->n_slices);
@@ -907,6 +985,12 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
         cudaFree(box);
         return rc;
     }
+    st->smem_bytes = st->mat.precision == PD_PREC_FP64
+                         ? 0
+                         : 2 * sizeof(float4) * (size_t)(kSlice + 2 * st->halo) * (st->by + 2 * st->halo) *
+                               (st->bz + 2 * st->halo);
+    PD_REQUIRE(st->smem_bytes <= 200 * 1024, "brick %dx%dx%d with halo %d needs %zu bytes of shared memory", kSlice,
+               st->by, st->bz, st->halo, st->smem_bytes);
     int32_t *bad = nullptr;
     if ((rc = dalloc(&st->ids, st->sell_len)) != PD_OK || (rc = dalloc(&bad, 1)) != PD_OK) {
         cudaFree(box);
@@ -914,8 +998,9 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
         return rc;
     }
     cudaMemset(bad, 0, sizeof(int32_t));
-    k_fill_ids<<<blocks_for(st->n_slices * C), 256, 0, s>>>(st->row_ptr, col, st->coord, N, st->n_slices, C, T,
-                                                           st->sell_off, st->sell_m, box, R, st->ids, bad);
+    k_fill_ids<<<blocks_for(st->n_slices * kSlice), 256, 0, s>>>(st->row_ptr, col, st->coord, st->slice_i0,
+                                                                st->slice_nv, st->n_slices, st->sell_off, st->sell_m,
+                                                                box, R, st->ids, bad);
     int32_t hbad = 0;
     cudaError_t e = cudaMemcpy(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost);
     cudaFree(box);
@@ -944,6 +1029,7 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
     }
     // per-sample arrays
     const bool f64 = st->mat.precision == PD_PREC_FP64;
+    (void)g;
     const size_t dsz = f64 ? sizeof(double) : sizeof(float);
     PD_CHECK_CUDA(cudaMalloc(&st->dmg, (size_t)B * st->sell_len * dsz));
     if (f64) {
@@ -954,7 +1040,7 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
     }
     PD_CHECK_CUDA(cudaMalloc(&st->rec[0], (size_t)B * N * 32));
     PD_CHECK_CUDA(cudaMalloc(&st->rec[1], (size_t)B * N * 32));
-    st->nblk = (int)((st->n_slices + kWarps - 1) / kWarps);
+    st->nblk = (int)st->n_bricks;
     PD_TRY(dalloc(&st->step, B));
     PD_TRY(dalloc(&st->done, B));
     PD_TRY(dalloc(&st->status, B));
@@ -1000,10 +1086,26 @@ extern "C" int pd_state_create(const pd_grid *g, const int32_t *row_ptr, const i
     st->B = batch;
     st->N = (int64_t)g->nx * g->ny * g->nz;
     st->nb = n_bonds;
-    st->lanes = 4;
-    if (const char *e = std::getenv("PD_LANES")) {
-        const int v = std::atoi(e);
-        if (v == 2 || v == 4 || v == 8) st->lanes = v;
+    // brick rows: the largest brick that still gives at least two blocks per SM
+    {
+        static const int cand[][2] = {{8, 8}, {8, 4}, {4, 4}, {4, 2}, {2, 2}, {2, 1}, {1, 1}};
+        st->by = 1;
+        st->bz = 1;
+        for (const auto &cb : cand) {
+            const long long nbr = (long long)((g->nx + 7) / 8) * ((g->ny + cb[0] - 1) / cb[0]) * ((g->nz + cb[1] - 1) / cb[1]);
+            if (nbr * batch >= 304) {
+                st->by = cb[0];
+                st->bz = cb[1];
+                break;
+            }
+        }
+        if (const char *e = std::getenv("PD_BRICK")) {
+            int y = 0, z = 0;
+            if (sscanf(e, "%dx%d", &y, &z) == 2 && y >= 1 && y <= 16 && z >= 1 && z <= 16) {
+                st->by = y;
+                st->bz = z;
+            }
+        }
     }
     const double delta = g->m_ratio * g->dx;
     st->c = 12.0 * mat->E / (M_PI * delta * delta * delta * delta);
@@ -1073,7 +1175,6 @@ extern "C" int pd_state_load(pd_state *st, const double *u, const double *v, con
     cudaStream_t s = (cudaStream_t)stream;
     const long long NB = st->N * st->B;
     const bool f64 = st->mat.precision == PD_PREC_FP64;
-    const int C = 32 / st->lanes;
     k_reset_run<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->step, st->done, st->status, st->peak, st->peak_step,
                                                   st->ticket, step);
     PD_CHECK_LAUNCH();
@@ -1086,11 +1187,13 @@ extern "C" int pd_state_load(pd_state *st, const double *u, const double *v, con
     PD_CHECK_LAUNCH();
     if (d) {
         if (f64)
-            k_dmg_map<double, true><<<blocks_for(NB), 256, 0, s>>>(st->row_ptr, st->N, st->B, st->nb, C, st->sell_off,
-                                                                   st->sell_len, (double *)st->dmg, (double *)d);
+            k_dmg_map<double, true><<<blocks_for(NB), 256, 0, s>>>(
+                st->row_ptr, st->N, st->B, st->nb, st->g.nx, st->g.ny, st->by, st->bz, st->nbx, st->nby, st->sell_off,
+                st->sell_len, (double *)st->dmg, (double *)d);
         else
-            k_dmg_map<float, true><<<blocks_for(NB), 256, 0, s>>>(st->row_ptr, st->N, st->B, st->nb, C, st->sell_off,
-                                                                  st->sell_len, (float *)st->dmg, (double *)d);
+            k_dmg_map<float, true><<<blocks_for(NB), 256, 0, s>>>(
+                st->row_ptr, st->N, st->B, st->nb, st->g.nx, st->g.ny, st->by, st->bz, st->nbx, st->nby, st->sell_off,
+                st->sell_len, (float *)st->dmg, (double *)d);
         PD_CHECK_LAUNCH();
     }
     return PD_OK;
@@ -1100,7 +1203,6 @@ extern "C" int pd_state_store(const pd_state *st, double *u, double *v, double *
     PD_REQUIRE(st != nullptr, "state is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     const long long NB = st->N * st->B;
-    const int C = 32 / st->lanes;
     if (u || v) {
         if (st->mat.precision == PD_PREC_FP64)
             k_store_u<true><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, st->u64, st->v64, st->vdf, st->step,
@@ -1112,11 +1214,13 @@ extern "C" int pd_state_store(const pd_state *st, double *u, double *v, double *
     }
     if (d) {
         if (st->mat.precision == PD_PREC_FP64)
-            k_dmg_map<double, false><<<blocks_for(NB), 256, 0, s>>>(st->row_ptr, st->N, st->B, st->nb, C,
-                                                                    st->sell_off, st->sell_len, (double *)st->dmg, d);
+            k_dmg_map<double, false><<<blocks_for(NB), 256, 0, s>>>(
+                st->row_ptr, st->N, st->B, st->nb, st->g.nx, st->g.ny, st->by, st->bz, st->nbx, st->nby, st->sell_off,
+                st->sell_len, (double *)st->dmg, d);
         else
-            k_dmg_map<float, false><<<blocks_for(NB), 256, 0, s>>>(st->row_ptr, st->N, st->B, st->nb, C, st->sell_off,
-                                                                   st->sell_len, (float *)st->dmg, d);
+            k_dmg_map<float, false><<<blocks_for(NB), 256, 0, s>>>(
+                st->row_ptr, st->N, st->B, st->nb, st->g.nx, st->g.ny, st->by, st->bz, st->nbx, st->nby, st->sell_off,
+                st->sell_len, (float *)st->dmg, d);
         PD_CHECK_LAUNCH();
     }
     return PD_OK;
@@ -1161,9 +1265,11 @@ extern "C" int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int
         StepKernel k = pick(st, false);
         const unsigned grid = (unsigned)st->nblk * (unsigned)st->B;
         cudaGraph_t graph;
-        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        cudaError_t e = cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)st->smem_bytes);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int q = 0; q < chunk; ++q) k<<<grid, kThreads, 0, cs>>>(a);
+            for (int q = 0; q < chunk; ++q) k<<<grid, kThreads, st->smem_bytes, cs>>>(a);
             e = cudaStreamEndCapture(cs, &graph);
         }
         if (e == cudaSuccess) {
