@@ -139,6 +139,20 @@ PD_API const char *pd_version(void);
 PD_API int pd_build_neighbours(const pd_grid *g, int32_t *row_ptr, int32_t *col, int64_t cap,
                         int64_t *n_bonds, pd_stream stream);
 
+/* The same neighbour list as pd_build_neighbours, computed without any device
+ * allocation (the paper has no counterpart: this serves callers that cannot
+ * call cudaMalloc, e.g. code running under an external memory manager that
+ * owns all device memory). The one word of device scratch (the scan's
+ * overflow flag) lives in a 256-byte static device array that every GPU
+ * loading the library holds until exit; it is cleared on every call. The
+ * first call on a device looks up the array's device address (with that
+ * device current), so make that first call before any stream capture. Calls
+ * that overlap on the GPU share the array and race. Sizes: at most 2^31 - 2
+ * nodes and 2^31 - 1 bonds; larger grids return PD_ERR_ARG. Arguments,
+ * outputs, synchronisation and errors are those of pd_build_neighbours. */
+PD_API int pd_build_neighbours_noalloc(const pd_grid *g, int32_t *row_ptr, int32_t *col, int64_t cap,
+                                       int64_t *n_bonds, pd_stream stream);
+
 /* Per-DOF boundary codes (device uint8[N*3]: 0 free, 1 fixed, 2 +U(n), 3 -U(n)). */
 PD_API int pd_bc_codes(const pd_grid *g, const pd_bc *bc, uint8_t *codes, pd_stream stream);
 

@@ -69,6 +69,7 @@ _SIGS = {
     "pd_last_error": (C.c_int, [C.c_char_p, C.c_size_t]),
     "pd_version": (C.c_char_p, []),
     "pd_build_neighbours": (C.c_int, [C.POINTER(Grid), _VP, _VP, C.c_int64, C.POINTER(C.c_int64), _VP]),
+    "pd_build_neighbours_noalloc": (C.c_int, [C.POINTER(Grid), _VP, _VP, C.c_int64, C.POINTER(C.c_int64), _VP]),
     "pd_bc_codes": (C.c_int, [C.POINTER(Grid), C.POINTER(BC), _VP, _VP]),
     "pd_state_create": (C.c_int, [C.POINTER(Grid), _VP, _VP, C.c_int64, C.POINTER(Material), C.POINTER(BC),
                                   C.c_int32, C.POINTER(_VP)]),

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <mutex>
 
 #include "pd_internal.cuh"
 
@@ -228,6 +229,69 @@ extern "C" int pd_bc_codes(const pd_grid *g, const pd_bc *bc, uint8_t *codes, pd
     PD_REQUIRE(bc->type == PD_BC_BAR_TENSION || bc->type == PD_BC_BEAM_3PT, "unknown bc type %d", bc->type);
     const long long n = (long long)g->nx * g->ny * g->nz;
     k_bc<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(g->nx, g->ny, g->nz, *bc, codes);
+    PD_CHECK_LAUNCH();
+    return PD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of pd_build_neighbours.
+//
+// The build needs one word of device scratch beyond its inputs and outputs:
+// the overflow flag of the row-pointer scan. pd_build_neighbours takes it from
+// cudaMalloc on every call; this variant keeps it in a file-scope device array
+// instead, for callers that cannot allocate device memory. Device addresses of
+// the array are looked up once per device (cudaGetSymbolAddress, with that
+// device current) on the first call made on that device.
+static __device__ __align__(256) int32_t g_noalloc_scratch[64];  // 256 bytes; word 0 = scan overflow flag
+
+static int noalloc_scratch(int32_t **out) {
+    static std::mutex mu;
+    static int32_t *addr[64] = {nullptr};
+    int dev = 0;
+    PD_CHECK_CUDA(cudaGetDevice(&dev));
+    PD_REQUIRE(dev >= 0 && dev < 64, "device index %d out of range for the static scratch table", dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            set_error("cudaGetSymbolAddress of the neighbour-build scratch failed: %s", cudaGetErrorString(e));
+            return PD_ERR_CUDA;
+        }
+        addr[dev] = (int32_t *)p;
+    }
+    *out = addr[dev];
+    return PD_OK;
+}
+
+extern "C" int pd_build_neighbours_noalloc(const pd_grid *g, int32_t *row_ptr, int32_t *col, int64_t cap,
+                                           int64_t *n_bonds, pd_stream stream) {
+    PD_TRY(validate_grid(g));
+    PD_REQUIRE(row_ptr != nullptr && n_bonds != nullptr, "row_ptr and n_bonds are required");
+    const long long n = (long long)g->nx * g->ny * g->nz;
+    PD_REQUIRE(n + 1 <= 2147483647ll, "at most 2^31 - 2 nodes");
+    int32_t *flag = nullptr;
+    PD_TRY(noalloc_scratch(&flag));
+    cudaStream_t s = (cudaStream_t)stream;
+    GridDev d = make_dev(g);
+    PD_CHECK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));  // the array keeps the previous call's value
+    const int bs = 256;
+    const unsigned nblk = (unsigned)((n + bs - 1) / bs);
+    k_rows<false><<<nblk, bs, 0, s>>>(d, row_ptr, nullptr);
+    PD_CHECK_LAUNCH();
+    PD_TRY(scan_inplace_i32(row_ptr, n, flag, s));
+    int32_t total = 0, ovf = 0;
+    PD_CHECK_CUDA(cudaMemcpyAsync(&total, row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PD_CHECK_CUDA(cudaMemcpyAsync(&ovf, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PD_CHECK_CUDA(cudaStreamSynchronize(s));
+    PD_REQUIRE(!ovf, "more than 2^31-1 bonds");
+    *n_bonds = total;
+    if (col == nullptr) return PD_OK;
+    if (cap < total) {
+        set_error("col capacity %lld < %d bonds", (long long)cap, total);
+        return PD_ERR_CAP;
+    }
+    k_rows<true><<<nblk, bs, 0, s>>>(d, row_ptr, col);
     PD_CHECK_LAUNCH();
     return PD_OK;
 }
