@@ -1,0 +1,274 @@
+// pd_device.cuh -- device-side pieces shared by the step kernels: launch
+// constants, the kernel argument block, double-float arithmetic and the bond
+// laws.
+#pragma once
+
+#include <cmath>
+
+#include "pd_internal.cuh"
+
+namespace pdi {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kLanes = 4;   // sub-lanes per node (T)
+constexpr int kSlice = 8;   // nodes per slice (C = 32 / T)
+constexpr int kTab = 256;     // stencil table entries: ids 0..n_off-1, padding id 0xFF
+constexpr int kPad = 0xFF;
+
+struct df {
+    float hi, lo;
+};
+
+struct StepArgs {
+    long long N;
+    long long n_slices;
+    int nblk;  // bricks per sample
+    int B;
+    int nx, ny, nz, BY, BZ, nbx, nby, H, Wx, Wy, Wz;
+    const long long *sell_off;
+    const int32_t *sell_m;
+    const int32_t *slice_i0;
+    const int32_t *slice_nv;
+    const uint8_t *ids;
+    const float4 *xi_tab;
+    const double4_32a *xid_tab;
+    const int32_t *off_tab;
+    int n_off;
+    void *dmg;
+    long long sell_len;
+    double *u64;
+    double *v64;
+    void *rec0;
+    void *rec1;
+    const float *kappa;
+    const uint8_t *codes;
+    int32_t *step;         // [2][B]: step index, double-buffered by launch parity
+    int32_t *done;         // [2][B]: stop flags, double-buffered the same way
+    int par;               // this launch reads buffer par and writes buffer 1 - par
+    const int32_t *brick_ridx;  // [n_bricks]: index among the reaction bricks, or -1
+    int32_t *status;
+    double *peak;
+    int32_t *peak_step;
+    double *partial;
+    unsigned int *ticket;
+    double *reaction;
+    int n_react;
+    int k_local;
+    double *F_out;
+    double dt, rho, zeta, u_max;
+    double ca, dtr, icb, idt;  // 1 - zeta dt/2, dt/rho, 1/(1 + zeta dt/2), 1/dt
+    df du_df, dudt_df;         // u_max / n_ramp and u_max / (n_ramp dt)
+    df ca_df, dtr_df, icb_df, dt_df;
+    float4 *vdf;
+    int n_ramp;
+    int max_steps;
+    int use_stop;
+    int st_wpb;      // stencil path: row pairs per brick
+    float4 half_tab[61];   // stencil path: xi of the positive half-stencil offsets (x, y, z) and |xi|
+    int half_off[3][61];   // stencil path: integer components of those offsets
+    float dxf;       // dx in FP32
+    float L0q[10];   // sqrt(q) dx in FP32, q = |k|^2 (stencil path)
+    double cV;  // micromodulus x node volume
+    double V;
+    double s_ratio, k, alpha, inv_1mek, inv_1pa;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---- double-float arithmetic (an unevaluated pair hi + lo of FP32 numbers;
+// Dekker 1971, Knuth TAOCP vol. 2, 4.2.2): about 48 significant bits with
+// FP32 instructions only.
+
+// s + e = a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = a + b;
+    const float z = s - a;
+    const float e = (a - (s - z)) + (b - z);
+    return {s, e};
+}
+
+// s + e = a + b exactly when |a| >= |b| (Dekker's FastTwoSum).
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ df df_add(df x, df y) {
+    const df s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+
+__device__ __forceinline__ df df_mul(df x, df y) {
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return fast_two_sum(p, e);
+}
+
+__host__ __device__ __forceinline__ df df_split(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+// s + x with the rounding error carried in c (accumulation by TwoSum).
+__device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
+    const df t = two_sum(s, x);
+    s = t.hi;
+    c += t.lo;
+}
+
+template <typename T>
+__device__ __forceinline__ T law_damage(int law, T s, T s0, T sc, T k, T alpha, T inv_1mek, T inv_1pa);
+
+template <>
+__device__ __forceinline__ float law_damage<float>(int law, float s, float s0, float sc, float k, float alpha,
+                                                   float inv_1mek, float inv_1pa) {
+    if (s >= sc) return 1.0f;
+    if (law == PD_LAW_BILINEAR) return 1.0f - s0 * (sc - s) / (s * (sc - s0));
+    const float t = (s - s0) / (sc - s0);
+    const float br = 1.0f - (1.0f - expf(-k * t)) * inv_1mek + alpha * (1.0f - t);
+    return 1.0f - (s0 / s) * br * inv_1pa;
+}
+
+template <>
+__device__ __forceinline__ double law_damage<double>(int law, double s, double s0, double sc, double k,
+                                                     double alpha, double inv_1mek, double inv_1pa) {
+    if (s >= sc) return 1.0;
+    if (law == PD_LAW_BILINEAR) return 1.0 - s0 * (sc - s) / (s * (sc - s0));
+    const double t = (s - s0) / (sc - s0);
+    const double br = 1.0 - (1.0 - exp(-k * t)) * inv_1mek + alpha * (1.0 - t);
+    return 1.0 - (s0 / s) * br * inv_1pa;
+}
+
+__device__ __forceinline__ double ramp(const StepArgs &a, int n) {
+    const int m = n < a.n_ramp ? n : a.n_ramp;
+    return a.u_max * (double)m / (double)a.n_ramp;
+}
+
+__device__ __forceinline__ float pick3(float a, float b, float c, int q) { return q == 0 ? a : (q == 1 ? b : c); }
+__device__ __forceinline__ double pick3(double a, double b, double c, int q) { return q == 0 ? a : (q == 1 ? b : c); }
+
+
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Sum over a warp along a fixed xor tree in double-float. TwoSum is exact and
+// the low-part sum is commutative, so every lane ends with the same total.
+__device__ __forceinline__ df warp_sum_df(df v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const df w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = df_add(v, w);
+    }
+    return v;
+}
+
+// Prescribed displacement U(n+1) and the prescribed velocity
+// (U(n+1) - U(n)) / dt of step n as double-float, from m = min(n, n_ramp)
+// (FP32 only; m is exact in FP32 below 2^24).
+__device__ __forceinline__ void prescribed(const StepArgs &a, int n, df &U1, df &vp) {
+    const int m0 = n < a.n_ramp ? n : a.n_ramp, m1 = n + 1 < a.n_ramp ? n + 1 : a.n_ramp;
+    U1 = df_mul(a.du_df, df{(float)m1, 0.f});
+    vp = df_mul(a.dudt_df, df{(float)(m1 - m0), 0.f});
+}
+
+// Bookkeeping of a step launch. Blocks read step/done from buffer par and the
+// last reaction block of a sample writes buffer 1 - par, so no block has to
+// wait for the others to have read the step index. A sample that is already
+// done is carried over by brick 0.
+__device__ __forceinline__ void carry_done(const StepArgs &a, int b) {
+    a.step[(1 - a.par) * a.B + b] = a.step[a.par * a.B + b];
+    a.done[(1 - a.par) * a.B + b] = 1;
+}
+
+// End of a step kernel in a reaction brick (one holding prescribed DOFs, or
+// brick 0), called by every warp of the block with all lanes active: the
+// reaction sum (sum over prescribed DOFs of -F sign, double-float) is reduced
+// along fixed trees -- warp, the block's warps in order (by the block's last
+// warp to finish), the reaction bricks of the sample in order (by the
+// sample's last reaction block) -- which then updates the run bookkeeping.
+// FP64 appears only in the final conversion R = V (hi + lo) and the peak test.
+__device__ __forceinline__ void reaction_finish(const StepArgs &a, df Rloc, int b, int blk, int warp, int lane,
+                                                int nwarps, float2 *red, unsigned *s_cnt, int n) {
+    if (__any_sync(0xffffffffu, Rloc.hi != 0.f || Rloc.lo != 0.f)) Rloc = warp_sum_df(Rloc);
+    unsigned flag = 0u;
+    if (lane == 0) {
+        red[warp] = make_float2(Rloc.hi, Rloc.lo);
+        __threadfence_block();
+        flag = (atomicAdd(s_cnt, 1u) == (unsigned)(nwarps - 1));
+    }
+    flag = __shfl_sync(0xffffffffu, flag, 0);
+    if (!flag) return;
+    __threadfence_block();
+    df v = {0.f, 0.f};
+    if (lane < nwarps) {
+        const volatile float2 *r = red + lane;
+        v = df{r->x, r->y};
+    }
+    // (shared-memory partials: one round trip)
+    if (__any_sync(0xffffffffu, v.hi != 0.f || v.lo != 0.f)) v = warp_sum_df(v);
+    float2 *part = (float2 *)a.partial + (size_t)b * a.nblk;
+    if (lane == 0) {
+        part[blk] = make_float2(v.hi, v.lo);
+        __threadfence();
+        flag = (atomicAdd(&a.ticket[b], 1u) == (unsigned)(a.nblk - 1));
+    }
+    flag = __shfl_sync(0xffffffffu, flag, 0);
+    if (!flag) return;
+    __threadfence();
+    // the block partials are read with L2 loads issued eight at a time (a
+    // dependent chain of volatile loads would cost one L2 round trip each)
+    df acc = {0.f, 0.f};
+    for (int q0 = lane; q0 < a.nblk; q0 += 256) {
+        float2 pv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + 32 * u;
+            pv[u] = q < a.nblk ? __ldcg(part + q) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = df_add(acc, df{pv[u].x, pv[u].y});
+    }
+    acc = warp_sum_df(acc);
+    if (lane == 0) {
+        const double R = a.V * ((double)acc.hi + (double)acc.lo);
+        if (!isfinite(R)) a.status[b] |= 1;
+        if (a.reaction) a.reaction[(size_t)b * a.n_react + a.k_local] = R;
+        double Q = a.peak[b];
+        int np = a.peak_step[b];
+        if (R > Q) {
+            Q = R;
+            np = n;
+            a.peak[b] = Q;
+            a.peak_step[b] = np;
+        }
+        const int out = (1 - a.par) * a.B + b;
+        a.step[out] = n + 1;
+        a.done[out] = (a.use_stop && ((Q > 0.0 && n - np >= 100 && R < 0.5 * Q) || n + 1 >= a.max_steps)) ||
+                              !isfinite(R)
+                          ? 1
+                          : 0;
+        a.ticket[b] = 0u;
+    }
+}
+
+// Kernels and host helpers of the compile-time 122-offset stencil path
+// (pd_stencil.cu): the horizon |k|^2 <= 9 of m in [3, sqrt(10)).
+bool stencil_applicable(const pd_state *st);
+int stencil_build(pd_state *st, const int32_t *col);
+int stencil_launch(const pd_state *st, const StepArgs &a, bool force_only, cudaStream_t s);
+int stencil_reset_damage(pd_state *st, cudaStream_t s);
+int stencil_map_damage(const pd_state *st, double *csr, bool to_state, cudaStream_t s);
+void stencil_fill_args(const pd_state *st, StepArgs &a);
+
+}  // namespace pdi

@@ -94,6 +94,14 @@ struct pd_state {
     double4_32a *xid_tab;   // [256]: the same in FP64
     int32_t *off_tab;       // [256]: neighbour offset (fp64 path: global j - i; mixed: brick-local)
     size_t smem_bytes;      // staged brick records (mixed path)
+    // compile-time 122-offset stencil path (mixed precision, m in [3, sqrt(10)))
+    bool stencil;
+    int32_t st_wpb;         // row pairs per brick (2 brick rows per warp)
+    int32_t st_q;           // warps sharing a row pair (parts of the half-stencil)
+    int64_t st_len;         // damage slots per sample
+    float *st_tmpl;         // [st_len]: 0 for real bonds, 1 for absent (broken) slots
+    int16_t *st_box;        // [7^3]: stencil code 2 m + t of an offset, -1 outside
+    int32_t *col_csr;       // CSR copy for damage load/store
     // per-sample state
     void *dmg;          // float or double [B][sell_len]
     double *u64;        // fp64 path: [B][N][3]
@@ -106,8 +114,12 @@ struct pd_state {
     uint8_t *codes;     // [N][3]
     int32_t *coord;     // [N] packed grid coordinates
     // run bookkeeping (device)
-    int32_t *step;      // [B]
-    int32_t *done;      // [B]
+    int32_t *step;      // [2][B], double-buffered by launch parity
+    int32_t *done;      // [2][B]
+    int32_t bk_par;     // buffer holding the current step/done
+    int32_t chunk_par;  // parity the captured chunk starts from
+    int32_t *brick_ridx;  // [n_bricks]: index among reaction bricks, or -1
+    int32_t nrb;          // reaction bricks (bricks with prescribed DOFs, and brick 0)
     int32_t *status;    // [B] bit 0: non-finite reaction
     double *peak;       // [B]
     int32_t *peak_step; // [B]

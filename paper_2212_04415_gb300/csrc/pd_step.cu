@@ -44,146 +44,9 @@
 #include <cstdlib>
 #include <vector>
 
-#include "pd_internal.cuh"
+#include "pd_device.cuh"
 
 namespace pdi {
-
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int kLanes = 4;   // sub-lanes per node (T)
-constexpr int kSlice = 8;   // nodes per slice (C = 32 / T)
-constexpr int kTab = 256;     // stencil table entries: ids 0..n_off-1, padding id 0xFF
-constexpr int kPad = 0xFF;
-
-struct df {
-    float hi, lo;
-};
-
-struct StepArgs {
-    long long N;
-    long long n_slices;
-    int nblk;  // bricks per sample
-    int B;
-    int nx, ny, nz, BY, BZ, nbx, nby, H, Wx, Wy, Wz;
-    const long long *sell_off;
-    const int32_t *sell_m;
-    const int32_t *slice_i0;
-    const int32_t *slice_nv;
-    const uint8_t *ids;
-    const float4 *xi_tab;
-    const double4_32a *xid_tab;
-    const int32_t *off_tab;
-    int n_off;
-    void *dmg;
-    long long sell_len;
-    double *u64;
-    double *v64;
-    void *rec0;
-    void *rec1;
-    const float *kappa;
-    const uint8_t *codes;
-    int32_t *step;
-    int32_t *done;
-    int32_t *status;
-    double *peak;
-    int32_t *peak_step;
-    double *partial;
-    unsigned int *ticket;
-    double *reaction;
-    int n_react;
-    int k_local;
-    double *F_out;
-    double dt, rho, zeta, u_max;
-    double ca, dtr, icb, idt;  // 1 - zeta dt/2, dt/rho, 1/(1 + zeta dt/2), 1/dt
-    df ca_df, dtr_df, icb_df, dt_df;
-    float4 *vdf;
-    int n_ramp;
-    int max_steps;
-    int use_stop;
-    double cV;  // micromodulus x node volume
-    double V;
-    double s_ratio, k, alpha, inv_1mek, inv_1pa;
-};
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// ---- double-float arithmetic (an unevaluated pair hi + lo of FP32 numbers;
-// Dekker 1971, Knuth TAOCP vol. 2, 4.2.2): about 48 significant bits with
-// FP32 instructions only.
-
-// s + e = a + b exactly (Knuth's TwoSum).
-__device__ __forceinline__ df two_sum(float a, float b) {
-    const float s = a + b;
-    const float z = s - a;
-    const float e = (a - (s - z)) + (b - z);
-    return {s, e};
-}
-
-// s + e = a + b exactly when |a| >= |b| (Dekker's FastTwoSum).
-__device__ __forceinline__ df fast_two_sum(float a, float b) {
-    const float s = a + b;
-    return {s, b - (s - a)};
-}
-
-__device__ __forceinline__ df df_add(df x, df y) {
-    const df s = two_sum(x.hi, y.hi);
-    return fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
-}
-
-__device__ __forceinline__ df df_mul(df x, df y) {
-    const float p = x.hi * y.hi;
-    float e = fmaf(x.hi, y.hi, -p);
-    e = fmaf(x.hi, y.lo, e);
-    e = fmaf(x.lo, y.hi, e);
-    return fast_two_sum(p, e);
-}
-
-__host__ __device__ __forceinline__ df df_split(double x) {
-    const float h = (float)x;
-    return {h, (float)(x - (double)h)};
-}
-
-// s + x with the rounding error carried in c (accumulation by TwoSum).
-__device__ __forceinline__ void two_sum_acc(float &s, float &c, float x) {
-    const df t = two_sum(s, x);
-    s = t.hi;
-    c += t.lo;
-}
-
-template <typename T>
-__device__ __forceinline__ T law_damage(int law, T s, T s0, T sc, T k, T alpha, T inv_1mek, T inv_1pa);
-
-template <>
-__device__ __forceinline__ float law_damage<float>(int law, float s, float s0, float sc, float k, float alpha,
-                                                   float inv_1mek, float inv_1pa) {
-    if (s >= sc) return 1.0f;
-    if (law == PD_LAW_BILINEAR) return 1.0f - s0 * (sc - s) / (s * (sc - s0));
-    const float t = (s - s0) / (sc - s0);
-    const float br = 1.0f - (1.0f - expf(-k * t)) * inv_1mek + alpha * (1.0f - t);
-    return 1.0f - (s0 / s) * br * inv_1pa;
-}
-
-template <>
-__device__ __forceinline__ double law_damage<double>(int law, double s, double s0, double sc, double k,
-                                                     double alpha, double inv_1mek, double inv_1pa) {
-    if (s >= sc) return 1.0;
-    if (law == PD_LAW_BILINEAR) return 1.0 - s0 * (sc - s) / (s * (sc - s0));
-    const double t = (s - s0) / (sc - s0);
-    const double br = 1.0 - (1.0 - exp(-k * t)) * inv_1mek + alpha * (1.0 - t);
-    return 1.0 - (s0 / s) * br * inv_1pa;
-}
-
-__device__ __forceinline__ double ramp(const StepArgs &a, int n) {
-    const int m = n < a.n_ramp ? n : a.n_ramp;
-    return a.u_max * (double)m / (double)a.n_ramp;
-}
-
-__device__ __forceinline__ float pick3(float a, float b, float c, int q) { return q == 0 ? a : (q == 1 ? b : c); }
-__device__ __forceinline__ double pick3(double a, double b, double c, int q) { return q == 0 ? a : (q == 1 ? b : c); }
 
 // One explicit step (or, with FORCE_ONLY, one force evaluation) of every
 // (sample, node) pair. Grid: n_bricks * B blocks, sample fastest; the warps of
@@ -196,23 +59,37 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
     __shared__ float4 s_xi[kTab];
     __shared__ int s_off[kTab];
     __shared__ double4_32a s_xid[F64 ? kTab : 1];
-    __shared__ double red[kWarps];
+    __shared__ float2 red[kWarps];
     __shared__ double s_U[2];
+    __shared__ float s_pre[4];
     __shared__ unsigned s_cnt;
 
     const int b = blockIdx.x % a.B;
     const int brick = blockIdx.x / a.B;
-    const bool done = FORCE_ONLY ? false : (a.done[b] != 0);
-    const int n = a.step[b];
+    const bool done = FORCE_ONLY ? false : (a.done[a.par * a.B + b] != 0);
+    const int n = a.step[a.par * a.B + b];
+    if (done) {  // block-uniform
+        if (brick == 0 && threadIdx.x == 0) carry_done(a, b);
+        return;
+    }
     for (int q = threadIdx.x; q < kTab; q += kThreads) {
         s_xi[q] = a.xi_tab[q];
         s_off[q] = a.off_tab[q];
         if (F64) s_xid[q] = a.xid_tab[q];
     }
-    if (threadIdx.x < kWarps) red[threadIdx.x] = 0.0;
+    if (threadIdx.x < kWarps) red[threadIdx.x] = make_float2(0.f, 0.f);
     if (threadIdx.x == 0) {
-        s_U[0] = ramp(a, n);
-        s_U[1] = ramp(a, n + 1);
+        if (F64) {
+            s_U[0] = ramp(a, n);
+            s_U[1] = ramp(a, n + 1);
+        } else {
+            df U1, vp;
+            prescribed(a, n, U1, vp);
+            s_pre[0] = U1.hi;
+            s_pre[1] = U1.lo;
+            s_pre[2] = vp.hi;
+            s_pre[3] = vp.lo;
+        }
         s_cnt = 0u;
     }
     const int bx = brick % a.nbx, by = (brick / a.nbx) % a.nby, bz = brick / (a.nbx * a.nby);
@@ -241,7 +118,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lane % C, t = lane / C;
-    double Rloc = 0.0;
+    df Rloc = {0.f, 0.f};
 
     if (!done) {
         for (int r = warp; r < a.BY * a.BZ; r += kWarps) {
@@ -311,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
                             vc = 0.0;
                         } else {
                             const double sg = code == 2 ? 1.0 : -1.0;
-                            Rloc -= sg * F * a.V;
+                            Rloc = df_add(Rloc, df_split(-sg * F));
                             vc = sg * (s_U[1] - s_U[0]) * a.idt;
                             uc = sg * s_U[1];
                         }
@@ -414,10 +291,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
                             u = {0.f, 0.f};
                             v = {0.f, 0.f};
                         } else {
-                            const double sg = code == 2 ? 1.0 : -1.0;
-                            Rloc -= sg * ((double)F.hi + (double)F.lo) * a.V;
-                            v = df_split(sg * (s_U[1] - s_U[0]) * a.idt);
-                            u = df_split(sg * s_U[1]);
+                            const float sg = code == 2 ? 1.0f : -1.0f;
+                            Rloc = df_add(Rloc, df{-sg * F.hi, -sg * F.lo});
+                            v = df{sg * s_pre[2], sg * s_pre[3]};
+                            u = df{sg * s_pre[0], sg * s_pre[1]};
                         }
                         vh[q] = v.hi;
                         vl[q] = v.lo;
@@ -433,54 +310,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
 
     if (FORCE_ONLY || done) return;  // uniform per block
 
-    // Deterministic reaction reduction without a block barrier: each warp
-    // sums its lanes (a fixed xor tree, skipped by warps without a prescribed
-    // DOF, whose sum is exactly 0) into shared memory; the last warp of the
-    // block to finish adds the 8 warp sums in a fixed order and posts the
-    // block partial; the last block of the sample adds the block partials in
-    // block order and updates the run bookkeeping. Early warps just exit.
-    if (__any_sync(0xffffffffu, Rloc != 0.0)) Rloc = warp_sum(Rloc);
-    unsigned flag = 0u;
-    if (lane == 0) {
-        red[warp] = Rloc;
-        __threadfence_block();
-        flag = (atomicAdd(&s_cnt, 1u) == (unsigned)(kWarps - 1));
-    }
-    flag = __shfl_sync(0xffffffffu, flag, 0);
-    if (!flag) return;
-    __threadfence_block();
-    double v = lane < kWarps ? ((volatile double *)red)[lane] : 0.0;
-    if (__any_sync(0xffffffffu, v != 0.0)) v = warp_sum(v);
-    if (lane == 0) {
-        a.partial[(size_t)b * a.nblk + brick] = v;
-        __threadfence();
-        flag = (atomicAdd(&a.ticket[b], 1u) == (unsigned)(a.nblk - 1));
-    }
-    flag = __shfl_sync(0xffffffffu, flag, 0);
-    if (!flag) return;
-    __threadfence();
-    const volatile double *p = a.partial + (size_t)b * a.nblk;
-    v = 0.0;
-    for (int q = lane; q < a.nblk; q += 32) v += p[q];
-    v = warp_sum(v);
-    if (lane == 0) {
-        const double R = v;
-        if (!isfinite(R)) a.status[b] |= 1;
-        if (a.reaction) a.reaction[(size_t)b * a.n_react + a.k_local] = R;
-        double Q = a.peak[b];
-        int np = a.peak_step[b];
-        if (R > Q) {
-            Q = R;
-            np = n;
-            a.peak[b] = Q;
-            a.peak_step[b] = np;
-        }
-        a.step[b] = n + 1;
-        if (a.use_stop) {
-            if ((Q > 0.0 && n - np >= 100 && R < 0.5 * Q) || n + 1 >= a.max_steps || !isfinite(R)) a.done[b] = 1;
-        }
-        a.ticket[b] = 0u;
-    }
+    const int ridx = a.brick_ridx[brick];
+    if (ridx >= 0) reaction_finish(a, Rloc, b, ridx, warp, lane, kWarps, red, &s_cnt, n);
 }
 
 // ---------------------------------------------------------------- set-up
@@ -600,7 +431,9 @@ __global__ void k_reset_run(int B, int32_t *step, int32_t *done, int32_t *status
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
     step[b] = step0;
+    step[B + b] = step0;
     done[b] = 0;
+    done[B + b] = 0;
     status[b] = 0;
     peak[b] = -INFINITY;
     peak_step[b] = -1;
@@ -763,7 +596,9 @@ static StepArgs make_args(const pd_state *st) {
     memset(&a, 0, sizeof(a));
     a.N = st->N;
     a.n_slices = st->n_slices;
-    a.nblk = st->nblk;
+    a.nblk = st->nrb;
+    a.par = st->bk_par;
+    a.brick_ridx = st->brick_ridx;
     a.B = st->B;
     a.sell_off = st->sell_off;
     a.sell_m = st->sell_m;
@@ -786,7 +621,11 @@ static StepArgs make_args(const pd_state *st) {
     a.off_tab = st->off_tab;
     a.n_off = st->n_off;
     a.dmg = st->dmg;
-    a.sell_len = st->sell_len;
+    a.sell_len = st->stencil ? st->st_len : st->sell_len;
+    a.dxf = (float)st->g.dx;
+    a.st_wpb = st->st_wpb;
+    if (st->stencil) stencil_fill_args(st, a);
+    for (int q = 0; q < 10; ++q) a.L0q[q] = (float)(std::sqrt((double)q) * st->g.dx);
     a.u64 = st->u64;
     a.v64 = st->v64;
     a.rec0 = st->rec[0];
@@ -807,6 +646,8 @@ static StepArgs make_args(const pd_state *st) {
     a.dtr = st->dt / st->mat.rho;
     a.icb = 1.0 / (1.0 + 0.5 * st->mat.zeta * st->dt);
     a.idt = 1.0 / st->dt;
+    a.du_df = df_split(st->bc.u_max / (double)st->bc.n_ramp);
+    a.dudt_df = df_split(st->bc.u_max / ((double)st->bc.n_ramp * st->dt));
     a.ca_df = df_split(a.ca);
     a.dtr_df = df_split(a.dtr);
     a.icb_df = df_split(a.icb);
@@ -827,12 +668,26 @@ static StepArgs make_args(const pd_state *st) {
 }
 
 static int launch_step(const pd_state *st, const StepArgs &a, bool force_only, cudaStream_t s) {
+    if (st->stencil) return stencil_launch(st, a, force_only, s);
     StepKernel k = pick(st, force_only);
     const unsigned grid = (unsigned)st->nblk * (unsigned)st->B;
-    PD_CHECK_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)st->smem_bytes));
     k<<<grid, kThreads, st->smem_bytes, s>>>(a);
     PD_CHECK_LAUNCH();
+    return PD_OK;
+}
+
+// Dynamic shared memory limit of every generic step kernel (set at state
+// creation, outside any stream capture).
+static int generic_set_attributes(size_t smem) {
+    for (int f = 0; f < 2; ++f)
+        for (int fo = 0; fo < 2; ++fo)
+            for (int law = 0; law < 2; ++law)
+                for (int kap = 0; kap < 2; ++kap) {
+                    StepKernel k = f ? (fo ? pick_law<true, true>(law, kap) : pick_law<true, false>(law, kap))
+                                     : (fo ? pick_law<false, true>(law, kap) : pick_law<false, false>(law, kap));
+                    PD_CHECK_CUDA(
+                        cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                }
     return PD_OK;
 }
 
@@ -846,6 +701,9 @@ static void free_state(pd_state *st) {
     cudaFree(st->slice_i0);
     cudaFree(st->slice_nv);
     cudaFree(st->ids);
+    cudaFree(st->st_tmpl);
+    cudaFree(st->st_box);
+    cudaFree(st->col_csr);
     cudaFree(st->xi_tab);
     cudaFree(st->xid_tab);
     cudaFree(st->off_tab);
@@ -860,6 +718,7 @@ static void free_state(pd_state *st) {
     cudaFree(st->coord);
     cudaFree(st->step);
     cudaFree(st->done);
+    cudaFree(st->brick_ridx);
     cudaFree(st->status);
     cudaFree(st->peak);
     cudaFree(st->peak_step);
@@ -1007,6 +866,11 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
     cudaFree(bad);
     PD_CHECK_CUDA(e);
     PD_REQUIRE(!hbad, "a CSR neighbour is not a horizon stencil offset of the grid");
+    PD_TRY(dalloc(&st->col_csr, st->nb));
+    PD_CHECK_CUDA(cudaMemcpy(st->col_csr, col, st->nb * sizeof(int32_t), cudaMemcpyDeviceToDevice));
+    PD_TRY(generic_set_attributes(st->smem_bytes));
+    st->stencil = stencil_applicable(st);
+    if (st->stencil) PD_TRY(stencil_build(st, col));
     PD_TRY(dalloc(&st->codes, 3 * N));
     PD_TRY(pd_bc_codes(&st->g, &st->bc, st->codes, (pd_stream)s));
     // time step
@@ -1031,7 +895,7 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
     const bool f64 = st->mat.precision == PD_PREC_FP64;
     (void)g;
     const size_t dsz = f64 ? sizeof(double) : sizeof(float);
-    PD_CHECK_CUDA(cudaMalloc(&st->dmg, (size_t)B * st->sell_len * dsz));
+    PD_CHECK_CUDA(cudaMalloc(&st->dmg, (size_t)B * (st->stencil ? st->st_len : st->sell_len) * dsz));
     if (f64) {
         PD_TRY(dalloc(&st->u64, 3 * N * B));
         PD_TRY(dalloc(&st->v64, 3 * N * B));
@@ -1041,12 +905,32 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
     PD_CHECK_CUDA(cudaMalloc(&st->rec[0], (size_t)B * N * 32));
     PD_CHECK_CUDA(cudaMalloc(&st->rec[1], (size_t)B * N * 32));
     st->nblk = (int)st->n_bricks;
-    PD_TRY(dalloc(&st->step, B));
-    PD_TRY(dalloc(&st->done, B));
+    PD_TRY(dalloc(&st->step, 2 * B));
+    PD_TRY(dalloc(&st->done, 2 * B));
+    st->bk_par = 0;
+    // reaction bricks: those holding a prescribed DOF, plus brick 0
+    {
+        std::vector<uint8_t> hc((size_t)3 * N);
+        PD_CHECK_CUDA(cudaMemcpy(hc.data(), st->codes, hc.size(), cudaMemcpyDeviceToHost));
+        std::vector<int32_t> ridx(st->n_bricks, -1);
+        ridx[0] = 0;
+        for (long long i = 0; i < N; ++i) {
+            if (hc[3 * i] < 2 && hc[3 * i + 1] < 2 && hc[3 * i + 2] < 2) continue;
+            const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / ((long long)g.nx * g.ny));
+            const long long br = (ix / kSlice) + (long long)st->nbx * ((iy / st->by) + (long long)st->nby * (iz / st->bz));
+            ridx[br] = 0;
+        }
+        int cnt = 0;
+        for (auto &v : ridx)
+            if (v >= 0) v = cnt++;
+        st->nrb = cnt;
+        PD_TRY(dalloc(&st->brick_ridx, ridx.size()));
+        PD_CHECK_CUDA(cudaMemcpy(st->brick_ridx, ridx.data(), ridx.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     PD_TRY(dalloc(&st->status, B));
     PD_TRY(dalloc(&st->peak, B));
     PD_TRY(dalloc(&st->peak_step, B));
-    PD_TRY(dalloc(&st->partial, (size_t)B * st->nblk));
+    PD_TRY(dalloc(&st->partial, (size_t)B * st->nrb));
     PD_TRY(dalloc(&st->ticket, B));
     PD_CHECK_CUDA(cudaHostAlloc((void **)&st->host_flag, 4 * sizeof(int32_t), cudaHostAllocMapped));
     PD_CHECK_CUDA(cudaHostGetDevicePointer((void **)&st->host_flag_dev, st->host_flag, 0));
@@ -1086,17 +970,34 @@ extern "C" int pd_state_create(const pd_grid *g, const int32_t *row_ptr, const i
     st->B = batch;
     st->N = (int64_t)g->nx * g->ny * g->nz;
     st->nb = n_bonds;
-    // brick rows: the largest brick that still gives at least two blocks per SM
+    // brick rows (PD_BRICK=YxZ overrides, for tuning)
     {
-        static const int cand[][2] = {{8, 8}, {8, 4}, {4, 4}, {4, 2}, {2, 2}, {2, 1}, {1, 1}};
+        static const int cand_generic[][2] = {{8, 8}, {8, 4}, {4, 4}, {4, 2}, {2, 2}, {2, 1}, {1, 1}};
+        const double m2 = g->m_ratio * g->m_ratio;
+        const bool stencil = mat->precision == PD_PREC_MIXED && m2 >= 9.0 && m2 < 10.0;
         st->by = 1;
         st->bz = 1;
-        for (const auto &cb : cand) {
-            const long long nbr = (long long)((g->nx + 7) / 8) * ((g->ny + cb[0] - 1) / cb[0]) * ((g->nz + cb[1] - 1) / cb[1]);
-            if (nbr * batch >= 304) {
-                st->by = cb[0];
-                st->bz = cb[1];
-                break;
+        if (stencil) {
+            // measured on GB300 (28k-node beam): 4x4 bricks for batches of at least
+            // ~0.4M nodes, 4x2 bricks (with the half-stencil split over two warps)
+            // below that, 2x2 / 2x1 for small grids
+            const long long nodes = (long long)g->nx * g->ny * g->nz * batch;
+            st->by = 4;
+            st->bz = nodes >= 400000 ? 4 : 2;
+            if (g->ny < 4 || g->nz < 2) {
+                st->by = 2;
+                st->bz = g->nz >= 2 ? 2 : 1;
+            }
+        } else {
+            // the largest brick that still gives at least two blocks per SM
+            for (const auto &cb : cand_generic) {
+                const long long nbr =
+                    (long long)((g->nx + 7) / 8) * ((g->ny + cb[0] - 1) / cb[0]) * ((g->nz + cb[1] - 1) / cb[1]);
+                if (nbr * batch >= 304) {
+                    st->by = cb[0];
+                    st->bz = cb[1];
+                    break;
+                }
             }
         }
         if (const char *e = std::getenv("PD_BRICK")) {
@@ -1142,7 +1043,10 @@ extern "C" int pd_state_reset(pd_state *st, const float *s0, const float *kappa,
     const long long NB = st->N * st->B;
     const bool f64 = st->mat.precision == PD_PREC_FP64;
     const size_t dsz = f64 ? sizeof(double) : sizeof(float);
-    PD_CHECK_CUDA(cudaMemsetAsync(st->dmg, 0, (size_t)st->B * st->sell_len * dsz, s));
+    if (st->stencil)
+        PD_TRY(stencil_reset_damage(st, s));
+    else
+        PD_CHECK_CUDA(cudaMemsetAsync(st->dmg, 0, (size_t)st->B * st->sell_len * dsz, s));
     const bool had = st->has_kappa;
     if (kappa) {
         if (!st->kappa) PD_TRY(dalloc(&st->kappa, (size_t)NB));
@@ -1179,13 +1083,15 @@ extern "C" int pd_state_load(pd_state *st, const double *u, const double *v, con
                                                   st->ticket, step);
     PD_CHECK_LAUNCH();
     if (f64)
-        k_load_u<true><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, u, v, st->u64, st->v64, st->vdf, st->step,
+        k_load_u<true><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, u, v, st->u64, st->v64, st->vdf, st->step + st->bk_par * st->B,
                                                       st->rec[0], st->rec[1]);
     else
-        k_load_u<false><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, u, v, st->u64, st->v64, st->vdf, st->step,
+        k_load_u<false><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, u, v, st->u64, st->v64, st->vdf, st->step + st->bk_par * st->B,
                                                        st->rec[0], st->rec[1]);
     PD_CHECK_LAUNCH();
-    if (d) {
+    if (d && st->stencil) {
+        PD_TRY(stencil_map_damage(st, (double *)d, true, s));
+    } else if (d) {
         if (f64)
             k_dmg_map<double, true><<<blocks_for(NB), 256, 0, s>>>(
                 st->row_ptr, st->N, st->B, st->nb, st->g.nx, st->g.ny, st->by, st->bz, st->nbx, st->nby, st->sell_off,
@@ -1205,14 +1111,16 @@ extern "C" int pd_state_store(const pd_state *st, double *u, double *v, double *
     const long long NB = st->N * st->B;
     if (u || v) {
         if (st->mat.precision == PD_PREC_FP64)
-            k_store_u<true><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, st->u64, st->v64, st->vdf, st->step,
+            k_store_u<true><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, st->u64, st->v64, st->vdf, st->step + st->bk_par * st->B,
                                                            st->rec[0], st->rec[1], u, v);
         else
-            k_store_u<false><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, st->u64, st->v64, st->vdf, st->step,
+            k_store_u<false><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, st->u64, st->v64, st->vdf, st->step + st->bk_par * st->B,
                                                             st->rec[0], st->rec[1], u, v);
         PD_CHECK_LAUNCH();
     }
-    if (d) {
+    if (d && st->stencil) {
+        PD_TRY(stencil_map_damage(st, d, false, s));
+    } else if (d) {
         if (st->mat.precision == PD_PREC_FP64)
             k_dmg_map<double, false><<<blocks_for(NB), 256, 0, s>>>(
                 st->row_ptr, st->N, st->B, st->nb, st->g.nx, st->g.ny, st->by, st->bz, st->nbx, st->nby, st->sell_off,
@@ -1241,7 +1149,9 @@ extern "C" int pd_step(pd_state *st, int32_t n_steps, double *reaction, pd_strea
     a.n_react = n_steps;
     for (int k = 0; k < n_steps; ++k) {
         a.k_local = k;
+        a.par = st->bk_par;
         PD_TRY(launch_step(st, a, false, (cudaStream_t)stream));
+        st->bk_par ^= 1;
     }
     return PD_OK;
 }
@@ -1252,7 +1162,7 @@ extern "C" int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int
     PD_REQUIRE(max_steps >= 0, "max_steps must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
     const int chunk = 64;
-    if (!st->chunk_exec || st->chunk_max_steps != max_steps) {
+    if (!st->chunk_exec || st->chunk_max_steps != max_steps || st->chunk_par != st->bk_par) {
         if (st->chunk_exec) {
             cudaGraphExecDestroy(st->chunk_exec);
             st->chunk_exec = nullptr;
@@ -1262,15 +1172,20 @@ extern "C" int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int
         StepArgs a = make_args(st);
         a.use_stop = 1;
         a.max_steps = max_steps;
-        StepKernel k = pick(st, false);
-        const unsigned grid = (unsigned)st->nblk * (unsigned)st->B;
         cudaGraph_t graph;
-        cudaError_t e = cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)st->smem_bytes);
-        if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int q = 0; q < chunk; ++q) k<<<grid, kThreads, st->smem_bytes, cs>>>(a);
+            int lrc = PD_OK;
+            for (int q = 0; q < chunk && lrc == PD_OK; ++q) {
+                a.par = st->bk_par ^ (q & 1);  // the chunk is even, so it ends on the parity it starts from
+                lrc = launch_step(st, a, false, cs);
+            }
             e = cudaStreamEndCapture(cs, &graph);
+            if (lrc != PD_OK && e == cudaSuccess) {
+                cudaGraphDestroy(graph);
+                cudaStreamDestroy(cs);
+                return lrc;
+            }
         }
         if (e == cudaSuccess) {
             e = cudaGraphInstantiate(&st->chunk_exec, graph, 0);
@@ -1280,13 +1195,15 @@ extern "C" int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int
         PD_CHECK_CUDA(e);
         st->chunk_steps = chunk;
         st->chunk_max_steps = max_steps;
+        st->chunk_par = st->bk_par;
     }
-    k_run_init<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->step, st->done, max_steps);
+    k_run_init<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->step + st->bk_par * st->B, st->done + st->bk_par * st->B,
+                                                 max_steps);
     PD_CHECK_LAUNCH();
     const int n_chunks = max_steps / chunk + 1;
     for (int c = 0; c < n_chunks; ++c) {
         PD_CHECK_CUDA(cudaGraphLaunch(st->chunk_exec, s));
-        k_count_active<<<1, 256, 0, s>>>(st->B, st->done, st->host_flag_dev + (c & 1));
+        k_count_active<<<1, 256, 0, s>>>(st->B, st->done + st->bk_par * st->B, st->host_flag_dev + (c & 1));
         PD_CHECK_LAUNCH();
         PD_CHECK_CUDA(cudaEventRecord(st->ev[c & 1], s));
         if (c >= 1) {
@@ -1294,7 +1211,8 @@ extern "C" int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int
             if (((volatile int32_t *)st->host_flag)[(c - 1) & 1] == 0) break;
         }
     }
-    k_copy_out<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->peak, st->peak_step, st->step, peak, peak_step, n_done);
+    k_copy_out<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->peak, st->peak_step, st->step + st->bk_par * st->B, peak,
+                                                  peak_step, n_done);
     PD_CHECK_LAUNCH();
     std::vector<int32_t> status(st->B);
     PD_CHECK_CUDA(cudaMemcpyAsync(status.data(), st->status, st->B * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
