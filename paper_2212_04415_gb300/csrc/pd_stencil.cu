@@ -30,6 +30,7 @@ namespace pdi {
 namespace {
 
 constexpr int kHalf = 61;            // positive half of the 122-offset stencil
+constexpr int kRounds = 64;          // half-stencil padded to 64 (entries 61..63 point at the node itself)
 constexpr int kHalo = 3;             // largest offset component
 constexpr int kWx = kSlice + 2 * kHalo;
 
@@ -54,65 +55,77 @@ __host__ __device__ constexpr I3 half_off(int m) {
     return I3{0, 0, 0};
 }
 
-// Bonds [m0, m1) of the half-stencil for one lane: a rolled loop over groups
-// of 8 bonds (small code, so the instruction cache holds it), the stencil
-// entry of a bond read from shared memory at a warp-uniform index
-// (broadcast), the next group's damage words requested while the current
-// group computes, FP32 sums per group added to a compensated (TwoSum)
-// accumulator. Sub-lane sign sig = +1 takes offset +k, sig = -1 takes -k: the
-// same instructions on exactly negated xi.
+// One bond of this lane: stencil entry m of the lane's sign table (xi, |xi|
+// and the byte offset of the neighbour's staged record), damage d.
 template <int LAW, bool KAPPA>
-__device__ __forceinline__ void bond_span(int m0, int m1, const float4 *s_tab, const int *s_loff,
-                                          const float4 *shi, const float4 *slo, float4 hi, float4 lo, float *dm,
-                                          float sig, int isig, float cV, float sr, float kf, float af, float i1,
+__device__ __forceinline__ void stencil_bond(int m, float d, const float4 *tab, const int *offb, const char *own,
+                                             float4 hi, float4 lo, float *dm, float cV, float sr, float kf, float af,
+                                             float i1, float i2, float &px, float &py, float &pz) {
+    const float4 k = tab[m];
+    const char *rj = own + offb[m];
+    const float4 hj = *(const float4 *)rj;
+    const float4 lj = *(const float4 *)(rj + 16);
+    const float ex = (hj.x - hi.x) + (lj.x - lo.x);
+    const float ey = (hj.y - hi.y) + (lj.y - lo.y);
+    const float ez = (hj.z - hi.z) + (lj.z - lo.z);
+    const float yx = k.x + ex, yy = k.y + ey, yz = k.z + ez;
+    const float y2 = yx * yx + yy * yy + yz * yz;
+    const float rL = rsqrtf(y2);
+    const float L = y2 * rL;
+    const float s = __fdividef(2.0f * (k.x * ex + k.y * ey + k.z * ez) + (ex * ex + ey * ey + ez * ez), k.w * (L + k.w));
+    const float s0 = 0.5f * (hi.w + hj.w);
+    if (s > s0) {
+        const float dl = law_damage<float>(LAW, s, s0, sr * s0, kf, af, i1, i2);
+        if (dl > d) {
+            d = dl;
+            dm[32 * m] = d;
+        }
+    }
+    float cv = cV;
+    if (KAPPA) cv = cV * 0.5f * (lo.w + lj.w);
+    const float gg = cv * (1.0f - d) * s * rL;
+    px = fmaf(gg, yx, px);
+    py = fmaf(gg, yy, py);
+    pz = fmaf(gg, yz, pz);
+}
+
+// Bonds [m0, m0 + 8 G) of the padded half-stencil for one lane, in groups of
+// 8: the FP32 sum of a group is added to the compensated (TwoSum)
+// accumulator, and the next group's damage words are requested while the
+// current group computes (two register sets in turn). The sign tables hold
+// xi = +k dx for sub-lane 0 and -k dx for sub-lane 1 (exact negations), so
+// both directed copies of a bond run the same instructions on negated operands.
+template <int G, int LAW, bool KAPPA>
+__device__ __forceinline__ void bond_span(int m0, const float4 *tab, const int *offb, const char *own, float4 hi,
+                                          float4 lo, float *dm, float cV, float sr, float kf, float af, float i1,
                                           float i2, float *acc) {
-    float cur[8], nxt[8];
+    static_assert(G % 2 == 0, "even number of groups");
+    float da[8], db[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) cur[u] = (m0 + u < m1) ? dm[32 * (m0 + u)] : 0.f;
-    for (int g = m0; g < m1; g += 8) {
+    for (int u = 0; u < 8; ++u) da[u] = dm[32 * (m0 + u)];
+#pragma unroll 1
+    for (int g = 0; g < G; g += 2) {
+        const int ma = m0 + 8 * g, mb = ma + 8;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) nxt[u] = (g + 8 + u < m1) ? dm[32 * (g + 8 + u)] : 0.f;
+        for (int u = 0; u < 8; ++u) db[u] = dm[32 * (mb + u)];
         float px = 0.f, py = 0.f, pz = 0.f;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int m = g + u;
-            if (m < m1) {
-                const float4 k = s_tab[m];  // xi of +k (x, y, z) and |xi|
-                const int off = isig * s_loff[m];
-                const float4 hj = shi[off];
-                const float4 lj = slo[off];
-                const float xx = sig * k.x, xy = sig * k.y, xz = sig * k.z;
-                const float ex = (hj.x - hi.x) + (lj.x - lo.x);
-                const float ey = (hj.y - hi.y) + (lj.y - lo.y);
-                const float ez = (hj.z - hi.z) + (lj.z - lo.z);
-                const float yx = xx + ex, yy = xy + ey, yz = xz + ez;
-                const float y2 = yx * yx + yy * yy + yz * yz;
-                const float rL = rsqrtf(y2);
-                const float L = y2 * rL;
-                const float s = __fdividef(2.0f * (xx * ex + xy * ey + xz * ez) + (ex * ex + ey * ey + ez * ez),
-                                           k.w * (L + k.w));
-                const float s0 = 0.5f * (hi.w + hj.w);
-                float d = cur[u];
-                if (s > s0) {
-                    const float dl = law_damage<float>(LAW, s, s0, sr * s0, kf, af, i1, i2);
-                    if (dl > d) {
-                        d = dl;
-                        dm[32 * m] = d;
-                    }
-                }
-                float cv = cV;
-                if (KAPPA) cv = cV * 0.5f * (lo.w + lj.w);
-                const float gg = cv * (1.0f - d) * s * rL;
-                px = fmaf(gg, yx, px);
-                py = fmaf(gg, yy, py);
-                pz = fmaf(gg, yz, pz);
-            }
-        }
+        for (int u = 0; u < 8; ++u)
+            stencil_bond<LAW, KAPPA>(ma + u, da[u], tab, offb, own, hi, lo, dm, cV, sr, kf, af, i1, i2, px, py, pz);
         two_sum_acc(acc[0], acc[3], px);
         two_sum_acc(acc[1], acc[4], py);
         two_sum_acc(acc[2], acc[5], pz);
+        if (g + 2 < G) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) cur[u] = nxt[u];
+            for (int u = 0; u < 8; ++u) da[u] = dm[32 * (mb + 8 + u)];
+        }
+        px = py = pz = 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            stencil_bond<LAW, KAPPA>(mb + u, db[u], tab, offb, own, hi, lo, dm, cV, sr, kf, af, i1, i2, px, py, pz);
+        two_sum_acc(acc[0], acc[3], px);
+        two_sum_acc(acc[1], acc[4], py);
+        two_sum_acc(acc[2], acc[5], pz);
     }
 }
 
@@ -124,8 +137,8 @@ __global__ void __launch_bounds__(512, 2) k_step_stencil(const StepArgs a) {
     __shared__ float2 red[16];
     __shared__ float s_pre[4];  // U(n+1) and the prescribed velocity, double-float
     __shared__ unsigned s_cnt;
-    __shared__ float4 s_tab[kHalf];
-    __shared__ int s_loff[kHalf];
+    __shared__ float4 s_tab[2][kRounds];  // per sub-lane sign: xi (x, y, z) and |xi|
+    __shared__ int s_offb[2][kRounds];    // per sign: byte offset of the neighbour's staged record
 
     const int nwarps = blockDim.x >> 5;
     const int wpb = a.st_wpb;
@@ -152,11 +165,19 @@ __global__ void __launch_bounds__(512, 2) k_step_stencil(const StepArgs a) {
     const size_t BN = (size_t)a.B * a.N;
     const int Wy = a.BY + 2 * kHalo, Wz = a.BZ + 2 * kHalo;
     const int Wtot = kWx * Wy * Wz;
-    float4 *s_hi = s_rec, *s_lo = s_rec + Wtot;
     float *s_part = (float *)(s_rec + 2 * Wtot);  // [Q-1][wpb][16][6]
-    for (int m = threadIdx.x; m < kHalf; m += blockDim.x) {
-        s_tab[m] = a.half_tab[m];
-        s_loff[m] = a.half_off[0][m] + kWx * a.half_off[1][m] + kWx * Wy * a.half_off[2][m];
+    for (int m = threadIdx.x; m < kRounds; m += blockDim.x) {
+        if (m < kHalf) {
+            const float4 k = a.half_tab[m];
+            const int lo_ = a.half_off[0][m] + kWx * a.half_off[1][m] + kWx * Wy * a.half_off[2][m];
+            s_tab[0][m] = k;
+            s_tab[1][m] = make_float4(-k.x, -k.y, -k.z, k.w);
+            s_offb[0][m] = 32 * lo_;
+            s_offb[1][m] = -32 * lo_;
+        } else {  // padding: the node itself (zero stretch, zero force)
+            s_tab[0][m] = s_tab[1][m] = make_float4(a.dxf, 0.f, 0.f, a.dxf);
+            s_offb[0][m] = s_offb[1][m] = 0;
+        }
     }
     const float4 *rhi = (const float4 *)((n & 1) ? a.rec1 : a.rec0) + (size_t)b * a.N;
     const float4 *rlo = rhi + BN;
@@ -168,8 +189,8 @@ __global__ void __launch_bounds__(512, 2) k_step_stencil(const StepArgs a) {
             const int gx = x0 - kHalo + lx, gy = y0 - kHalo + ly, gz = z0 - kHalo + lz;
             const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz;
             const int gi = in ? gx + a.nx * (gy + a.ny * gz) : 0;
-            cp_async16(s_hi + q, rhi + gi, in ? 16 : 0);
-            cp_async16(s_lo + q, rlo + gi, in ? 16 : 0);
+            cp_async16(s_rec + 2 * q, rhi + gi, in ? 16 : 0);  // records interleaved: hi, lo
+            cp_async16(s_rec + 2 * q + 1, rlo + gi, in ? 16 : 0);
         }
         cp_async_wait_all();
     }
@@ -187,15 +208,14 @@ __global__ void __launch_bounds__(512, 2) k_step_stencil(const StepArgs a) {
     const size_t node = (size_t)b * a.N + ii;
     const int il = (kHalo + c) + kWx * ((kHalo + ly) + Wy * (kHalo + lz));
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sx, sy, sz, cx, cy, cz
-    const float4 hi = s_hi[il], lo = s_lo[il];
+    const float4 hi = s_rec[2 * il], lo = s_rec[2 * il + 1];
     if (!done) {
         if (own) {
-            constexpr int R = (kHalf + Q - 1) / Q;
-            const int m0 = part * R, m1 = min(kHalf, m0 + R);
-            float *dm = (float *)a.dmg + (size_t)b * a.sell_len + ((size_t)brick * wpb + rp) * (kHalf * 32) + lane;
-            bond_span<LAW, KAPPA>(m0, m1, s_tab, s_loff, s_hi + il, s_lo + il, hi, lo, dm, t ? -1.0f : 1.0f,
-                                  t ? -1 : 1, (float)a.cV, (float)a.s_ratio, (float)a.k, (float)a.alpha,
-                                  (float)a.inv_1mek, (float)a.inv_1pa, acc);
+            constexpr int R = kRounds / Q;
+            float *dm = (float *)a.dmg + (size_t)b * a.sell_len + ((size_t)brick * wpb + rp) * (kRounds * 32) + lane;
+            bond_span<R / 8, LAW, KAPPA>(part * R, s_tab[t], s_offb[t], (const char *)(s_rec + 2 * il), hi, lo, dm,
+                                         (float)a.cV, (float)a.s_ratio, (float)a.k, (float)a.alpha,
+                                         (float)a.inv_1mek, (float)a.inv_1pa, acc);
         }
         // add the two sub-lane partials in double-float (TwoSum is exact, so
         // both sub-lanes end with the same total)
@@ -275,7 +295,7 @@ __device__ __forceinline__ long long slot_of(int i, int code, int nx, int ny, in
     const int row = (iy % BY) + BY * (iz % BZ);
     const int w = row >> 1, rr = row & 1, c = ix % kSlice;
     const int m = code >> 1, t = code & 1;
-    return ((brick * wpb + w) * kHalf + m) * 32 + (16 * t + 8 * rr + c);
+    return ((brick * wpb + w) * kRounds + m) * 32 + (16 * t + 8 * rr + c);
 }
 
 // code of the CSR neighbour j of i: 2 m + t, or -1 if not a stencil offset
@@ -374,7 +394,7 @@ int stencil_set_attributes(size_t smem) {
 int stencil_build(pd_state *st, const int32_t *col) {
     const long long N = st->N;
     st->st_wpb = st->by * st->bz / 2;
-    st->st_len = st->n_bricks * st->st_wpb * (long long)kHalf * 32;
+    st->st_len = st->n_bricks * st->st_wpb * (long long)kRounds * 32;
     // split the half-stencil over Q warps when the mesh gives too few warps per SM
     // (measured on GB300: Q = 2 for single samples of the 28k-node beam, 1 for batches)
     const long long warps1 = st->n_bricks * st->B * st->st_wpb;
