@@ -250,7 +250,9 @@ typedef struct pd_mlmc_cfg {
     pd_material mat;
     pd_field_cfg field;
     uint64_t seed;
-    int32_t batch; /* samples per launch (<= 4096) */
+    int32_t batch;                /* samples per launch (<= 4096) */
+    const int64_t *first_sample;  /* [n_levels] id of the first sample of each level, or NULL (0): a
+                                     process of a sharded run takes ids first .. first + n - 1 */
 } pd_mlmc_cfg;
 
 typedef struct pd_mlmc_level {
@@ -274,9 +276,14 @@ typedef struct pd_mlmc_result {
 
 /* Host-synchronous; owns its own device buffers. q_fine/q_coarse (host,
  * optional) receive every sample's Q_l and Q_{l-1} level after level
- * (sum_l n_samples[l] entries; q_coarse entries of level 0 are 0). */
+ * (sum_l n_samples[l] entries; q_coarse entries of level 0 are 0).
+ * batch_sums (host, optional) receives, level after level and batch after
+ * batch, the GPU's FP64 (n, sum Y, sum Y^2) of every batch of `batch`
+ * consecutive samples: the level totals are these added in batch order, so
+ * the batch sums of processes that each took whole batches of a level merge
+ * (in sample order) to exactly the totals of a single-process run. */
 PD_API int mlmc_estimate(const pd_mlmc_cfg *cfg, pd_mlmc_result *out, double *q_fine,
-                  double *q_coarse, pd_stream stream);
+                  double *q_coarse, double *batch_sums, pd_stream stream);
 
 /* Optimal allocation N_l = floor(eps_s^-2 (sum_k sqrt(V_k C_k)) sqrt(V_l/C_l))
  * (Eq. sample_allocation), host arrays of length n_levels. */

@@ -50,7 +50,8 @@ class FieldCfg(C.Structure):
 class MlmcCfg(C.Structure):
     _fields_ = [("n_levels", C.c_int32), ("grid", C.POINTER(Grid)), ("bc", C.POINTER(BC)),
                 ("max_steps", C.POINTER(C.c_int32)), ("n_samples", C.POINTER(C.c_int64)),
-                ("mat", Material), ("field", FieldCfg), ("seed", C.c_uint64), ("batch", C.c_int32)]
+                ("mat", Material), ("field", FieldCfg), ("seed", C.c_uint64), ("batch", C.c_int32),
+                ("first_sample", C.POINTER(C.c_int64))]
 
 
 class MlmcLevel(C.Structure):
@@ -87,7 +88,7 @@ _SIGS = {
     "pd_field_destroy": (C.c_int, [_VP]),
     "pd_field_info": (C.c_int, [_VP, C.POINTER(C.c_int32), _VP]),
     "pd_sample_field": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, _VP, _VP, _VP]),
-    "mlmc_estimate": (C.c_int, [C.POINTER(MlmcCfg), C.POINTER(MlmcResult), _VP, _VP, _VP]),
+    "mlmc_estimate": (C.c_int, [C.POINTER(MlmcCfg), C.POINTER(MlmcResult), _VP, _VP, _VP, _VP]),
     "pd_mlmc_allocation": (C.c_int, [C.c_int32, _VP, _VP, C.c_double, _VP]),
 }
 
@@ -285,21 +286,28 @@ class Field:
 
 
 def mlmc_estimate(grids, bcs, max_steps, n_samples, mat, field, seed, batch, precision=PREC_MIXED,
-                  return_samples=False, stream=None):
-    """Fixed-allocation MLMC over len(grids) nested levels (coarsest first)."""
+                  first_sample=None, return_samples=False, stream=None):
+    """Fixed-allocation MLMC over len(grids) nested levels (coarsest first).
+
+    Returns per-level totals, the estimator, and the per-batch FP64 sums
+    (n, sum Y, sum Y^2) in batch order (``batch_sums``), which is what
+    ``shard.merge`` combines across processes."""
     import numpy as np
     L = len(grids)
     G = (Grid * L)(*[grid_struct(g) for g in grids])
     Bc = (BC * L)(*[bc_struct(b) for b in bcs])
     ms = (C.c_int32 * L)(*max_steps)
     ns = (C.c_int64 * L)(*n_samples)
-    cfg = MlmcCfg(L, G, Bc, ms, ns, material_struct(mat, precision), field_struct(field), seed, batch)
+    fs = (C.c_int64 * L)(*(first_sample if first_sample is not None else [0] * L))
+    cfg = MlmcCfg(L, G, Bc, ms, ns, material_struct(mat, precision), field_struct(field), seed, batch, fs)
     res = MlmcResult()
     tot = int(sum(n_samples))
+    nbat = [(n + min(batch, max(n, 1)) - 1) // min(batch, max(n, 1)) for n in n_samples]
     qf = np.zeros(max(tot, 1))
     qc = np.zeros(max(tot, 1))
+    bs = np.zeros((max(sum(nbat), 1), 3))
     _check(lib().mlmc_estimate(C.byref(cfg), C.byref(res), qf.ctypes.data_as(C.c_void_p),
-                               qc.ctypes.data_as(C.c_void_p), _stream(stream)))
+                               qc.ctypes.data_as(C.c_void_p), bs.ctypes.data_as(C.c_void_p), _stream(stream)))
     levels = []
     for l in range(L):
         lv = res.level[l]
@@ -307,6 +315,11 @@ def mlmc_estimate(grids, bcs, max_steps, n_samples, mat, field, seed, batch, pre
                            var_unbiased=lv.var_unbiased, cost_s=lv.cost_s, steps=lv.steps,
                            bond_updates=lv.bond_updates))
     out = dict(levels=levels, q_ml=res.q_ml, var_ml=res.var_ml)
+    o = 0
+    out["batch_sums"] = []
+    for l in range(L):
+        out["batch_sums"].append(bs[o:o + nbat[l]].copy())
+        o += nbat[l]
     if return_samples:
         out["q_fine"], out["q_coarse"] = qf[:tot], qc[:tot]
     return out

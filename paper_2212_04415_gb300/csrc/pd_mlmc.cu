@@ -3,6 +3,7 @@
 // sums on the GPU, the estimator Q_ML = sum_l Y_hat_l (Eq. MLMC_estimator),
 // the sample variance of Eq. sample_variance and the optimal allocation of
 // Eq. sample_allocation.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <vector>
@@ -82,7 +83,7 @@ struct Buffers {
 };
 
 static int run_level(const pd_mlmc_cfg *cfg, pd_field *field, int l, pd_mlmc_level *lv, double *q_fine,
-                     double *q_coarse, cudaStream_t s) {
+                     double *q_coarse, double *batch_sums, cudaStream_t s) {
     const int64_t n_total = cfg->n_samples[l];
     lv->n = 0;
     lv->sum_y = lv->sum_y2 = 0.0;
@@ -128,7 +129,8 @@ static int run_level(const pd_mlmc_cfg *cfg, pd_field *field, int l, pd_mlmc_lev
         }
         cudaStreamSynchronize(s);
         const auto t0 = std::chrono::steady_clock::now();
-        k_iota<<<(b + 255) / 256, 256, 0, s>>>((uint64_t)first, b, bf.ids);
+        const int64_t id0 = (cfg->first_sample ? cfg->first_sample[l] : 0) + first;
+        k_iota<<<(b + 255) / 256, 256, 0, s>>>((uint64_t)id0, b, bf.ids);
         if ((rc = pd_draw_xi(cfg->seed, l, bf.ids, b, K, bf.xi, (pd_stream)s))) break;
         if ((rc = pd_sample_field(field, l, bf.xi, b, bf.ff, l > 0 ? bf.fc : nullptr, (pd_stream)s))) break;
         if ((rc = pd_state_reset(sf, bf.ff, nullptr, (pd_stream)s))) break;
@@ -156,6 +158,12 @@ static int run_level(const pd_mlmc_cfg *cfg, pd_field *field, int l, pd_mlmc_lev
         lv->sum_y += sums[0];
         lv->sum_y2 += sums[1];
         lv->n += b;
+        if (batch_sums) {
+            const int64_t q = first / Bmax;
+            batch_sums[3 * q + 0] = (double)b;
+            batch_sums[3 * q + 1] = sums[0];
+            batch_sums[3 * q + 2] = sums[1];
+        }
         for (int q = 0; q < b; ++q) {
             lv->steps += hnd[q];
             lv->bond_updates += (int64_t)hnd[q] * mf.nb;
@@ -193,11 +201,15 @@ extern "C" int pd_mlmc_allocation(int32_t n_levels, const double *V, const doubl
 }
 
 extern "C" int mlmc_estimate(const pd_mlmc_cfg *cfg, pd_mlmc_result *out, double *q_fine, double *q_coarse,
-                             pd_stream stream) {
+                             double *batch_sums, pd_stream stream) {
     PD_REQUIRE(cfg && out, "cfg and out are required");
     PD_REQUIRE(cfg->n_levels >= 1 && cfg->n_levels <= PD_MAX_LEVELS, "n_levels out of range");
     PD_REQUIRE(cfg->grid && cfg->bc && cfg->max_steps && cfg->n_samples, "per-level arrays are required");
     PD_REQUIRE(cfg->batch >= 1 && cfg->batch <= 4096, "batch must be in [1, 4096]");
+    for (int l = 0; l < cfg->n_levels; ++l) {
+        PD_REQUIRE(cfg->n_samples[l] >= 0, "n_samples[%d] is negative", l);
+        PD_REQUIRE(!cfg->first_sample || cfg->first_sample[l] >= 0, "first_sample[%d] is negative", l);
+    }
     for (int l = 1; l < cfg->n_levels; ++l) {
         const pd_grid &f = cfg->grid[l], &c = cfg->grid[l - 1];
         PD_REQUIRE(f.nx == 2 * c.nx && f.ny == 2 * c.ny && f.nz == 2 * c.nz &&
@@ -211,11 +223,13 @@ extern "C" int mlmc_estimate(const pd_mlmc_cfg *cfg, pd_mlmc_result *out, double
     memset(&r, 0, sizeof(r));
     r.n_levels = cfg->n_levels;
     int rc = PD_OK;
-    int64_t off = 0;
+    int64_t off = 0, boff = 0;
     for (int l = 0; l < cfg->n_levels && rc == PD_OK; ++l) {
         rc = run_level(cfg, field, l, &r.level[l], q_fine ? q_fine + off : nullptr,
-                       q_coarse ? q_coarse + off : nullptr, s);
+                       q_coarse ? q_coarse + off : nullptr, batch_sums ? batch_sums + 3 * boff : nullptr, s);
         off += cfg->n_samples[l];
+        const int64_t bl = std::min<int64_t>(cfg->batch, std::max<int64_t>(cfg->n_samples[l], 1));
+        boff += (cfg->n_samples[l] + bl - 1) / bl;
     }
     pd_field_destroy(field);
     if (rc != PD_OK) return rc;

@@ -161,6 +161,26 @@ def beam_levels():
     return out
 
 
+def small_beam_levels():
+    """A two-level hierarchy of a small notched beam (80 x 25 x 10 mm, span 2.5 D,
+    notch 0.2 D) at dx = 5 / 2.5 mm, for MLMC parity against the oracle:
+    N_l = 6 / 4 samples, 600 / 1200 steps, the ramp scaled as in ``beam_levels``."""
+    D, L, T = 25.0, 80.0, 10.0
+    out = []
+    for lvl, (dxm, nl) in enumerate(((5.0, 6), (2.5, 4))):
+        n_steps = 600 * (2 ** lvl)
+        g = _beam_grid(D, dxm, L, T, True)
+        span = 2.5 * D
+        sx = ((L - span) / 2.0, (L + span) / 2.0)
+        bc = BC(BC_BEAM_3PT, u_max=2.5e-5, n_ramp=n_steps,
+                support_x2=(round(2 * sx[0] / dxm), round(2 * sx[1] / dxm)),
+                load_x2=round(2 * (L / 2.0) / dxm))
+        mat = Material(E=30e9, law=LAW_BILINEAR, s0=1e-4, s_ratio=10.0, zeta=5e4)
+        fld = FieldCfg(COV_SQEXP, 5e-3, 16, MARG_LOGNORMAL, 1e-4, 0.1)
+        out.append(Workload(f"small_beam_80x25x10_dx{dxm}mm", g, mat, bc, n_steps, fld, 3, batch=nl))
+    return out
+
+
 def sweep(D_mm: float, dx_mm: float = 2.5, n_steps: int = 5000) -> Workload:
     """Size-effect sweep member: depth D, span 3 D, length 3.5 D, thickness 50 mm."""
     L, T = 3.5 * D_mm, 50.0

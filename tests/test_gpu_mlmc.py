@@ -1,0 +1,110 @@
+"""MLMC estimator on the GPU against the oracle (Section 4): per-sample peak
+loads of the coupled fine / coarse pairs, the FP64 level sums, the estimator,
+and a two-shard run merged back to the single-run totals bit for bit."""
+import numpy as np
+import pytest
+
+import pd_workloads as W
+from oracle import core, field
+from oracle import mlmc as omlmc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pd(built_lib):
+    import paper_2212_04415_gb300 as pd
+    return pd
+
+
+def _args(levels, n_samples=None):
+    return dict(grids=[w.grid for w in levels], bcs=[w.bc for w in levels],
+                max_steps=[w.n_steps for w in levels],
+                n_samples=n_samples if n_samples is not None else [w.batch for w in levels],
+                mat=levels[0].mat, field=levels[0].field, seed=levels[0].seed)
+
+
+def _oracle_pairs(levels, l, ids):
+    """Q of the fine member (level l) and coarse member (level l-1) of each pair:
+    one Gaussian field on the finest grid from xi(seed, l, id), restricted down."""
+    f = levels[0].field
+    L = len(levels)
+    Phi, lam = field.kl_separable(levels[-1].grid, f.length, f.n_modes)
+    g = field.gaussian(Phi, lam, field.draw_xi(levels[0].seed, l, ids, f.n_modes))
+    for k in range(L - 1, l, -1):
+        g = field.restrict(g, levels[k].grid)
+    qf = core.run_batch(core.Model(levels[l]), field.lognormal(g, f.mean, f.cov), levels[l].n_steps)["peak"]
+    if l == 0:
+        return qf, np.zeros_like(qf)
+    gc = field.restrict(g, levels[l].grid)
+    qc = core.run_batch(core.Model(levels[l - 1]), field.lognormal(gc, f.mean, f.cov),
+                        levels[l - 1].n_steps)["peak"]
+    return qf, qc
+
+
+def test_mlmc_estimate_against_oracle(pd):
+    levels = W.small_beam_levels()
+    a = _args(levels)
+    res = pd.mlmc_estimate(batch=4, return_samples=True, **a)  # level 0: batches of 4 and 2
+    off = 0
+    Yh, V = [], []
+    for l, n in enumerate(a["n_samples"]):
+        qf, qc = res["q_fine"][off:off + n], res["q_coarse"][off:off + n]
+        off += n
+        of, oc = _oracle_pairs(levels, l, list(range(n)))
+        scale = np.abs(of).max()
+        print(f"level {l}: Qf {qf} vs {of}; Qc {qc} vs {oc}")
+        assert np.all(np.abs(qf - of) <= 1e-3 * np.abs(of))
+        assert np.all(np.abs(qc - oc) <= 1e-3 * np.maximum(np.abs(oc), 1e-30))
+        lv = res["levels"][l]
+        y = qf - qc
+        assert lv["n"] == n
+        # the GPU's FP64 level sums of its own samples (summation order differs: 1e-12)
+        assert lv["sum_y"] == pytest.approx(y.sum(), rel=1e-12, abs=1e-12 * scale * n)
+        assert lv["sum_y2"] == pytest.approx((y * y).sum(), rel=1e-12)
+        mean, var_b, _ = omlmc.level_stats(of - oc)
+        assert abs(lv["mean"] - mean) <= 2e-3 * scale
+        Yh.append(mean)
+        V.append(var_b)
+        assert lv["steps"] > 0 and lv["bond_updates"] > 0
+    q, _ = omlmc.mlmc_estimate(Yh, V, a["n_samples"])
+    assert abs(res["q_ml"] - q) <= 2e-3 * abs(q)
+    # the estimator is the sum of the level means; its variance sum_l V_l / N_l
+    assert res["q_ml"] == pytest.approx(sum(lv["mean"] for lv in res["levels"]), rel=1e-14)
+    assert res["var_ml"] == pytest.approx(sum(lv["var"] / lv["n"] for lv in res["levels"]), rel=1e-14)
+
+
+def test_mlmc_two_shards_merge_to_the_single_run(pd):
+    from paper_2212_04415_gb300 import shard
+    levels = W.small_beam_levels()
+    a = _args(levels, n_samples=[5, 3])
+    batch = 2
+    one = pd.mlmc_estimate(batch=batch, return_samples=True, **a)
+    parts = []
+    for r in range(2):
+        first, count = shard.split(a["n_samples"], batch, 2, r)
+        b = dict(a, n_samples=count)
+        parts.append((first, count, pd.mlmc_estimate(batch=batch, first_sample=first, return_samples=True, **b)))
+    merged = shard.merge([p[2]["batch_sums"] for p in parts])
+    for l in range(2):
+        for key in ("n", "sum_y", "sum_y2", "mean", "var"):
+            assert merged["levels"][l][key] == one["levels"][l][key]
+    assert merged["q_ml"] == one["q_ml"] and merged["var_ml"] == one["var_ml"]
+    # per-sample results do not depend on which process ran them
+    off_one = 0
+    offs = [0, 0]
+    for l, n in enumerate(a["n_samples"]):
+        got = []
+        for r, (first, count, res) in enumerate(parts):
+            got.append(res["q_fine"][offs[r]:offs[r] + count[l]])
+            offs[r] += count[l]
+        assert np.array_equal(np.concatenate(got), one["q_fine"][off_one:off_one + n])
+        off_one += n
+
+
+def test_mlmc_rejects_unnested_grids(pd):
+    levels = W.small_beam_levels()
+    a = _args(levels)
+    a["grids"] = [levels[0].grid, levels[0].grid]
+    with pytest.raises(pd.PdError, match="refinement"):
+        pd.mlmc_estimate(batch=4, **a)
