@@ -221,6 +221,9 @@ PD_API int pd_draw_xi(uint64_t seed, int32_t level, const uint64_t *sample_ids, 
  * size; the exponential kernel needs the dense covariance (finest N <= 4096). */
 PD_API int pd_field_create(const pd_grid *finest, int32_t n_levels, const pd_field_cfg *cfg,
                     pd_field **out);
+/* Synchronises the device; returns PD_ERR_TIMEOUT if a sampling launch of
+ * this field gave up waiting for its tile copies or MMAs (that tile was
+ * written as NaN). */
 PD_API int pd_field_destroy(pd_field *f);
 
 /* K and the KL eigenvalues (host double[K], may be NULL). */
@@ -229,7 +232,11 @@ PD_API int pd_field_info(const pd_field *f, int32_t *n_modes, double *lambda);
 /* Field of B samples on grid `level`: g = Phi diag(sqrt(lambda)) xi, then the
  * marginal transform (Section 5.2). node_field: device float[B][N_level].
  * coarse_field (level > 0, or NULL): the same samples on grid level-1, from
- * the 2x2x2 mean of the Gaussian field before the transform (Section 4.2). */
+ * the 2x2x2 mean of the Gaussian field before the transform (Section 4.2).
+ * The product runs on the tensor cores in split TF32 (FP32-class accuracy).
+ * A field's sampling calls must be ordered on one stream: each level keeps
+ * one scratch buffer for the split coefficients (grown, with a device
+ * synchronisation, when B exceeds every earlier call's). */
 PD_API int pd_sample_field(pd_field *f, int32_t level, const double *xi, int32_t B,
                     float *node_field, float *coarse_field, pd_stream stream);
 

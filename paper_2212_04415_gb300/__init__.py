@@ -259,11 +259,17 @@ class Field:
         self.sizes = [(finest.nx >> s, finest.ny >> s, finest.nz >> s) for s in range(n_levels - 1, -1, -1)]
 
     def close(self):
-        if getattr(self, "h", None):
-            lib().pd_field_destroy(self.h)
+        """Free the field; raises if a sampling launch had given up waiting (PD_ERR_TIMEOUT)."""
+        h = getattr(self, "h", None)
+        if h:
             self.h = None
+            _check(lib().pd_field_destroy(h))
 
-    __del__ = close
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.h = None
+            lib().pd_field_destroy(h)
 
     def eigenvalues(self):
         import numpy as np

@@ -72,6 +72,9 @@ struct StepArgs {
     double cV;  // micromodulus x node volume
     double V;
     double s_ratio, k, alpha, inv_1mek, inv_1pa;
+    // the same constants rounded to FP32 on the host: a conversion from FP64
+    // in the kernel would run on the FP64 pipe, which is narrow on this part
+    float cVf, s_ratio_f, k_f, alpha_f, inv_1mek_f, inv_1pa_f;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {

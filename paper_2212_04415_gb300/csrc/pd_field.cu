@@ -18,8 +18,9 @@
 //     FP64 and stored as FP32; every coarser level's basis is the 2x2x2 mean
 //     of the next finer one, so a coarse field equals the coarsened fine
 //     field of the same coefficients.
-// Sampling: g = Phi_l xi (FP32 multiply-add over K terms per node and
-// sample), then the marginal transform, written as FP32 node fields.
+// Sampling: g = Phi_l xi as a tensor-core GEMM (split TF32, FP32
+// accumulation; pd_kl.cu), then the marginal transform, written as FP32
+// node fields.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -33,6 +34,7 @@ struct pd_field {
     int32_t K;
     std::vector<double> lambda;
     float *phi[PD_MAX_LEVELS];  // [N_l][K], sqrt(lambda) folded in
+    KlOperand *kl[PD_MAX_LEVELS];  // the same, split into TF32 hi / lo, with TMA descriptors
 };
 
 namespace pdi {
@@ -239,46 +241,7 @@ __global__ void k_restrict_basis(int cnx, int cny, int cnz, int K, const float *
     coarse[t] = (yz0 + yz1) * 0.125f;
 }
 
-// node_field[b][i] = T(sum_k Phi[i][k] xi[b][k]) for a tile of samples.
-constexpr int kSampTile = 8;
 constexpr int kMaxK = 256;
-
-__global__ void __launch_bounds__(256) k_sample(long long N, int K, int B, const float *phi,
-                                                const double *xi, int marginal, double mu, double sig,
-                                                double wscale, double winvm, float *out) {
-    __shared__ float sx[kSampTile][kMaxK];
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    for (int b0 = 0; b0 < B; b0 += kSampTile) {
-        const int nb = min(kSampTile, B - b0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < nb * K; t += blockDim.x)
-            sx[t / K][t % K] = (float)xi[(size_t)(b0 + t / K) * K + (t % K)];
-        __syncthreads();
-        if (i < N) {
-            float acc[kSampTile];
-#pragma unroll
-            for (int q = 0; q < kSampTile; ++q) acc[q] = 0.0f;
-            const float *row = phi + (size_t)i * K;
-            for (int k = 0; k < K; ++k) {
-                const float p = __ldg(row + k);
-#pragma unroll
-                for (int q = 0; q < kSampTile; ++q) acc[q] = fmaf(p, sx[q][k], acc[q]);
-            }
-            for (int q = 0; q < nb; ++q) {
-                const double g = (double)acc[q];
-                double v;
-                if (marginal == PD_MARG_LOGNORMAL) {
-                    v = exp(mu + sig * g);
-                } else {
-                    // Weibull copula: F_W^-1(Phi(g)), upper tail via erfc for accuracy
-                    const double q1 = 0.5 * erfc(g / 1.4142135623730951);  // 1 - Phi(g)
-                    v = wscale * pow(-log(q1), winvm);
-                }
-                out[(size_t)(b0 + q) * N + i] = (float)v;
-            }
-        }
-    }
-}
 
 }  // namespace pdi
 
@@ -298,7 +261,10 @@ extern "C" int pd_draw_xi(uint64_t seed, int32_t level, const uint64_t *sample_i
 
 static void free_field(pd_field *f) {
     if (!f) return;
-    for (int l = 0; l < PD_MAX_LEVELS; ++l) cudaFree(f->phi[l]);
+    for (int l = 0; l < PD_MAX_LEVELS; ++l) {
+        cudaFree(f->phi[l]);
+        kl_operand_destroy(f->kl[l]);
+    }
     delete f;
 }
 
@@ -396,6 +362,10 @@ static int build_field(pd_field *f) {
         k_restrict_basis<<<(unsigned)((Nc * K + 255) / 256), 256>>>(c.nx, c.ny, c.nz, K, f->phi[l + 1], f->phi[l]);
         PD_CHECK_LAUNCH();
     }
+    for (int l = 0; l < f->n_levels; ++l) {
+        const pd_grid &c = f->grid[l];
+        PD_TRY(kl_operand_create(f->phi[l], (long long)c.nx * c.ny * c.nz, K, &f->kl[l]));
+    }
     PD_CHECK_CUDA(cudaDeviceSynchronize());
     return PD_OK;
 }
@@ -416,7 +386,10 @@ extern "C" int pd_field_create(const pd_grid *finest, int32_t n_levels, const pd
     f->cfg = *cfg;
     f->n_levels = n_levels;
     f->K = cfg->n_modes;
-    for (int l = 0; l < PD_MAX_LEVELS; ++l) f->phi[l] = nullptr;
+    for (int l = 0; l < PD_MAX_LEVELS; ++l) {
+        f->phi[l] = nullptr;
+        f->kl[l] = nullptr;
+    }
     f->grid[n_levels - 1] = *finest;
     for (int l = n_levels - 2; l >= 0; --l) {
         pd_grid c = f->grid[l + 1];
@@ -441,11 +414,17 @@ extern "C" int pd_field_create(const pd_grid *finest, int32_t n_levels, const pd
 }
 
 extern "C" int pd_field_destroy(pd_field *f) {
+    int rc = PD_OK;
     if (f) {
         cudaDeviceSynchronize();
+        for (int l = 0; l < f->n_levels; ++l)
+            if (f->kl[l] && kl_operand_error(f->kl[l]) != 0) {
+                set_error("a field sampling tile gave up waiting for its copies or MMAs (level %d)", l);
+                rc = PD_ERR_TIMEOUT;
+            }
         free_field(f);
     }
-    return PD_OK;
+    return rc;
 }
 
 extern "C" int pd_field_info(const pd_field *f, int32_t *n_modes, double *lambda) {
@@ -457,8 +436,6 @@ extern "C" int pd_field_info(const pd_field *f, int32_t *n_modes, double *lambda
 }
 
 static int sample_level(const pd_field *f, int level, const double *xi, int B, float *out, cudaStream_t s) {
-    const pd_grid &g = f->grid[level];
-    const long long N = (long long)g.nx * g.ny * g.nz;
     const pd_field_cfg &c = f->cfg;
     double mu = 0, sig = 0, wscale = 0, winvm = 0;
     if (c.marginal == PD_MARG_LOGNORMAL) {
@@ -469,10 +446,7 @@ static int sample_level(const pd_field *f, int level, const double *xi, int B, f
         wscale = c.mean / std::tgamma(1.0 + 1.0 / c.weibull_m);
         winvm = 1.0 / c.weibull_m;
     }
-    k_sample<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, f->K, B, f->phi[level], xi, c.marginal, mu, sig,
-                                                          wscale, winvm, out);
-    PD_CHECK_LAUNCH();
-    return PD_OK;
+    return kl_sample_tc(f->kl[level], xi, B, c.marginal, mu, sig, wscale, winvm, out, s);
 }
 
 extern "C" int pd_sample_field(pd_field *f, int32_t level, const double *xi, int32_t B, float *node_field,

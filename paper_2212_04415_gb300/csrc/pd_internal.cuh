@@ -134,3 +134,12 @@ struct pd_state {
     int32_t *host_flag_dev; // device alias
     cudaEvent_t ev[2];
 };
+
+// Tensor-core KL sampling (pd_kl.cu): the split TF32 operand Psi of one level
+// with its TMA descriptors, and the sampling launch.
+struct KlOperand;
+int kl_operand_create(const float *phi, long long N, int K, KlOperand **out);
+void kl_operand_destroy(KlOperand *op);
+int kl_operand_error(const KlOperand *op);
+int kl_sample_tc(KlOperand *op, const double *xi, int B, int marginal, double mu, double sig, double wscale,
+                 double winvm, float *out, cudaStream_t s);

@@ -214,8 +214,7 @@ __global__ void __launch_bounds__(512, 2) k_step_stencil(const StepArgs a) {
             constexpr int R = kRounds / Q;
             float *dm = (float *)a.dmg + (size_t)b * a.sell_len + ((size_t)brick * wpb + rp) * (kRounds * 32) + lane;
             bond_span<R / 8, LAW, KAPPA>(part * R, s_tab[t], s_offb[t], (const char *)(s_rec + 2 * il), hi, lo, dm,
-                                         (float)a.cV, (float)a.s_ratio, (float)a.k, (float)a.alpha,
-                                         (float)a.inv_1mek, (float)a.inv_1pa, acc);
+                                         a.cVf, a.s_ratio_f, a.k_f, a.alpha_f, a.inv_1mek_f, a.inv_1pa_f, acc);
         }
         // add the two sub-lane partials in double-float (TwoSum is exact, so
         // both sub-lanes end with the same total)

@@ -205,9 +205,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
                 const float4 hi = s_hi[il], lo = s_lo[il];
                 if (own) {
                     float *dm = (float *)a.dmg + (size_t)b * a.sell_len + a.sell_off[sl] + lane;
-                    const float cVf = (float)a.cV;
-                    const float sr = (float)a.s_ratio, kf = (float)a.k, af = (float)a.alpha;
-                    const float i1 = (float)a.inv_1mek, i2 = (float)a.inv_1pa;
+                    const float cVf = a.cVf;
+                    const float sr = a.s_ratio_f, kf = a.k_f, af = a.alpha_f;
+                    const float i1 = a.inv_1mek_f, i2 = a.inv_1pa_f;
                     // Padding slots (id 0xFF) point at the node itself with |xi| = dx:
                     // zero stretch, zero force, no damage write, no branch.
                     // Bonds are summed in plain FP32 over groups of 4 rounds and each
@@ -664,6 +664,12 @@ static StepArgs make_args(const pd_state *st) {
     a.alpha = st->mat.alpha;
     a.inv_1mek = 1.0 / (1.0 - std::exp(-st->mat.k));
     a.inv_1pa = 1.0 / (1.0 + st->mat.alpha);
+    a.cVf = (float)a.cV;
+    a.s_ratio_f = (float)a.s_ratio;
+    a.k_f = (float)a.k;
+    a.alpha_f = (float)a.alpha;
+    a.inv_1mek_f = (float)a.inv_1mek;
+    a.inv_1pa_f = (float)a.inv_1pa;
     return a;
 }
 
