@@ -11,7 +11,10 @@ Pins (tests under ``tests/test_oracle_*.py``):
   (antisymmetry); the interior force of a uniform stretch vanishes and its
   strain energy density matches the lattice closed form and, within the
   lattice error, the continuum value that defines the micromodulus;
-* run: R(2U) = 2R(U) in the linear regime; damage monotone in time.
+* run: R(2U) = 2R(U) in the linear regime; damage monotone in time;
+* adjoint: central differences of the run with respect to node s0 and kappa
+  (elastic and softening windows, both laws); s0 has no influence before a
+  bond softens; linear in the observation weights.
 """
 from __future__ import annotations
 
@@ -88,6 +91,8 @@ def lib():
                                    C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_max_threads.restype = C.c_int
+        L.or_adjoint.argtypes = [C.POINTER(Problem), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p]
     return _lib
 
 
@@ -197,6 +202,19 @@ class Model:
         k = nd.value
         return dict(u=u, v=v, d=d, reaction=R[:k], smax=sm[:k], peak=pk.value,
                     peak_step=ps.value, n_done=k)
+
+
+    def adjoint(self, n_steps, obs_steps, weights):
+        """Gradient of J = sum_o weights[o] R^{obs_steps[o]} over n_steps steps from the
+        zero state with respect to the node fields s0 and (when set) kappa."""
+        obs = np.ascontiguousarray(np.asarray(obs_steps, np.int32))
+        wts = np.ascontiguousarray(np.asarray(weights, np.float64))
+        gs = np.zeros(self.n)
+        gk = np.zeros(self.n) if self.kappa is not None else None
+        rc = lib().or_adjoint(C.byref(self.P), n_steps, obs.size, _p(obs), _p(wts), _p(gs), _p(gk))
+        if rc != 0:
+            raise RuntimeError(f"or_adjoint failed ({rc})")
+        return gs, gk
 
 
 def run_batch(model: Model, s0, n_steps, use_stop=True, kappa=None):

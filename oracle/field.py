@@ -35,6 +35,12 @@ What is computed, step by step:
 6. Marginal transform (copula, Section 5.2): lognormal
    s0 = exp(mu + sigma g), sigma^2 = ln(1 + COV^2), mu = ln(mean) - sigma^2/2;
    Weibull s0 = F_W^-1(Phi(g)) with modulus m and scale mean / Gamma(1 + 1/m).
+7. Chain rule back to the coefficients (for gradients of a quantity J with
+   respect to xi, given dJ/ds0 per node): dJ/dg_i = dJ/ds0_i ds0/dg_i with
+   ds0/dg = sigma s0 (lognormal) or, for the Weibull copula with
+   q = 1 - Phi(g), ds0/dg = (scale / m) (-ln q)^(1/m - 1) phi(g) / q; then
+   dJ/dxi_k = sum_i dJ/dg_i sqrt(lambda_k) Phi_ik. Pinned by central
+   differences of the whole chain xi -> s0 -> run -> J.
 """
 from __future__ import annotations
 
@@ -214,6 +220,24 @@ def weibull(g, mean: float, m: float):
     scale = mean / math.gamma(1.0 + 1.0 / m)
     p = ndtr(np.asarray(g))
     return scale * (-np.log1p(-p)) ** (1.0 / m)
+
+
+def grad_xi(fcfg, Phi, lam, xi, dJ_ds0):
+    """dJ/dxi [B, K] from dJ/ds0 [B, N] through the marginal transform and the
+    truncated KL expansion (step 7 above)."""
+    g = gaussian(Phi, lam, xi)
+    dJ = np.asarray(dJ_ds0, np.float64)
+    if fcfg.marginal == 0:
+        s2 = math.log(1.0 + fcfg.cov * fcfg.cov)
+        dg = dJ * math.sqrt(s2) * lognormal(g, fcfg.mean, fcfg.cov)
+    else:
+        from scipy.special import ndtr
+        m = fcfg.weibull_m
+        scale = fcfg.mean / math.gamma(1.0 + 1.0 / m)
+        q = 1.0 - ndtr(g)
+        pdf = np.exp(-0.5 * g * g) / math.sqrt(2.0 * math.pi)
+        dg = dJ * (scale / m) * (-np.log(q)) ** (1.0 / m - 1.0) * pdf / q
+    return (dg @ Phi) * np.sqrt(lam)[None, :]
 
 
 def sample_field(w, Phi, lam, seed, level, sample_ids):

@@ -441,3 +441,183 @@ int or_max_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------ adjoint */
+
+/* Derivatives of the softening law d = D(s; s0, sc = ratio s0) on (s0, sc):
+ * dD/ds and the total dD/ds0 (sc moves with s0). Zero outside (s0, sc),
+ * where D is flat (0 or 1).
+ *   bilinear:  D = 1 - (r s0 / s - 1) / (r - 1)
+ *              dD/ds = r s0 / ((r - 1) s^2),  dD/ds0 = -r / ((r - 1) s)
+ *   exp-linear (Eq. exp_damage_parameter): D = 1 - (s0/s) beta(t) / (1 + alpha),
+ *              t = (s - s0) / ((r - 1) s0),
+ *              beta(t) = 1 - (1 - e^{-k t}) / (1 - e^{-k}) + alpha (1 - t),
+ *              beta'(t) = -k e^{-k t} / (1 - e^{-k}) - alpha,
+ *              dt/ds = 1 / ((r - 1) s0),  dt/ds0 = -s / ((r - 1) s0^2). */
+static void law_derivs(int32_t law, double s, double s0, double r, double k, double alpha,
+                       double *dDds, double *dDds0) {
+    double sc = r * s0;
+    *dDds = 0.0;
+    *dDds0 = 0.0;
+    if (s <= s0 || s >= sc) return;
+    if (law == 0) {
+        *dDds = r * s0 / ((r - 1.0) * s * s);
+        *dDds0 = -r / ((r - 1.0) * s);
+        return;
+    }
+    double t = (s - s0) / ((r - 1.0) * s0);
+    double beta = 1.0 - (1.0 - exp(-k * t)) / (1.0 - exp(-k)) + alpha * (1.0 - t);
+    double dbeta = -k * exp(-k * t) / (1.0 - exp(-k)) - alpha;
+    double dtds = 1.0 / ((r - 1.0) * s0);
+    double dtds0 = -s / ((r - 1.0) * s0 * s0);
+    /* D = 1 - s0 beta / ((1 + alpha) s) */
+    *dDds = (s0 * beta / (s * s) - (s0 / s) * dbeta * dtds) / (1.0 + alpha);
+    *dDds0 = -(beta / s + (s0 / s) * dbeta * dtds0) / (1.0 + alpha);
+}
+
+/* Reverse-mode derivative of J = sum_o w[o] R^{obs_step[o]} over a run of
+ * n_steps steps from the zero state (no stop rule), with respect to the
+ * per-node s0 (grad_s0, N) and kappa (grad_kappa, N, may be NULL; needs
+ * p->kappa when non-NULL). The exact discrete adjoint of the step of or_run:
+ * the branch of d_n = max(d_{n-1}, D(s_n)) taken forward is kept, so the
+ * derivative follows D when it set the new value and d_{n-1} otherwise.
+ *
+ * The forward pass stores u^n and d^n of every step (test sizes only). With
+ * h = s/L, the pair of directed forces of an undirected bond contributes
+ *   Phi = lamF_i . f_ij + lamF_j . f_ji = -c_ij V (1 - d) h(y) (y . (lamF_j - lamF_i))
+ * to the Lagrangian, and the reverse step n is:
+ *   free DOF:    lv' = lamv^{n+1/2} + dt lamu^{n+1};  lamF^n = dt lv' / (rho b);
+ *                lamv^{n-1/2} = a lv' / b;  lamu^n = lamu^{n+1} + bond terms
+ *   prescribed:  lamF^n = -sign V sum_{o: obs_step[o] = n} w[o]
+ *   bond (i,j):  lamd_tot = lamd + c_ij V h (y . dlam)
+ *                lamy = dPhi/dy|_d + [active] lamd_tot D'(s) y / (L L0)
+ *                lamu_i -= lamy   (the row of j adds +lamy for j)
+ *                grad_s0_i += 0.5 [active] lamd_tot dD/ds0
+ *                grad_kappa_i += 0.5 c dPhi/dc_ij,  dPhi/dc_ij = -V (1 - d) h (y . dlam)
+ *                lamd <- [not active] lamd_tot */
+int or_adjoint(const or_problem *p, int32_t n_steps, int32_t n_obs, const int32_t *obs_step,
+               const double *w, double *grad_s0, double *grad_kappa) {
+    int64_t n = (int64_t)p->nx * p->ny * p->nz;
+    int64_t nb = p->row_ptr[n];
+    double V = p->dx * p->dx * p->dx;
+    double a = 1.0 - 0.5 * p->zeta * p->dt;
+    double b = 1.0 + 0.5 * p->zeta * p->dt;
+    if (n_steps < 0 || (grad_kappa && !p->kappa)) return OR_ERR_ARG;
+    double *U = (double *)malloc(sizeof(double) * 3 * (size_t)n * (size_t)(n_steps > 0 ? n_steps : 1));
+    double *Dh = (double *)calloc((size_t)nb * (size_t)(n_steps + 1), sizeof(double));
+    double *u = (double *)calloc(3 * (size_t)n, sizeof(double));
+    double *v = (double *)calloc(3 * (size_t)n, sizeof(double));
+    double *lu = (double *)calloc(3 * (size_t)n, sizeof(double));
+    double *lun = (double *)calloc(3 * (size_t)n, sizeof(double));
+    double *lv = (double *)calloc(3 * (size_t)n, sizeof(double));
+    double *lF = (double *)calloc(3 * (size_t)n, sizeof(double));
+    double *ld = (double *)calloc((size_t)nb, sizeof(double));
+    double *F = (double *)calloc(3 * (size_t)n, sizeof(double));
+    if (!U || !Dh || !u || !v || !lu || !lun || !lv || !lF || !ld || !F) return OR_ERR_ARG;
+    /* forward, storing u^n and d^n (Dh[0] = d^{-1} = 0) */
+    for (int32_t s = 0; s < n_steps; ++s) {
+        memcpy(U + (size_t)s * 3 * n, u, sizeof(double) * 3 * (size_t)n);
+        memcpy(Dh + (size_t)(s + 1) * nb, Dh + (size_t)s * nb, sizeof(double) * (size_t)nb);
+        forces(p, u, Dh + (size_t)(s + 1) * nb, F, NULL);
+        double Un = ramp(p, s), Un1 = ramp(p, s + 1);
+        for (int64_t q = 0; q < 3 * n; ++q) {
+            uint8_t code = p->bc[q];
+            if (code == 0) {
+                v[q] = (a * v[q] + p->dt * F[q] / p->rho) / b;
+                u[q] = u[q] + p->dt * v[q];
+            } else if (code == 1) {
+                u[q] = 0.0;
+                v[q] = 0.0;
+            } else {
+                double sg = code == 2 ? 1.0 : -1.0;
+                v[q] = sg * (Un1 - Un) / p->dt;
+                u[q] = sg * Un1;
+            }
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        grad_s0[i] = 0.0;
+        if (grad_kappa) grad_kappa[i] = 0.0;
+    }
+    or_grid g = {p->nx, p->ny, p->nz, p->dx, 0.0, 0, 0, 0};
+    for (int32_t s = n_steps - 1; s >= 0; --s) {
+        double wn = 0.0;
+        for (int32_t o = 0; o < n_obs; ++o)
+            if (obs_step[o] == s) wn += w[o];
+        /* integrator */
+        for (int64_t q = 0; q < 3 * n; ++q) {
+            uint8_t code = p->bc[q];
+            if (code == 0) {
+                double lvp = lv[q] + p->dt * lu[q];
+                lF[q] = p->dt * lvp / (p->rho * b);
+                lv[q] = a * lvp / b;
+                lun[q] = lu[q];
+            } else if (code == 1) {
+                lF[q] = 0.0;
+                lv[q] = 0.0;
+                lun[q] = 0.0;
+            } else {
+                double sg = code == 2 ? 1.0 : -1.0;
+                lF[q] = -sg * V * wn;
+                lv[q] = 0.0;
+                lun[q] = 0.0;
+            }
+        }
+        /* bonds, from u^s, d^{s-1} and d^s */
+        const double *us = U + (size_t)s * 3 * n;
+        const double *dprev = Dh + (size_t)s * nb;
+        const double *dcur = Dh + (size_t)(s + 1) * nb;
+        for (int64_t i = 0; i < n; ++i) {
+            double xi_[3];
+            node_xyz(&g, i, xi_);
+            for (int32_t q = p->row_ptr[i]; q < p->row_ptr[i + 1]; ++q) {
+                int64_t j = p->col[q];
+                double xj[3], y[3], dl[3];
+                node_xyz(&g, j, xj);
+                double L0 = 0.0, L = 0.0, ydl = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    double xic = xj[c] - xi_[c];
+                    y[c] = xic + (us[3 * j + c] - us[3 * i + c]);
+                    dl[c] = lF[3 * j + c] - lF[3 * i + c];
+                    L0 += xic * xic;
+                    L += y[c] * y[c];
+                    ydl += y[c] * dl[c];
+                }
+                L0 = sqrt(L0);
+                L = sqrt(L);
+                double sv = (L - L0) / L0;
+                double h = sv / L;
+                double s0 = 0.5 * (p->s0[i] + p->s0[j]);
+                double cij = p->c;
+                if (p->kappa) cij = p->c * 0.5 * (p->kappa[i] + p->kappa[j]);
+                double dD = or_damage_law(p->law, sv, s0, p->s_ratio * s0, p->k, p->alpha);
+                int active = dD > dprev[q];
+                double d = dcur[q];
+                double lamd_tot = ld[q] + cij * V * h * ydl;
+                double dDds = 0.0, dDds0 = 0.0;
+                if (active) law_derivs(p->law, sv, s0, p->s_ratio, p->k, p->alpha, &dDds, &dDds0);
+                for (int c = 0; c < 3; ++c) {
+                    double dh = y[c] / (L * L * L0) - sv * y[c] / (L * L * L);
+                    double lamy = -cij * V * (1.0 - d) * (ydl * dh + h * dl[c]);
+                    if (active) lamy += lamd_tot * dDds * y[c] / (L * L0);
+                    lun[3 * i + c] -= lamy;
+                }
+                if (active) grad_s0[i] += 0.5 * lamd_tot * dDds0;
+                if (grad_kappa) grad_kappa[i] += 0.5 * p->c * (-V * (1.0 - d) * h * ydl);
+                ld[q] = active ? 0.0 : lamd_tot;
+            }
+        }
+        memcpy(lu, lun, sizeof(double) * 3 * (size_t)n);
+    }
+    free(U);
+    free(Dh);
+    free(u);
+    free(v);
+    free(lu);
+    free(lun);
+    free(lv);
+    free(lF);
+    free(ld);
+    free(F);
+    return OR_OK;
+}
