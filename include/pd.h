@@ -206,6 +206,33 @@ PD_API int pd_step(pd_state *st, int32_t n_steps, double *reaction, pd_stream st
 PD_API int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int32_t *peak_step,
                    int32_t *n_done, pd_stream stream);
 
+/* ---------------------------------------------------------------- adjoint */
+
+/* Reverse-mode gradient of J = sum_o dJ_dR[b][o] R^{n0 + obs_steps[o]} of every
+ * sample b over a run of n_steps steps from the state's current content
+ * (all samples at the same step index n0, as after pd_state_reset or
+ * pd_state_load), with respect to the per-node fields s0 and kappa: the exact
+ * discrete adjoint of the step (Eq. PD_EOM_Dynamic, Eq. exp_scalar_force,
+ * Eq. exp_damage_parameter, the damped leapfrog update and the reaction), the
+ * branch of d_n = max(d_{n-1}, D(s_n)) taken forward kept. The paper has no
+ * counterpart; it serves parameter-importance studies of the random fields.
+ *   obs_steps: host int32[n_obs], local step indices in [0, n_steps)
+ *   dJ_dR:     device double[B][n_obs]
+ *   s0, kappa: device float[B][N], the fields passed to pd_state_reset
+ *              (kappa NULL: kappa = 1)
+ *   grad_s0, grad_kappa: device double[B][N] out (grad_kappa may be NULL)
+ *   R_obs:     device double[B][n_obs] out, the forward reactions, or NULL
+ * Checkpoints (u, v, d) every ckpt_every steps and recomputes each segment;
+ * device memory: ((n_steps / ckpt_every + 2) (6N + n_b) + ckpt_every (3N + n_b)
+ * + 12 N + n_b) B doubles, allocated per call (PD_ERR_OOM when unavailable).
+ * Arithmetic is FP64; the states come from the state's own forward path.
+ * Host-synchronous. On return the state holds the forward run's final state
+ * (step n0 + n_steps), as after pd_step(n_steps). */
+PD_API int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int32_t n_obs,
+                      const int32_t *obs_steps, const double *dJ_dR, const float *s0,
+                      const float *kappa, double *grad_s0, double *grad_kappa, double *R_obs,
+                      pd_stream stream);
+
 /* ---------------------------------------------------------- random field */
 
 /* KL coefficients xi (device double[B][K]) of samples sample_ids (device
@@ -228,6 +255,15 @@ PD_API int pd_field_destroy(pd_field *f);
 
 /* K and the KL eigenvalues (host double[K], may be NULL). */
 PD_API int pd_field_info(const pd_field *f, int32_t *n_modes, double *lambda);
+
+/* Chain rule of a node-field gradient back to the KL coefficients
+ * (Section 5): dJ/dxi_k = sum_i dJ/ds0_i ds0_i/dg_i sqrt(lambda_k) phi_k(x_i),
+ * with ds0/dg = sigma s0 (lognormal) or the Weibull copula's derivative;
+ * g is recomputed in FP64 from xi. xi: device double[B][K]; dJ_ds0: device
+ * double[B][N_level]; dJ_dxi: device double[B][K] out (FP64, fixed-order
+ * sums). Host-synchronous. */
+PD_API int pd_field_adjoint(const pd_field *f, int32_t level, const double *xi, int32_t B,
+                            const double *dJ_ds0, double *dJ_dxi, pd_stream stream);
 
 /* Field of B samples on grid `level`: g = Phi diag(sqrt(lambda)) xi, then the
  * marginal transform (Section 5.2). node_field: device float[B][N_level].

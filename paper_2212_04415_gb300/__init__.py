@@ -89,6 +89,8 @@ _SIGS = {
     "pd_field_info": (C.c_int, [_VP, C.POINTER(C.c_int32), _VP]),
     "pd_sample_field": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, _VP, _VP, _VP]),
     "mlmc_estimate": (C.c_int, [C.POINTER(MlmcCfg), C.POINTER(MlmcResult), _VP, _VP, _VP, _VP]),
+    "pd_adjoint": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "pd_field_adjoint": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, _VP, _VP, _VP]),
     "pd_mlmc_allocation": (C.c_int, [C.c_int32, _VP, _VP, C.c_double, _VP]),
 }
 
@@ -235,6 +237,21 @@ class State:
         _check(lib().pd_run_to_peak(self.h, max_steps, _ptr(pk), _ptr(ps), _ptr(nd), _stream(stream)))
         return pk, ps, nd
 
+    def adjoint(self, n_steps, obs_steps, dJ_dR, s0, kappa=None, ckpt_every=100, grad_kappa=True,
+                stream=None):
+        """Gradient of J = sum_o dJ_dR[:, o] R^{obs_steps[o]} over n_steps steps from the
+        current state with respect to the node fields s0 and kappa (pd_adjoint).
+        Returns (grad_s0, grad_kappa or None, R at the observation steps)."""
+        import torch
+        obs = (C.c_int32 * max(len(obs_steps), 1))(*[int(o) for o in obs_steps])
+        gs = torch.empty((self.B, self.N), dtype=torch.float64, device="cuda")
+        gk = torch.empty_like(gs) if grad_kappa else None
+        R = torch.empty((self.B, len(obs_steps)), dtype=torch.float64, device="cuda")
+        _check(lib().pd_adjoint(self.h, n_steps, ckpt_every, len(obs_steps), C.cast(obs, C.c_void_p),
+                                _ptr(dJ_dR), _ptr(s0), _ptr(kappa), _ptr(gs), _ptr(gk), _ptr(R),
+                                _stream(stream)))
+        return gs, gk, R
+
 
 def draw_xi(seed, level, sample_ids, n_modes, stream=None, out=None):
     import torch
@@ -270,6 +287,14 @@ class Field:
         if h:
             self.h = None
             lib().pd_field_destroy(h)
+
+    def adjoint(self, level, xi, dJ_ds0, stream=None):
+        """dJ/dxi [B, K] from dJ/ds0 [B, N_level] (pd_field_adjoint)."""
+        import torch
+        B = xi.shape[0]
+        out = torch.empty((B, self.K), dtype=torch.float64, device="cuda")
+        _check(lib().pd_field_adjoint(self.h, level, _ptr(xi), B, _ptr(dJ_ds0), _ptr(out), _stream(stream)))
+        return out
 
     def eigenvalues(self):
         import numpy as np
@@ -339,3 +364,49 @@ def mlmc_allocation(V, Cst, eps_s):
     _check(lib().pd_mlmc_allocation(V.size, V.ctypes.data_as(C.c_void_p), Cs.ctypes.data_as(C.c_void_p),
                                     eps_s, N.ctypes.data_as(C.c_void_p)))
     return N
+
+
+def reaction_at(xi_s, xi_k, state, field_s, field_k, level, n_steps, obs_steps, ckpt_every=100):
+    """Reactions R^{obs_steps} [B, n_obs] of the samples whose strength field has
+    KL coefficients xi_s (and stiffness field xi_k, or None), differentiable
+    with respect to both coefficient sets: the backward pass runs pd_adjoint and
+    pd_field_adjoint."""
+    return _reaction_fn().apply(xi_s, xi_k, state, field_s, field_k, level, n_steps, list(obs_steps), ckpt_every)
+
+
+_RFN = None
+
+
+def _reaction_fn():
+    global _RFN
+    if _RFN is not None:
+        return _RFN
+    import torch
+
+    class ReactionAt(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, xi_s, xi_k, state, field_s, field_k, level, n_steps, obs_steps, ckpt_every):
+            s0 = field_s.sample(level, xi_s)
+            kap = field_k.sample(level, xi_k) if xi_k is not None else None
+            state.reset(s0, kap)
+            R = state.step(n_steps)
+            ctx.save_for_backward(xi_s, xi_k if xi_k is not None else torch.empty(0))
+            ctx.args = (state, field_s, field_k, level, n_steps, obs_steps, ckpt_every, xi_k is not None)
+            return R[:, obs_steps].contiguous()
+
+        @staticmethod
+        def backward(ctx, gR):
+            xi_s, xi_k = ctx.saved_tensors
+            state, field_s, field_k, level, n_steps, obs_steps, ckpt_every, has_k = ctx.args
+            s0 = field_s.sample(level, xi_s)
+            kap = field_k.sample(level, xi_k) if has_k else None
+            state.reset(s0, kap)
+            gs, gk, _ = state.adjoint(n_steps, obs_steps, gR.contiguous().to(torch.float64), s0, kap,
+                                      ckpt_every=ckpt_every, grad_kappa=has_k)
+            g_xs = field_s.adjoint(level, xi_s, gs)
+            g_xk = field_k.adjoint(level, xi_k, gk) if has_k else None
+            return g_xs, g_xk, None, None, None, None, None, None, None
+
+    _RFN = ReactionAt
+    return _RFN
+

@@ -1,0 +1,396 @@
+// pd_adjoint.cu -- discrete adjoint of the explicit step (Sections 2-3,
+// Eq. PD_EOM_Dynamic, Eq. exp_scalar_force, Eq. exp_damage_parameter) and
+// its chain rule back through the truncated-KL field (Section 5), giving
+// dJ/dxi for J = sum_o w_o R^{n_o}.
+//
+// Reverse sweep with checkpoints: the forward run stores (u, v, d) every k
+// steps; each segment is then recomputed step by step from its checkpoint
+// (states u^n and damage d^n kept for the segment) and walked backwards:
+//
+//   integrator (per DOF), lv' = lamv^{n+1/2} + dt lamu^{n+1}:
+//     free        lamF^n = dt lv' / (rho b),  lamv^{n-1/2} = a lv' / b,
+//                 lamu^n = lamu^{n+1} + bond terms
+//     prescribed  lamF^n = -sign V sum_{o: n_o = n} w_o  (u, v prescribed: no carry)
+//     fixed       nothing
+//   bonds (one warp per node, lanes over the node's bonds), y = xi + eta,
+//   h = s / |y|, dlam = lamF_j - lamF_i, the branch of d_n = max(d_{n-1},
+//   D(s_n)) taken forward kept (active when d_n > d_{n-1}):
+//     lamd_tot = lamd + c_ij V h (y . dlam)
+//     lamy     = -c_ij V (1 - d_n) [(y . dlam) dh/dy + h dlam]
+//                + [active] lamd_tot D'(s) y / (|y| |xi|)
+//     lamu_i  -= lamy;  grad_s0_i += [active] lamd_tot dD/ds0 / 2;
+//     grad_kappa_i += c (-V (1 - d_n) h (y . dlam)) / 2;
+//     lamd <- [not active] lamd_tot
+//
+// The undirected bond's damage adjoint is kept in both directed slots (both
+// copies compute the same value), and the node sums are fixed xor trees, so
+// the gradient is deterministic. Arithmetic is FP64 throughout (the adjoint
+// is an offline gradient study; its states come from the state's own
+// forward path, FP64 or mixed).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "pd_internal.cuh"
+
+namespace pdi {
+
+struct AdjArgs {
+    int B;
+    long long N, nb;
+    int nx, ny;
+    double dx, c, V, dt, rho, a, b;
+    int law;
+    double s_ratio, k, alpha;
+    const int32_t *row_ptr, *col;
+    const uint8_t *codes;
+    const float *s0, *kappa;
+    int n_obs;
+    const int32_t *obs;  // [n_obs] local step of each observation
+    const double *w;     // [B][n_obs]
+};
+
+// dD/ds and the total dD/ds0 (s_crit = ratio s0) on (s0, s_crit); zero outside.
+__device__ __forceinline__ void law_derivs(const AdjArgs &a, double s, double s0, double &dDds, double &dDds0) {
+    const double r = a.s_ratio;
+    dDds = 0.0;
+    dDds0 = 0.0;
+    if (s <= s0 || s >= r * s0) return;
+    if (a.law == PD_LAW_BILINEAR) {  // D = 1 - (r s0 / s - 1) / (r - 1)
+        dDds = r * s0 / ((r - 1.0) * s * s);
+        dDds0 = -r / ((r - 1.0) * s);
+        return;
+    }
+    // D = 1 - (s0 / s) beta(t) / (1 + alpha), t = (s - s0) / ((r - 1) s0)
+    const double t = (s - s0) / ((r - 1.0) * s0);
+    const double e = exp(-a.k * t), ek = 1.0 - exp(-a.k);
+    const double beta = 1.0 - (1.0 - e) / ek + a.alpha * (1.0 - t);
+    const double dbeta = -a.k * e / ek - a.alpha;
+    const double dtds = 1.0 / ((r - 1.0) * s0), dtds0 = -s / ((r - 1.0) * s0 * s0);
+    dDds = (s0 * beta / (s * s) - (s0 / s) * dbeta * dtds) / (1.0 + a.alpha);
+    dDds0 = -(beta / s + (s0 / s) * dbeta * dtds0) / (1.0 + a.alpha);
+}
+
+// Integrator adjoint of local step `ls`: lamF, lamv (in place) and the carried
+// part of lamu^n (lun) from lamu^{n+1} (lu).
+__global__ void k_adj_nodes(const AdjArgs a, int ls, const double *lu, double *lv, double *lF, double *lun) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)a.B * a.N * 3) return;
+    const int b = (int)(t / (a.N * 3));
+    const long long q = t % (a.N * 3);
+    const uint8_t code = a.codes[q];
+    if (code == 0) {
+        const double lvp = lv[t] + a.dt * lu[t];
+        lF[t] = a.dt * lvp / (a.rho * a.b);
+        lv[t] = a.a * lvp / a.b;
+        lun[t] = lu[t];
+    } else if (code == 1) {
+        lF[t] = 0.0;
+        lv[t] = 0.0;
+        lun[t] = 0.0;
+    } else {
+        double wn = 0.0;
+        for (int o = 0; o < a.n_obs; ++o)
+            if (a.obs[o] == ls) wn += a.w[(size_t)b * a.n_obs + o];
+        const double sg = code == 2 ? 1.0 : -1.0;
+        lF[t] = -sg * a.V * wn;
+        lv[t] = 0.0;
+        lun[t] = 0.0;
+    }
+}
+
+__device__ __forceinline__ double warp_sum_fixed(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Bond adjoint of one step: one warp per (sample, node).
+__global__ void __launch_bounds__(256) k_adj_bonds(const AdjArgs a, const double *u, const double *dprev,
+                                                   const double *dcur, const double *lF, double *ld, double *lun,
+                                                   double *g_s0, double *g_k) {
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= (long long)a.B * a.N) return;  // warp-uniform
+    const int b = (int)(gw / a.N);
+    const long long i = gw % a.N;
+    const int ix = (int)(i % a.nx), iy = (int)((i / a.nx) % a.ny), iz = (int)(i / ((long long)a.nx * a.ny));
+    const double *ub = u + (size_t)b * a.N * 3;
+    const double *lFb = lF + (size_t)b * a.N * 3;
+    const float *s0b = a.s0 + (size_t)b * a.N;
+    const float *kb = a.kappa ? a.kappa + (size_t)b * a.N : nullptr;
+    const size_t db = (size_t)b * a.nb;
+    const double ui[3] = {ub[3 * i], ub[3 * i + 1], ub[3 * i + 2]};
+    const double li[3] = {lFb[3 * i], lFb[3 * i + 1], lFb[3 * i + 2]};
+    const double s0i = (double)s0b[i], ki = kb ? (double)kb[i] : 1.0;
+    double acc[3] = {0.0, 0.0, 0.0}, gs = 0.0, gk = 0.0;
+    for (int q = a.row_ptr[i] + lane; q < a.row_ptr[i + 1]; q += 32) {
+        const long long j = a.col[q];
+        const int jx = (int)(j % a.nx), jy = (int)((j / a.nx) % a.ny), jz = (int)(j / ((long long)a.nx * a.ny));
+        const double xi[3] = {(jx - ix) * a.dx, (jy - iy) * a.dx, (jz - iz) * a.dx};
+        double y[3], dl[3], L0 = 0.0, L = 0.0, ydl = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            y[c] = xi[c] + (ub[3 * j + c] - ui[c]);
+            dl[c] = lFb[3 * j + c] - li[c];
+            L0 += xi[c] * xi[c];
+            L += y[c] * y[c];
+            ydl += y[c] * dl[c];
+        }
+        L0 = sqrt(L0);
+        L = sqrt(L);
+        const double s = (L - L0) / L0, h = s / L;
+        const double s0 = 0.5 * (s0i + (double)s0b[j]);
+        const double cij = kb ? a.c * 0.5 * (ki + (double)kb[j]) : a.c;
+        const double dp = dprev[db + q], dc = dcur[db + q];
+        const bool active = dc > dp;
+        const double lamd = ld[db + q] + cij * a.V * h * ydl;
+        double dDds = 0.0, dDds0 = 0.0;
+        if (active) law_derivs(a, s, s0, dDds, dDds0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double dh = y[c] / (L * L * L0) - s * y[c] / (L * L * L);
+            double lamy = -cij * a.V * (1.0 - dc) * (ydl * dh + h * dl[c]);
+            if (active) lamy += lamd * dDds * y[c] / (L * L0);
+            acc[c] -= lamy;
+        }
+        if (active) gs += 0.5 * lamd * dDds0;
+        gk += 0.5 * a.c * (-a.V * (1.0 - dc) * h * ydl);
+        ld[db + q] = active ? 0.0 : lamd;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = warp_sum_fixed(acc[c]);
+    gs = warp_sum_fixed(gs);
+    gk = warp_sum_fixed(gk);
+    if (lane == 0) {
+        double *lb = lun + (size_t)b * a.N * 3 + 3 * i;
+        lb[0] += acc[0];
+        lb[1] += acc[1];
+        lb[2] += acc[2];
+        g_s0[(size_t)b * a.N + i] += gs;
+        if (g_k) g_k[(size_t)b * a.N + i] += gk;
+    }
+}
+
+// R_obs[b][o] = reaction[b][m] for the observations inside a segment.
+__global__ void k_gather_obs(int B, int len, int start, int n_obs, const int32_t *obs, const double *reaction,
+                             double *R_obs) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B * n_obs) return;
+    const int b = t / n_obs, o = t % n_obs;
+    const int m = obs[o] - start;
+    if (m >= 0 && m < len) R_obs[t] = reaction[(size_t)b * len + m];
+}
+
+// ---- chain rule to the KL coefficients
+
+constexpr int kFgNodes = 2048;  // nodes per partial
+constexpr int kFgMaxK = 256;
+
+// partial[b][chunk][k] = sum over the chunk's nodes of dJ/dg_i Psi_ik (FP64,
+// fixed order: thread t takes nodes t, t + 256, ...; then a fixed tree).
+__global__ void __launch_bounds__(256) k_field_grad_partial(long long N, int K, const float *psi, const double *xi,
+                                                            const double *dJ_ds0, int marginal, double mu, double sig,
+                                                            double wscale, double m_w, int nchunks, double *partial) {
+    __shared__ double sxi[kFgMaxK];
+    __shared__ double red[256];
+    const int b = blockIdx.y, chunk = blockIdx.x;
+    for (int k = threadIdx.x; k < K; k += 256) sxi[k] = xi[(size_t)b * K + k];
+    __syncthreads();
+    const long long i0 = (long long)chunk * kFgNodes;
+    const long long i1 = min(N, i0 + kFgNodes);
+    // dJ/dg per node for this thread's nodes, then one mode at a time
+    double wts[kFgNodes / 256];
+#pragma unroll
+    for (int r = 0; r < kFgNodes / 256; ++r) {
+        const long long i = i0 + threadIdx.x + 256 * r;
+        double wg = 0.0;
+        if (i < i1) {
+            double g = 0.0;
+            for (int k = 0; k < K; ++k) g += (double)psi[(size_t)i * K + k] * sxi[k];
+            const double dj = dJ_ds0[(size_t)b * N + i];
+            if (marginal == PD_MARG_LOGNORMAL) {
+                wg = dj * sig * exp(mu + sig * g);
+            } else {
+                const double q = 0.5 * erfc(g / 1.4142135623730951);
+                const double pdf = exp(-0.5 * g * g) / 2.5066282746310002;
+                wg = dj * (wscale / m_w) * pow(-log(q), 1.0 / m_w - 1.0) * pdf / q;
+            }
+        }
+        wts[r] = wg;
+    }
+    for (int k = 0; k < K; ++k) {
+        double v = 0.0;
+#pragma unroll
+        for (int r = 0; r < kFgNodes / 256; ++r) {
+            const long long i = i0 + threadIdx.x + 256 * r;
+            if (i < i1) v += wts[r] * (double)psi[(size_t)i * K + k];
+        }
+        red[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[((size_t)b * nchunks + chunk) * K + k] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_field_grad_sum(int B, int K, int nchunks, const double *partial, double *out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B * K) return;
+    const int b = t / K, k = t % K;
+    double v = 0.0;
+    for (int c = 0; c < nchunks; ++c) v += partial[((size_t)b * nchunks + c) * K + k];
+    out[t] = v;
+}
+
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    ~DevBuf() { cudaFree(p); }
+};
+
+}  // namespace pdi
+
+using namespace pdi;
+
+extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int32_t n_obs, const int32_t *obs_steps,
+                          const double *dJ_dR, const float *s0, const float *kappa, double *grad_s0,
+                          double *grad_kappa, double *R_obs, pd_stream stream) {
+    PD_REQUIRE(st != nullptr, "state is NULL");
+    PD_REQUIRE(n_steps >= 1 && ckpt_every >= 1, "n_steps >= 1 and ckpt_every >= 1 required");
+    PD_REQUIRE(n_obs >= 0 && (n_obs == 0 || (obs_steps && dJ_dR)), "obs_steps and dJ_dR are required");
+    PD_REQUIRE(s0 && grad_s0, "s0 and grad_s0 are required");
+    for (int o = 0; o < n_obs; ++o)
+        PD_REQUIRE(obs_steps[o] >= 0 && obs_steps[o] < n_steps, "obs_steps[%d] = %d outside [0, %d)", o,
+                   obs_steps[o], n_steps);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int B = st->B;
+    const long long N = st->N, nb = st->nb, U3 = (long long)B * N * 3, D1 = (long long)B * nb;
+    const int k = std::min(ckpt_every, n_steps);
+    const int nseg = (n_steps + k - 1) / k;
+    int32_t n0 = 0;
+    PD_CHECK_CUDA(cudaStreamSynchronize(s));
+    PD_CHECK_CUDA(cudaMemcpy(&n0, st->step + st->bk_par * B, sizeof(int32_t), cudaMemcpyDeviceToHost));
+
+    DevBuf<double> ck_u, ck_v, ck_d, tr_u, tr_d, lu, lun, lv, lF, ld, rbuf;
+    DevBuf<int32_t> obs;
+    PD_TRY(dalloc(&ck_u.p, (size_t)(nseg + 1) * U3));  // checkpoints + the final state
+    PD_TRY(dalloc(&ck_v.p, (size_t)(nseg + 1) * U3));
+    PD_TRY(dalloc(&ck_d.p, (size_t)(nseg + 1) * D1));
+    PD_TRY(dalloc(&tr_u.p, (size_t)k * U3));
+    PD_TRY(dalloc(&tr_d.p, (size_t)(k + 1) * D1));
+    PD_TRY(dalloc(&lu.p, U3));
+    PD_TRY(dalloc(&lun.p, U3));
+    PD_TRY(dalloc(&lv.p, U3));
+    PD_TRY(dalloc(&lF.p, U3));
+    PD_TRY(dalloc(&ld.p, D1));
+    PD_TRY(dalloc(&rbuf.p, (size_t)B * k));
+    PD_TRY(dalloc(&obs.p, std::max(n_obs, 1)));
+    if (n_obs) PD_CHECK_CUDA(cudaMemcpyAsync(obs.p, obs_steps, n_obs * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+
+    // forward with checkpoints (the first load clears run bookkeeping, e.g. done flags)
+    for (int g = 0; g < nseg; ++g) {
+        const int start = g * k, len = std::min(k, n_steps - start);
+        PD_TRY(pd_state_store(st, ck_u.p + (size_t)g * U3, ck_v.p + (size_t)g * U3, ck_d.p + (size_t)g * D1, stream));
+        if (g == 0) PD_TRY(pd_state_load(st, ck_u.p, ck_v.p, ck_d.p, n0, stream));
+        PD_TRY(pd_step(st, len, rbuf.p, stream));
+        if (R_obs && n_obs) {
+            k_gather_obs<<<(B * n_obs + 255) / 256, 256, 0, s>>>(B, len, start, n_obs, obs.p, rbuf.p, R_obs);
+            PD_CHECK_LAUNCH();
+        }
+    }
+    PD_TRY(pd_state_store(st, ck_u.p + (size_t)nseg * U3, ck_v.p + (size_t)nseg * U3, ck_d.p + (size_t)nseg * D1,
+                          stream));
+
+    AdjArgs a;
+    a.B = B;
+    a.N = N;
+    a.nb = nb;
+    a.nx = st->g.nx;
+    a.ny = st->g.ny;
+    a.dx = st->g.dx;
+    a.c = st->c;
+    a.V = st->V;
+    a.dt = st->dt;
+    a.rho = st->mat.rho;
+    a.a = 1.0 - 0.5 * st->mat.zeta * st->dt;
+    a.b = 1.0 + 0.5 * st->mat.zeta * st->dt;
+    a.law = st->mat.law;
+    a.s_ratio = st->mat.s_ratio;
+    a.k = st->mat.k;
+    a.alpha = st->mat.alpha;
+    a.row_ptr = st->row_ptr;
+    a.col = st->col_csr;
+    a.codes = st->codes;
+    a.s0 = s0;
+    a.kappa = kappa;
+    a.n_obs = n_obs;
+    a.obs = obs.p;
+    a.w = dJ_dR;
+    PD_CHECK_CUDA(cudaMemsetAsync(lu.p, 0, U3 * sizeof(double), s));
+    PD_CHECK_CUDA(cudaMemsetAsync(lv.p, 0, U3 * sizeof(double), s));
+    PD_CHECK_CUDA(cudaMemsetAsync(ld.p, 0, D1 * sizeof(double), s));
+    PD_CHECK_CUDA(cudaMemsetAsync(grad_s0, 0, (size_t)B * N * sizeof(double), s));
+    if (grad_kappa) PD_CHECK_CUDA(cudaMemsetAsync(grad_kappa, 0, (size_t)B * N * sizeof(double), s));
+    const unsigned nblk_dof = (unsigned)((U3 + 255) / 256);
+    const unsigned nblk_bond = (unsigned)(((long long)B * N * 32 + 255) / 256);
+    double *plu = lu.p, *plun = lun.p;
+    for (int g = nseg - 1; g >= 0; --g) {
+        const int start = g * k, len = std::min(k, n_steps - start);
+        PD_TRY(pd_state_load(st, ck_u.p + (size_t)g * U3, ck_v.p + (size_t)g * U3, ck_d.p + (size_t)g * D1,
+                             n0 + start, stream));
+        for (int m = 0; m < len; ++m) {
+            PD_TRY(pd_state_store(st, tr_u.p + (size_t)m * U3, nullptr, tr_d.p + (size_t)m * D1, stream));
+            PD_TRY(pd_step(st, 1, nullptr, stream));
+        }
+        PD_TRY(pd_state_store(st, nullptr, nullptr, tr_d.p + (size_t)len * D1, stream));
+        for (int m = len - 1; m >= 0; --m) {
+            k_adj_nodes<<<nblk_dof, 256, 0, s>>>(a, start + m, plu, lv.p, lF.p, plun);
+            PD_CHECK_LAUNCH();
+            k_adj_bonds<<<nblk_bond, 256, 0, s>>>(a, tr_u.p + (size_t)m * U3, tr_d.p + (size_t)m * D1,
+                                                  tr_d.p + (size_t)(m + 1) * D1, lF.p, ld.p, plun, grad_s0,
+                                                  grad_kappa);
+            PD_CHECK_LAUNCH();
+            std::swap(plu, plun);
+        }
+    }
+    // leave the state where the forward run left it
+    PD_TRY(pd_state_load(st, ck_u.p + (size_t)nseg * U3, ck_v.p + (size_t)nseg * U3, ck_d.p + (size_t)nseg * D1,
+                         n0 + n_steps, stream));
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("adjoint failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return PD_ERR_CUDA;
+    }
+    return PD_OK;
+}
+
+// The field's basis and marginal parameters live in pd_field.cu.
+int field_grad_inputs(const pd_field *f, int level, const float **psi, long long *N, int *K, int *marginal,
+                      double *mu, double *sig, double *wscale, double *m_w);
+
+extern "C" int pd_field_adjoint(const pd_field *f, int32_t level, const double *xi, int32_t B, const double *dJ_ds0,
+                                double *dJ_dxi, pd_stream stream) {
+    PD_REQUIRE(f && xi && dJ_ds0 && dJ_dxi, "field, xi, dJ_ds0 and dJ_dxi are required");
+    PD_REQUIRE(B >= 0, "B must be >= 0");
+    if (B == 0) return PD_OK;
+    const float *psi;
+    long long N;
+    int K, marginal;
+    double mu, sig, wscale, m_w;
+    PD_TRY(field_grad_inputs(f, level, &psi, &N, &K, &marginal, &mu, &sig, &wscale, &m_w));
+    PD_REQUIRE(K <= kFgMaxK, "n_modes above %d", kFgMaxK);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nchunks = (int)((N + kFgNodes - 1) / kFgNodes);
+    DevBuf<double> part;
+    PD_TRY(dalloc(&part.p, (size_t)B * nchunks * K));
+    k_field_grad_partial<<<dim3(nchunks, B), 256, 0, s>>>(N, K, psi, xi, dJ_ds0, marginal, mu, sig, wscale, m_w,
+                                                          nchunks, part.p);
+    PD_CHECK_LAUNCH();
+    k_field_grad_sum<<<(B * K + 255) / 256, 256, 0, s>>>(B, K, nchunks, part.p, dJ_dxi);
+    PD_CHECK_LAUNCH();
+    PD_CHECK_CUDA(cudaStreamSynchronize(s));  // the partials are freed on return
+    return PD_OK;
+}

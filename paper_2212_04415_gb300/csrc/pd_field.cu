@@ -435,6 +435,29 @@ extern "C" int pd_field_info(const pd_field *f, int32_t *n_modes, double *lambda
     return PD_OK;
 }
 
+// Inputs of the coefficient gradient (pd_adjoint.cu): the level's basis with
+// sqrt(lambda) folded in and the marginal's parameters.
+int field_grad_inputs(const pd_field *f, int level, const float **psi, long long *N, int *K, int *marginal,
+                      double *mu, double *sig, double *wscale, double *m_w) {
+    PD_REQUIRE(level >= 0 && level < f->n_levels, "level out of range");
+    const pd_grid &g = f->grid[level];
+    const pd_field_cfg &c = f->cfg;
+    *psi = f->phi[level];
+    *N = (long long)g.nx * g.ny * g.nz;
+    *K = f->K;
+    *marginal = c.marginal;
+    *mu = *sig = *wscale = *m_w = 0.0;
+    if (c.marginal == PD_MARG_LOGNORMAL) {
+        const double s2 = std::log(1.0 + c.cov * c.cov);
+        *mu = std::log(c.mean) - 0.5 * s2;
+        *sig = std::sqrt(s2);
+    } else {
+        *wscale = c.mean / std::tgamma(1.0 + 1.0 / c.weibull_m);
+        *m_w = c.weibull_m;
+    }
+    return PD_OK;
+}
+
 static int sample_level(const pd_field *f, int level, const double *xi, int B, float *out, cudaStream_t s) {
     const pd_field_cfg &c = f->cfg;
     double mu = 0, sig = 0, wscale = 0, winvm = 0;

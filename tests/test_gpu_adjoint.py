@@ -1,0 +1,175 @@
+"""Discrete adjoint on the GPU (pd_adjoint, pd_field_adjoint and the autograd
+function) against the oracle's adjoint, against central differences of the
+GPU's own forward run, and for checkpoint-independence."""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+import pd_workloads as W
+from oracle import core, field
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pd(built_lib):
+    import paper_2212_04415_gb300 as pd
+    return pd
+
+
+def _case():
+    w = W.tiny_beam(16, 6, 4, n_steps=1500)
+    return dataclasses.replace(w, bc=dataclasses.replace(w.bc, u_max=2.5e-5))
+
+
+def _fields(w, B, seed=0):
+    """Float32 node fields (the precision the state receives) and their FP64 copies."""
+    Phi, lam = field.kl_separable(w.grid, w.field.length, w.field.n_modes)
+    s0 = field.sample_field(w, Phi, lam, w.seed, 0, list(range(seed, seed + B)))
+    kap = np.exp(0.1 * np.random.default_rng(seed + 1).standard_normal((B, w.grid.n_nodes)))
+    return np.ascontiguousarray(s0, np.float32), np.ascontiguousarray(kap, np.float32)
+
+
+@pytest.mark.parametrize("prec,T", [("fp64", 150), ("fp64", 300), ("mixed", 300)])
+def test_node_gradients_against_oracle(pd, prec, T):
+    w = _case()
+    g = w.grid
+    B = 2
+    s0, kap = _fields(w, B)
+    row, col = pd.build_neighbours(g)
+    precision = pd.PREC_FP64 if prec == "fp64" else pd.PREC_MIXED
+    st = pd.State(g, row, col, w.mat, w.bc, batch=B, precision=precision)
+    s0d, kd = torch.tensor(s0, device="cuda"), torch.tensor(kap, device="cuda")
+    obs = [T - 1, T // 2, T - 40]
+    wts = np.array([[1.0, 0.5, -0.3], [-0.7, 1.0, 0.2]])
+    st.reset(s0d, kd)
+    gs, gk, R = st.adjoint(T, obs, torch.tensor(wts, device="cuda"), s0d, kd, ckpt_every=64)
+    gs, gk, R = gs.cpu().numpy(), gk.cpu().numpy(), R.cpu().numpy()
+    tol = 1e-8 if prec == "fp64" else 2e-3
+    for b in range(B):
+        m = core.Model(w, s0=s0[b].astype(np.float64), kappa=kap[b].astype(np.float64), dt=st.dt)
+        ogs, ogk = m.adjoint(T, obs, wts[b])
+        rr = m.run(T)["reaction"]
+        es = np.abs(gs[b] - ogs).max() / max(np.abs(ogs).max(), 1e-300)
+        ek = np.abs(gk[b] - ogk).max() / np.abs(ogk).max()
+        er = np.abs(R[b] - rr[obs]).max() / np.abs(rr[obs]).max()
+        print(f"{prec} T={T} sample {b}: grad_s0 err {es:.2e} (max {np.abs(ogs).max():.3e}), "
+              f"grad_kappa err {ek:.2e}, R err {er:.2e}")
+        assert er <= (1e-10 if prec == "fp64" else 1e-5)
+        assert ek <= tol
+        if np.abs(ogs).max() == 0:
+            assert np.all(gs[b] == 0)
+        else:
+            assert es <= tol
+    st.close()
+
+
+def test_checkpoint_interval_does_not_change_the_gradient(pd):
+    w = _case()
+    s0, kap = _fields(w, 1, seed=3)
+    row, col = pd.build_neighbours(w.grid)
+    st = pd.State(w.grid, row, col, w.mat, w.bc, batch=1, precision=pd.PREC_FP64)
+    s0d, kd = torch.tensor(s0, device="cuda"), torch.tensor(kap, device="cuda")
+    wts = torch.tensor([[1.0, -0.5]], dtype=torch.float64, device="cuda")
+    out = []
+    for k in (1000, 64, 7):
+        st.reset(s0d, kd)
+        out.append(st.adjoint(260, [259, 100], wts, s0d, kd, ckpt_every=k))
+    for a, b in zip(out[0], out[1]):
+        assert torch.equal(a, b)
+    for a, b in zip(out[0], out[2]):
+        assert torch.equal(a, b)
+    # the state is left where the forward run ends
+    st.reset(s0d, kd)
+    R = st.step(260)
+    u_ref = st.store()[0]
+    st.reset(s0d, kd)
+    st.adjoint(260, [259], wts[:, :1].contiguous(), s0d, kd, ckpt_every=64)
+    assert torch.equal(st.store()[0], u_ref)
+    st.close()
+
+
+def _kl(pd, w, K_k=8):
+    fk_cfg = W.FieldCfg(W.COV_SQEXP, w.field.length, K_k, W.MARG_LOGNORMAL, 1.0, 0.1)
+    return pd.Field(w.grid, 1, w.field), pd.Field(w.grid, 1, fk_cfg), fk_cfg
+
+
+@pytest.mark.parametrize("T", [150, 300])
+def test_coefficient_gradient_against_oracle_chain(pd, T):
+    w = _case()
+    row, col = pd.build_neighbours(w.grid)
+    st = pd.State(w.grid, row, col, w.mat, w.bc, batch=2, precision=pd.PREC_FP64)
+    fs, fk, fk_cfg = _kl(pd, w)
+    ids = torch.arange(2, dtype=torch.int64, device="cuda")
+    xs = pd.draw_xi(w.seed, 0, ids, w.field.n_modes).requires_grad_(True)
+    xk = pd.draw_xi(w.seed + 1, 0, ids, fk_cfg.n_modes).requires_grad_(True)
+    obs = [T - 1, T // 2]
+    R = pd.reaction_at(xs, xk, st, fs, fk, 0, T, obs, ckpt_every=50)
+    wts = torch.tensor([[1.0, -0.4], [0.3, 1.0]], dtype=torch.float64, device="cuda")
+    (R * wts).sum().backward()
+    g_s, g_k = xs.grad.cpu().numpy(), xk.grad.cpu().numpy()
+    Phi, lam = field.kl_separable(w.grid, w.field.length, w.field.n_modes)
+    Pk, lk = field.kl_separable(w.grid, fk_cfg.length, fk_cfg.n_modes)
+    xs_h, xk_h = xs.detach().cpu().numpy(), xk.detach().cpu().numpy()
+    for b in range(2):
+        s0 = field.lognormal(field.gaussian(Phi, lam, xs_h[b:b + 1]), w.field.mean, w.field.cov)[0]
+        kap = field.lognormal(field.gaussian(Pk, lk, xk_h[b:b + 1]), 1.0, 0.1)[0]
+        m = core.Model(w, s0=s0, kappa=kap, dt=st.dt)
+        ogs, ogk = m.adjoint(T, obs, wts[b].cpu().numpy())
+        o_s = field.grad_xi(w.field, Phi, lam, xs_h[b:b + 1], ogs[None])[0]
+        o_k = field.grad_xi(fk_cfg, Pk, lk, xk_h[b:b + 1], ogk[None])[0]
+        ek = np.abs(g_k[b] - o_k).max() / np.abs(o_k).max()
+        es = np.abs(g_s[b] - o_s).max() / max(np.abs(o_s).max(), 1e-300)
+        print(f"T={T} sample {b}: dJ/dxi_k err {ek:.2e}, dJ/dxi_s err {es:.2e} (max {np.abs(o_s).max():.3e})")
+        assert ek <= 1e-5
+        if np.abs(o_s).max() == 0:
+            assert np.all(g_s[b] == 0)
+        else:
+            assert es <= 1e-4
+    st.close()
+    fs.close()
+    fk.close()
+
+
+def test_coefficient_gradient_against_central_differences(pd):
+    """Elastic window, stiffness coefficients: adjoint vs central differences of
+    the GPU's own FP64 forward run, 1e-4 relative. The state takes its fields
+    in FP32, so a step of h on xi moves kappa by ~3e-2 h relative, and at
+    h = 1e-3 the FP32 rounding of kappa (6e-8) is 2e-3 of the step; h = 1e-2
+    keeps that noise well below the tolerance while the elastic response
+    stays smooth (truncation ~1e-7, as the oracle's pins show)."""
+    w = _case()
+    T = 150
+    row, col = pd.build_neighbours(w.grid)
+    st = pd.State(w.grid, row, col, w.mat, w.bc, batch=1, precision=pd.PREC_FP64)
+    fs, fk, fk_cfg = _kl(pd, w)
+    ids = torch.arange(1, dtype=torch.int64, device="cuda")
+    xs = pd.draw_xi(w.seed, 0, ids, w.field.n_modes)
+    xk = pd.draw_xi(w.seed + 1, 0, ids, fk_cfg.n_modes).requires_grad_(True)
+    obs = [T - 1, 90]
+    wv = torch.tensor([[1.0, 0.5]], dtype=torch.float64, device="cuda")
+    (pd.reaction_at(xs, xk, st, fs, fk, 0, T, obs) * wv).sum().backward()
+    grad = xk.grad[0].cpu().numpy()
+    # FD noise from the FP32 rounding of kappa: |dJ| <= sum_i |dJ/dkappa_i kappa_i| 2^-24 per run
+    kap = fk.sample(0, xk.detach())
+    st.reset(fs.sample(0, xs), kap)
+    _, gk, _ = st.adjoint(T, obs, wv, fs.sample(0, xs), kap)
+    jitter = float((gk * kap.double()).abs().sum()) * 2.0 ** -24
+
+    def J(x):
+        with torch.no_grad():
+            return float((pd.reaction_at(xs, x, st, fs, fk, 0, T, obs) * wv).sum())
+    h = 1e-2
+    for k in range(fk_cfg.n_modes):
+        p = xk.detach().clone()
+        q = xk.detach().clone()
+        p[0, k] += h
+        q[0, k] -= h
+        fd = (J(p) - J(q)) / (2 * h)
+        print(f"dJ/dxi_k[{k}]: adjoint {grad[k]:.9e} fd {fd:.9e} (FD noise bound {jitter / h:.1e})")
+        assert abs(grad[k] - fd) <= 1e-4 * abs(fd) + jitter / h
+    st.close()
+    fs.close()
+    fk.close()
