@@ -165,6 +165,30 @@ PD_API int pd_bc_codes(const pd_grid *g, const pd_bc *bc, uint8_t *codes, pd_str
 PD_API int pd_state_create(const pd_grid *g, const int32_t *row_ptr, const int32_t *col,
                     int64_t n_bonds, const pd_material *mat, const pd_bc *bc, int32_t batch,
                     pd_state **out);
+
+/* Launch schedule of a state: bricks of 8 x by x bz nodes per block (by bz
+ * even and <= 32 on the compile-time stencil path) and q warps sharing each
+ * row pair's half-stencil (1, 2 or 4; 0 = the built-in choice). A schedule
+ * changes the summation grouping, not the method: results agree to rounding.
+ * The paper has no counterpart. */
+typedef struct pd_schedule {
+    int32_t by, bz, q;
+} pd_schedule;
+
+/* pd_state_create with an explicit schedule (NULL: the built-in choice). */
+PD_API int pd_state_create_sched(const pd_grid *g, const int32_t *row_ptr, const int32_t *col,
+                                 int64_t n_bonds, const pd_material *mat, const pd_bc *bc,
+                                 int32_t batch, const pd_schedule *sched, pd_state **out);
+
+/* Autotuner: times trial_steps captured steps of every candidate schedule of
+ * this mesh and batch (a state per candidate, uniform fields, CUDA events) and
+ * returns the fastest with its time per step in microseconds (best_us may be
+ * NULL). Results are cached per (grid, batch, law, precision, horizon) for the
+ * life of the process, so repeated calls cost nothing. Host-synchronous;
+ * allocates one candidate state at a time. */
+PD_API int pd_autotune(const pd_grid *g, const int32_t *row_ptr, const int32_t *col, int64_t n_bonds,
+                       const pd_material *mat, const pd_bc *bc, int32_t batch, int32_t trial_steps,
+                       pd_schedule *best, double *best_us);
 PD_API int pd_state_destroy(pd_state *st);
 
 /* dt [s], micromodulus c, node and bond counts of a state (host outputs, any may be NULL). */
@@ -296,6 +320,8 @@ typedef struct pd_mlmc_cfg {
     int32_t batch;                /* samples per launch (<= 4096) */
     const int64_t *first_sample;  /* [n_levels] id of the first sample of each level, or NULL (0): a
                                      process of a sharded run takes ids first .. first + n - 1 */
+    int32_t tune_steps;           /* > 0: schedules from pd_autotune with this many trial steps per
+                                     candidate (fine and coarse states); 0: the built-in choice */
 } pd_mlmc_cfg;
 
 typedef struct pd_mlmc_level {

@@ -51,7 +51,11 @@ class MlmcCfg(C.Structure):
     _fields_ = [("n_levels", C.c_int32), ("grid", C.POINTER(Grid)), ("bc", C.POINTER(BC)),
                 ("max_steps", C.POINTER(C.c_int32)), ("n_samples", C.POINTER(C.c_int64)),
                 ("mat", Material), ("field", FieldCfg), ("seed", C.c_uint64), ("batch", C.c_int32),
-                ("first_sample", C.POINTER(C.c_int64))]
+                ("first_sample", C.POINTER(C.c_int64)), ("tune_steps", C.c_int32)]
+
+
+class Schedule(C.Structure):
+    _fields_ = [("by", C.c_int32), ("bz", C.c_int32), ("q", C.c_int32)]
 
 
 class MlmcLevel(C.Structure):
@@ -75,6 +79,10 @@ _SIGS = {
     "pd_state_create": (C.c_int, [C.POINTER(Grid), _VP, _VP, C.c_int64, C.POINTER(Material), C.POINTER(BC),
                                   C.c_int32, C.POINTER(_VP)]),
     "pd_state_destroy": (C.c_int, [_VP]),
+    "pd_state_create_sched": (C.c_int, [C.POINTER(Grid), _VP, _VP, C.c_int64, C.POINTER(Material), C.POINTER(BC),
+                                        C.c_int32, C.POINTER(Schedule), C.POINTER(_VP)]),
+    "pd_autotune": (C.c_int, [C.POINTER(Grid), _VP, _VP, C.c_int64, C.POINTER(Material), C.POINTER(BC), C.c_int32,
+                              C.c_int32, C.POINTER(Schedule), C.POINTER(C.c_double)]),
     "pd_state_info": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int64)]),
     "pd_state_reset": (C.c_int, [_VP, _VP, _VP, _VP]),
@@ -180,15 +188,18 @@ def bc_codes(g, b, stream=None):
 class State:
     """B independent samples of the explicit peridynamic dynamics on one mesh."""
 
-    def __init__(self, g, row, col, mat, bc, batch=1, precision=PREC_MIXED, dt=0.0):
+    def __init__(self, g, row, col, mat, bc, batch=1, precision=PREC_MIXED, dt=0.0, schedule=None):
+        """schedule: None (built-in choice) or (by, bz, q), e.g. from ``autotune``."""
         import torch
         torch.cuda.synchronize()
         self.grid = g
         self.B = batch
         self._G, self._M, self._BC = grid_struct(g), material_struct(mat, precision, dt), bc_struct(bc)
         h = C.c_void_p()
-        _check(lib().pd_state_create(C.byref(self._G), _ptr(row), _ptr(col), int(col.numel()),
-                                     C.byref(self._M), C.byref(self._BC), batch, C.byref(h)))
+        sch = Schedule(*schedule) if schedule is not None else None
+        _check(lib().pd_state_create_sched(C.byref(self._G), _ptr(row), _ptr(col), int(col.numel()),
+                                           C.byref(self._M), C.byref(self._BC), batch,
+                                           C.byref(sch) if sch is not None else None, C.byref(h)))
         self.h = h
         dtv, cv, nn, nb = C.c_double(), C.c_double(), C.c_int64(), C.c_int64()
         _check(lib().pd_state_info(h, C.byref(dtv), C.byref(cv), C.byref(nn), C.byref(nb)))
@@ -251,6 +262,17 @@ class State:
                                 _ptr(dJ_dR), _ptr(s0), _ptr(kappa), _ptr(gs), _ptr(gk), _ptr(R),
                                 _stream(stream)))
         return gs, gk, R
+
+
+def autotune(g, row, col, mat, bc, batch=1, precision=PREC_MIXED, trial_steps=20, dt=0.0):
+    """Fastest launch schedule (by, bz, q) of a mesh and batch, and its time per
+    step in microseconds (pd_autotune; cached per process)."""
+    G, M, BCs = grid_struct(g), material_struct(mat, precision, dt), bc_struct(bc)
+    best = Schedule()
+    us = C.c_double()
+    _check(lib().pd_autotune(C.byref(G), _ptr(row), _ptr(col), int(col.numel()), C.byref(M), C.byref(BCs), batch,
+                             trial_steps, C.byref(best), C.byref(us)))
+    return (best.by, best.bz, best.q), us.value
 
 
 def draw_xi(seed, level, sample_ids, n_modes, stream=None, out=None):
@@ -317,7 +339,7 @@ class Field:
 
 
 def mlmc_estimate(grids, bcs, max_steps, n_samples, mat, field, seed, batch, precision=PREC_MIXED,
-                  first_sample=None, return_samples=False, stream=None):
+                  first_sample=None, return_samples=False, tune_steps=0, stream=None):
     """Fixed-allocation MLMC over len(grids) nested levels (coarsest first).
 
     Returns per-level totals, the estimator, and the per-batch FP64 sums
@@ -330,7 +352,8 @@ def mlmc_estimate(grids, bcs, max_steps, n_samples, mat, field, seed, batch, pre
     ms = (C.c_int32 * L)(*max_steps)
     ns = (C.c_int64 * L)(*n_samples)
     fs = (C.c_int64 * L)(*(first_sample if first_sample is not None else [0] * L))
-    cfg = MlmcCfg(L, G, Bc, ms, ns, material_struct(mat, precision), field_struct(field), seed, batch, fs)
+    cfg = MlmcCfg(L, G, Bc, ms, ns, material_struct(mat, precision), field_struct(field), seed, batch, fs,
+                  tune_steps)
     res = MlmcResult()
     tot = int(sum(n_samples))
     nbat = [(n + min(batch, max(n, 1)) - 1) // min(batch, max(n, 1)) for n in n_samples]

@@ -16,9 +16,10 @@
 // arrive by TMA with the 128B swizzle and one thread issues the 4 x 3 MMAs of
 // the chunk. The epilogue reads the accumulators with tcgen05.ld (warps w and
 // w + 4 share TMEM lanes 32 (w mod 4) .. + 31 and split the columns), applies
-// the marginal transform and writes the node fields, coalesced along nodes. Every wait on an mbarrier has an iteration limit; on expiry the CTA
-// records an error, writes NaN into its tile and still waits (bounded) for
-// its own copies and MMAs before it frees tensor memory.
+// the marginal transform and writes the node fields, coalesced along nodes.
+// Every wait on an mbarrier has an iteration limit; on expiry the CTA records
+// an error, writes NaN into its tile and still waits (bounded) for its own
+// copies and MMAs before it frees tensor memory.
 #include <cuda.h>
 
 #include <mutex>

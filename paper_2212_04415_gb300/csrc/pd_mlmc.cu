@@ -121,9 +121,20 @@ static int run_level(const pd_mlmc_cfg *cfg, pd_field *field, int l, pd_mlmc_lev
             pd_state_destroy(sf);
             pd_state_destroy(sc);
             sf = sc = nullptr;
-            if ((rc = pd_state_create(&cfg->grid[l], mf.row, mf.col, mf.nb, &cfg->mat, &cfg->bc[l], b, &sf))) break;
-            if (l > 0 && (rc = pd_state_create(&cfg->grid[l - 1], mc.row, mc.col, mc.nb, &cfg->mat, &cfg->bc[l - 1],
-                                               b, &sc)))
+            pd_schedule shf{0, 0, 0}, shc{0, 0, 0};
+            if (cfg->tune_steps > 0) {
+                if ((rc = pd_autotune(&cfg->grid[l], mf.row, mf.col, mf.nb, &cfg->mat, &cfg->bc[l], b,
+                                      cfg->tune_steps, &shf, nullptr)))
+                    break;
+                if (l > 0 && (rc = pd_autotune(&cfg->grid[l - 1], mc.row, mc.col, mc.nb, &cfg->mat, &cfg->bc[l - 1],
+                                               b, cfg->tune_steps, &shc, nullptr)))
+                    break;
+            }
+            if ((rc = pd_state_create_sched(&cfg->grid[l], mf.row, mf.col, mf.nb, &cfg->mat, &cfg->bc[l], b,
+                                            cfg->tune_steps > 0 ? &shf : nullptr, &sf)))
+                break;
+            if (l > 0 && (rc = pd_state_create_sched(&cfg->grid[l - 1], mc.row, mc.col, mc.nb, &cfg->mat,
+                                                     &cfg->bc[l - 1], b, cfg->tune_steps > 0 ? &shc : nullptr, &sc)))
                 break;
             cur_b = b;
         }

@@ -20,6 +20,7 @@
 // compile-time offsets.
 #include <cmath>
 #include <cstdlib>
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -380,13 +381,23 @@ bool stencil_applicable(const pd_state *st) {
            st->by * st->bz <= 32;
 }
 
+// The dynamic shared-memory limit of the stencil kernels only ever grows (per
+// device): states of several meshes coexist (the fine and coarse members of
+// MLMC pairs) and each launches with its own brick size.
 int stencil_set_attributes(size_t smem) {
+    static std::mutex mu;
+    static size_t limit[64] = {};
+    int dev = 0;
+    PD_CHECK_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && smem <= limit[dev]) return PD_OK;
     for (int q = 1; q <= 4; q *= 2)
         for (int law = 0; law < 2; ++law)
             for (int kap = 0; kap < 2; ++kap)
                 for (int fo = 0; fo < 2; ++fo)
                     PD_CHECK_CUDA(cudaFuncSetAttribute((const void *)pick_stencil(q, law, kap, fo),
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (dev >= 0 && dev < 64) limit[dev] = smem;
     return PD_OK;
 }
 
@@ -402,6 +413,7 @@ int stencil_build(pd_state *st, const int32_t *col) {
         const int v = std::atoi(e);
         if (v == 1 || v == 2 || v == 4) st->st_q = v;
     }
+    if (st->q_req) st->st_q = st->q_req;
     while (st->st_q > 1 && 32 * st->st_wpb * st->st_q > 512) st->st_q /= 2;
     st->smem_bytes += (size_t)(st->st_q - 1) * st->st_wpb * 16 * 6 * sizeof(float);
     std::vector<int16_t> box(343, -1);

@@ -42,6 +42,7 @@
 #include <array>
 #include <cmath>
 #include <cstdlib>
+#include <mutex>
 #include <vector>
 
 #include "pd_device.cuh"
@@ -683,8 +684,15 @@ static int launch_step(const pd_state *st, const StepArgs &a, bool force_only, c
 }
 
 // Dynamic shared memory limit of every generic step kernel (set at state
-// creation, outside any stream capture).
+// creation, outside any stream capture). It only ever grows (per device):
+// states of several meshes coexist and each launches with its own size.
 static int generic_set_attributes(size_t smem) {
+    static std::mutex mu;
+    static size_t limit[64] = {};
+    int dev = 0;
+    PD_CHECK_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && smem <= limit[dev]) return PD_OK;
     for (int f = 0; f < 2; ++f)
         for (int fo = 0; fo < 2; ++fo)
             for (int law = 0; law < 2; ++law)
@@ -694,6 +702,7 @@ static int generic_set_attributes(size_t smem) {
                     PD_CHECK_CUDA(
                         cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
                 }
+    if (dev >= 0 && dev < 64) limit[dev] = smem;
     return PD_OK;
 }
 
@@ -951,8 +960,9 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
 
 using namespace pdi;
 
-extern "C" int pd_state_create(const pd_grid *g, const int32_t *row_ptr, const int32_t *col, int64_t n_bonds,
-                               const pd_material *mat, const pd_bc *bc, int32_t batch, pd_state **out) {
+extern "C" int pd_state_create_sched(const pd_grid *g, const int32_t *row_ptr, const int32_t *col,
+                                     int64_t n_bonds, const pd_material *mat, const pd_bc *bc, int32_t batch,
+                                     const pd_schedule *sched, pd_state **out) {
     PD_REQUIRE(out != nullptr, "out is NULL");
     *out = nullptr;
     PD_TRY(validate_grid(g));
@@ -1013,6 +1023,21 @@ extern "C" int pd_state_create(const pd_grid *g, const int32_t *row_ptr, const i
                 st->bz = z;
             }
         }
+        if (sched && (sched->by > 0 || sched->bz > 0)) {
+            if (sched->by < 1 || sched->by > 16 || sched->bz < 1 || sched->bz > 16) {
+                delete st;
+                set_error("schedule bricks %d x %d outside [1, 16]", sched->by, sched->bz);
+                return PD_ERR_ARG;
+            }
+            st->by = sched->by;
+            st->bz = sched->bz;
+        }
+        st->q_req = sched ? sched->q : 0;
+        if (st->q_req != 0 && st->q_req != 1 && st->q_req != 2 && st->q_req != 4) {
+            delete st;
+            set_error("schedule q = %d is not 0, 1, 2 or 4", st->q_req);
+            return PD_ERR_ARG;
+        }
     }
     const double delta = g->m_ratio * g->dx;
     st->c = 12.0 * mat->E / (M_PI * delta * delta * delta * delta);
@@ -1024,6 +1049,11 @@ extern "C" int pd_state_create(const pd_grid *g, const int32_t *row_ptr, const i
     }
     *out = st;
     return PD_OK;
+}
+
+extern "C" int pd_state_create(const pd_grid *g, const int32_t *row_ptr, const int32_t *col, int64_t n_bonds,
+                               const pd_material *mat, const pd_bc *bc, int32_t batch, pd_state **out) {
+    return pd_state_create_sched(g, row_ptr, col, n_bonds, mat, bc, batch, nullptr, out);
 }
 
 extern "C" int pd_state_destroy(pd_state *st) {

@@ -108,3 +108,21 @@ def test_mlmc_rejects_unnested_grids(pd):
     a["grids"] = [levels[0].grid, levels[0].grid]
     with pytest.raises(pd.PdError, match="refinement"):
         pd.mlmc_estimate(batch=4, **a)
+
+
+def test_states_of_two_meshes_coexist(pd):
+    """A state created after another (smaller bricks) must not break the first
+    one's launches, captured or not (the fine and coarse members of a pair)."""
+    import torch
+    fine, coarse = W.beam(2.5), W.beam(5.0)
+    rf, cf = pd.build_neighbours(fine.grid)
+    rc, cc = pd.build_neighbours(coarse.grid)
+    big = pd.State(fine.grid, rf, cf, fine.mat, fine.bc, batch=16)    # 8x4x4 bricks
+    small = pd.State(coarse.grid, rc, cc, coarse.mat, coarse.bc, batch=1)
+    R = big.step(3)
+    pk, _, nd = big.run_to_peak(70)
+    small.step(3)
+    torch.cuda.synchronize()
+    assert torch.isfinite(R).all() and (nd == 70).all()
+    big.close()
+    small.close()

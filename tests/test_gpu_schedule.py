@@ -1,0 +1,85 @@
+"""Launch schedules and the autotuner: every schedule regroups the same
+arithmetic, so trajectories agree to rounding; the autotuner returns one of
+its candidates, caches it, and MLMC with tuned schedules matches the built-in
+choice to rounding."""
+import numpy as np
+import pytest
+import torch
+
+import pd_workloads as W
+from oracle import field
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pd(built_lib):
+    import paper_2212_04415_gb300 as pd
+    return pd
+
+
+SCHEDULES = [(2, 2, 1), (2, 2, 4), (4, 2, 1), (4, 2, 2), (4, 4, 1), (8, 2, 1), (2, 8, 2), (6, 2, 1)]
+
+
+def _run(pd, w, row, col, s0, sched, n=120):
+    st = pd.State(w.grid, row, col, w.mat, w.bc, batch=s0.shape[0], schedule=sched)
+    st.reset(s0)
+    R = st.step(n)
+    u = st.store()[0]
+    st.close()
+    return R, u
+
+
+def test_every_schedule_gives_the_same_trajectory(pd):
+    levels = W.small_beam_levels()
+    w = levels[1]
+    row, col = pd.build_neighbours(w.grid)
+    Phi, lam = field.kl_separable(w.grid, w.field.length, w.field.n_modes)
+    s0 = field.sample_field(w, Phi, lam, w.seed, 1, [0, 1, 2])
+    s0 = torch.tensor(np.ascontiguousarray(s0, np.float32), device="cuda")
+    R0, u0 = _run(pd, w, row, col, s0, None)
+    for sch in SCHEDULES:
+        R, u = _run(pd, w, row, col, s0, sch)
+        er = ((R - R0).abs().max() / R0.abs().max()).item()
+        eu = ((u - u0).abs().max() / u0.abs().max()).item()
+        print(f"schedule {sch}: reaction {er:.1e}, displacement {eu:.1e}")
+        assert er <= 1e-6 and eu <= 1e-6
+
+
+def test_bad_schedules_are_rejected(pd):
+    w = W.small_beam_levels()[0]
+    row, col = pd.build_neighbours(w.grid)
+    for sch in [(0, 2, 1), (17, 1, 1), (2, 2, 3)]:
+        with pytest.raises(pd.PdError):
+            pd.State(w.grid, row, col, w.mat, w.bc, schedule=sch)
+
+
+def test_autotune_picks_a_candidate_and_caches(pd):
+    w = W.beam(5.0)
+    row, col = pd.build_neighbours(w.grid)
+    import time
+    t0 = time.perf_counter()
+    sch, us = pd.autotune(w.grid, row, col, w.mat, w.bc, batch=64, trial_steps=10)
+    t1 = time.perf_counter()
+    sch2, us2 = pd.autotune(w.grid, row, col, w.mat, w.bc, batch=64, trial_steps=10)
+    t2 = time.perf_counter()
+    print(f"tuned {sch} at {us:.1f} us/step in {t1 - t0:.2f} s; cached call {1e3 * (t2 - t1):.3f} ms")
+    assert sch == sch2 and us == us2 and us > 0
+    by, bz, q = sch
+    assert (by * bz) % 2 == 0 and by * bz <= 32 and q in (1, 2, 4)
+    assert t2 - t1 < 0.05
+    st = pd.State(w.grid, row, col, w.mat, w.bc, batch=64, schedule=sch)
+    st.step(2)
+    st.close()
+
+
+def test_mlmc_with_tuned_schedules(pd):
+    levels = W.small_beam_levels()
+    a = dict(grids=[w.grid for w in levels], bcs=[w.bc for w in levels], max_steps=[w.n_steps for w in levels],
+             n_samples=[4, 2], mat=levels[0].mat, field=levels[0].field, seed=levels[0].seed, batch=4)
+    base = pd.mlmc_estimate(return_samples=True, **a)
+    tuned = pd.mlmc_estimate(return_samples=True, tune_steps=5, **a)
+    for key in ("q_fine", "q_coarse"):
+        d = np.abs(tuned[key] - base[key]).max() / np.abs(base[key]).max()
+        print(key, d)
+        assert d <= 1e-5
