@@ -152,6 +152,75 @@ def cpu_baseline_leg(n_steps: int = 300):
                       f"{w.grid.nz} notched beam, FP64, single thread ({el:.1f} s)"}
 
 
+def mlmc_leg(pd, W, dist, tune_steps: int = 10, tol: float = 1e-3):
+    """MLMC on the notched-beam hierarchy (dx = 5 / 2.5 / 1.25 mm, 1024 / 128 / 16
+    samples, coupled pairs): batched (every level's samples in one launch,
+    autotuned schedules) against the plain path (one sample per launch), and
+    the allocation and time needed for a relative RMSE `tol` of the mean peak
+    load. Under torchrun every rank takes whole batches of each level and the
+    level sums are merged on the host (shard.merge)."""
+    import math
+
+    import torch
+
+    from paper_2212_04415_gb300 import shard
+    lv = W.beam_levels()
+    a = dict(grids=[w.grid for w in lv], bcs=[w.bc for w in lv], max_steps=[w.n_steps for w in lv],
+             mat=lv[0].mat, field=lv[0].field, seed=lv[0].seed)
+    n_samples = [w.batch for w in lv]
+    batch = max(n_samples)
+    ws = dist.get_world_size() if dist else 1
+    rank = dist.get_rank() if dist else 0
+    first, count = shard.split(n_samples, batch, ws, rank)
+    # schedules of every (level, member, batch) are tuned before the timed run (the tuner caches them)
+    meshes = [pd.build_neighbours(w.grid) for w in lv]
+    for l, c in enumerate(count):
+        b = min(batch, c)
+        if b < 1:
+            continue
+        pd.autotune(lv[l].grid, *meshes[l], lv[l].mat, lv[l].bc, batch=b, trial_steps=tune_steps)
+        if l > 0:
+            pd.autotune(lv[l - 1].grid, *meshes[l - 1], lv[l - 1].mat, lv[l - 1].bc, batch=b, trial_steps=tune_steps)
+    del meshes
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    local = pd.mlmc_estimate(n_samples=count, batch=batch, tune_steps=tune_steps, first_sample=first, **a)
+    wall = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([wall], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        wall = float(t[0])
+    merged = shard.merge(shard.allgather(local["batch_sums"]))
+    # plain path: one sample per launch on a few samples of every level
+    plain_n = [8, 4, 2]
+    plain = pd.mlmc_estimate(n_samples=plain_n, batch=1, first_sample=[2_000_000] * 3, **a)
+    plain_cost = [lv_["cost_s"] / lv_["n"] for lv_ in plain["levels"]]
+    plain_time = sum(n * c for n, c in zip(n_samples, plain_cost))
+    # cost per sample of every level from the batched run; allocation for the tolerance
+    C = [max(lv_["cost_s"], 1e-12) / max(lv_["n"], 1) for lv_ in local["levels"]]
+    V = [lv_["var"] for lv_ in merged["levels"]]
+    eps = tol * abs(merged["q_ml"])
+    eps_s = eps / math.sqrt(2.0)
+    N_tol = pd.mlmc_allocation(V, C, eps_s)
+    total = sum(n_samples)
+    return {
+        "workload": "notched beam hierarchy dx 5 / 2.5 / 1.25 mm (3,500 / 28,000 / 224,000 nodes), "
+                    "1024 / 128 / 16 samples, coupled pairs",
+        "samples": total, "wall_s": wall, "samples_per_s": total / wall,
+        "compute_s": sum(lv_["cost_s"] for lv_ in local["levels"]),
+        "plain_samples_per_s": total / plain_time, "speedup_vs_plain": plain_time / wall,
+        "plain_sample": f"{plain_n} samples per level, one per launch, extrapolated per level",
+        "bond_updates_per_s": sum(lv_["bond_updates"] for lv_ in local["levels"]) * ws / wall,
+        "q_ml": merged["q_ml"], "rel_rmse": math.sqrt(max(merged["var_ml"], 0.0)) / abs(merged["q_ml"]),
+        "levels": [{"n": m["n"], "mean": m["mean"], "var": m["var"], "cost_per_sample_s": c}
+                   for m, c in zip(merged["levels"], C)],
+        "tolerance": {"rel": tol, "eps_s": eps_s, "n_per_level": [int(x) for x in N_tol],
+                      "time_s": sum(int(n) * c for n, c in zip(N_tol, C)) / ws},
+    }
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -191,6 +260,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--batched", type=int, default=32, help="samples per launch for the batched comparison (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mlmc", action="store_true", help="skip the MLMC hierarchy leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -351,6 +421,8 @@ def main():
                      "algorithmic_bytes_per_launch": alg_bytes, "launch_us": per_launch_ms * 1e3},
         "batched": batched,
     }
+    if not args.no_mlmc:
+        line["mlmc"] = mlmc_leg(pd, W, dist)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg()
     if rank == 0:
