@@ -359,6 +359,33 @@ PD_API int mlmc_estimate(const pd_mlmc_cfg *cfg, pd_mlmc_result *out, double *q_
 PD_API int pd_mlmc_allocation(int32_t n_levels, const double *V, const double *C, double eps_s,
                        int64_t *N);
 
+/* Settings of the adaptive estimator (Algorithm MLMC, Section 4.2). */
+typedef struct pd_mlmc_adaptive_cfg {
+    double eps_s;              /* sampling tolerance of Eq. sample_allocation [units of Q] */
+    double eps_b;              /* bias tolerance: stop once |Y_hat_L| / (m_dof^alpha - 1) < eps_b
+                                  (Eq. bias_error with r = 1) */
+    double m_dof;              /* ratio of degrees of freedom between levels (8 in 3D) */
+    double alpha;              /* rate of |Y_hat_l| ~ M_l^-alpha (Eq. alpha_convergence_mlmc) */
+    int32_t n_star;            /* warm-up samples on every new level (the paper uses 100) */
+    const double *cost_model;  /* [n_levels] cost per sample, or NULL: the measured GPU time */
+} pd_mlmc_adaptive_cfg;
+
+/* Adaptive MLMC (Algorithm MLMC): start with level 0; on each new level L
+ * take n_star samples; re-allocate N_l (Eq. sample_allocation, floor) for
+ * l <= L from the level variances (Eq. sample_variance) and costs, and top
+ * every level up to N_l with new sample ids (level l's samples are ids
+ * first_sample[l] + 0, 1, ...); stop once the bias estimate of Eq.
+ * bias_error falls below eps_b or L reaches cfg->n_levels - 1, else add a
+ * level. cfg->n_samples is ignored (may be NULL). out receives the level
+ * statistics of levels 0..L (n_levels = L + 1), L_used the last level,
+ * bias the final bias estimate. q_fine/q_coarse (host, optional, capacity
+ * cap entries) receive every sample's Q_l and Q_{l-1} level after level in
+ * id order; PD_ERR_CAP (with out filled) when the run took more than cap
+ * samples. Host-synchronous. */
+PD_API int mlmc_adaptive(const pd_mlmc_cfg *cfg, const pd_mlmc_adaptive_cfg *ad, pd_mlmc_result *out,
+                         int32_t *L_used, double *bias, double *q_fine, double *q_coarse, int64_t cap,
+                         pd_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,11 @@ class MlmcCfg(C.Structure):
                 ("first_sample", C.POINTER(C.c_int64)), ("tune_steps", C.c_int32)]
 
 
+class AdaptiveCfg(C.Structure):
+    _fields_ = [("eps_s", C.c_double), ("eps_b", C.c_double), ("m_dof", C.c_double), ("alpha", C.c_double),
+                ("n_star", C.c_int32), ("cost_model", C.POINTER(C.c_double))]
+
+
 class Schedule(C.Structure):
     _fields_ = [("by", C.c_int32), ("bz", C.c_int32), ("q", C.c_int32)]
 
@@ -97,6 +102,8 @@ _SIGS = {
     "pd_field_info": (C.c_int, [_VP, C.POINTER(C.c_int32), _VP]),
     "pd_sample_field": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, _VP, _VP, _VP]),
     "mlmc_estimate": (C.c_int, [C.POINTER(MlmcCfg), C.POINTER(MlmcResult), _VP, _VP, _VP, _VP]),
+    "mlmc_adaptive": (C.c_int, [C.POINTER(MlmcCfg), C.POINTER(AdaptiveCfg), C.POINTER(MlmcResult),
+                                C.POINTER(C.c_int32), C.POINTER(C.c_double), _VP, _VP, C.c_int64, _VP]),
     "pd_adjoint": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "pd_field_adjoint": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, _VP, _VP, _VP]),
     "pd_mlmc_allocation": (C.c_int, [C.c_int32, _VP, _VP, C.c_double, _VP]),
@@ -377,6 +384,41 @@ def mlmc_estimate(grids, bcs, max_steps, n_samples, mat, field, seed, batch, pre
     if return_samples:
         out["q_fine"], out["q_coarse"] = qf[:tot], qc[:tot]
     return out
+
+
+def mlmc_adaptive(grids, bcs, max_steps, mat, field, seed, batch, eps_s, eps_b, m_dof=8.0, alpha=1.0,
+                  n_star=100, cost_model=None, first_sample=None, cap=1 << 20, precision=PREC_MIXED,
+                  tune_steps=0, stream=None):
+    """Adaptive MLMC (Algorithm MLMC) over up to len(grids) levels: returns the
+    last level L, the bias estimate, per-level statistics, the estimator and
+    every sample's (Q_l, Q_{l-1}) per level, in id order."""
+    import numpy as np
+    L = len(grids)
+    G = (Grid * L)(*[grid_struct(g) for g in grids])
+    Bc = (BC * L)(*[bc_struct(b) for b in bcs])
+    ms = (C.c_int32 * L)(*max_steps)
+    fs = (C.c_int64 * L)(*(first_sample if first_sample is not None else [0] * L))
+    cfg = MlmcCfg(L, G, Bc, ms, None, material_struct(mat, precision), field_struct(field), seed, batch, fs,
+                  tune_steps)
+    cm = (C.c_double * L)(*cost_model) if cost_model is not None else None
+    ad = AdaptiveCfg(eps_s, eps_b, m_dof, alpha, n_star, cm)
+    res = MlmcResult()
+    Lu, eb = C.c_int32(), C.c_double()
+    qf = np.zeros(cap)
+    qc = np.zeros(cap)
+    _check(lib().mlmc_adaptive(C.byref(cfg), C.byref(ad), C.byref(res), C.byref(Lu), C.byref(eb),
+                               qf.ctypes.data_as(C.c_void_p), qc.ctypes.data_as(C.c_void_p), cap,
+                               _stream(stream)))
+    levels, q = [], []
+    o = 0
+    for l in range(res.n_levels):
+        lv = res.level[l]
+        levels.append(dict(n=lv.n, sum_y=lv.sum_y, sum_y2=lv.sum_y2, mean=lv.mean, var=lv.var,
+                           var_unbiased=lv.var_unbiased, cost_s=lv.cost_s, steps=lv.steps,
+                           bond_updates=lv.bond_updates))
+        q.append((qf[o:o + lv.n].copy(), qc[o:o + lv.n].copy()))
+        o += lv.n
+    return dict(L=Lu.value, bias=eb.value, levels=levels, q_ml=res.q_ml, var_ml=res.var_ml, samples=q)
 
 
 def mlmc_allocation(V, Cst, eps_s):

@@ -253,3 +253,111 @@ extern "C" int mlmc_estimate(const pd_mlmc_cfg *cfg, pd_mlmc_result *out, double
     *out = r;
     return PD_OK;
 }
+
+// Adaptive MLMC (Algorithm MLMC). Level l's samples are taken in id order
+// across rounds (warm-up, then top-ups), each round one call of run_level.
+extern "C" int mlmc_adaptive(const pd_mlmc_cfg *cfg, const pd_mlmc_adaptive_cfg *ad, pd_mlmc_result *out,
+                             int32_t *L_used, double *bias, double *q_fine, double *q_coarse, int64_t cap,
+                             pd_stream stream) {
+    PD_REQUIRE(cfg && ad && out, "cfg, ad and out are required");
+    PD_REQUIRE(cfg->n_levels >= 1 && cfg->n_levels <= PD_MAX_LEVELS, "n_levels out of range");
+    PD_REQUIRE(cfg->grid && cfg->bc && cfg->max_steps, "per-level grids, bcs and max_steps are required");
+    PD_REQUIRE(cfg->batch >= 1 && cfg->batch <= 4096, "batch must be in [1, 4096]");
+    PD_REQUIRE(ad->eps_s > 0 && ad->eps_b > 0, "eps_s and eps_b must be positive");
+    PD_REQUIRE(ad->m_dof > 1 && ad->alpha > 0, "m_dof > 1 and alpha > 0 required");
+    PD_REQUIRE(ad->n_star >= 2, "n_star must be >= 2");
+    for (int l = 1; l < cfg->n_levels; ++l) {
+        const pd_grid &f = cfg->grid[l], &c = cfg->grid[l - 1];
+        PD_REQUIRE(f.nx == 2 * c.nx && f.ny == 2 * c.ny && f.nz == 2 * c.nz &&
+                       std::fabs(f.dx * 2.0 - c.dx) <= 1e-12 * c.dx,
+                   "grid %d is not the 2x refinement of grid %d", l, l - 1);
+    }
+    if (ad->cost_model)
+        for (int l = 0; l < cfg->n_levels; ++l) PD_REQUIRE(ad->cost_model[l] > 0, "cost_model must be positive");
+    cudaStream_t s = (cudaStream_t)stream;
+    pd_field *field = nullptr;
+    PD_TRY(pd_field_create(&cfg->grid[cfg->n_levels - 1], cfg->n_levels, &cfg->field, &field));
+
+    const int Lmax = cfg->n_levels - 1;
+    pd_mlmc_level acc[PD_MAX_LEVELS];
+    memset(acc, 0, sizeof(acc));
+    std::vector<double> qf[PD_MAX_LEVELS], qc[PD_MAX_LEVELS];
+    int64_t ns[PD_MAX_LEVELS] = {0}, fs[PD_MAX_LEVELS] = {0};
+    pd_mlmc_cfg c2 = *cfg;
+    c2.n_samples = ns;
+    c2.first_sample = fs;
+    // take n more samples on level l (ids continue from the samples already taken)
+    auto take = [&](int l, int64_t n) -> int {
+        for (int k = 0; k <= Lmax; ++k) ns[k] = 0;
+        ns[l] = n;
+        fs[l] = (cfg->first_sample ? cfg->first_sample[l] : 0) + acc[l].n;
+        pd_mlmc_level lv;
+        std::vector<double> f(n), c(n);
+        PD_TRY(run_level(&c2, field, l, &lv, f.data(), c.data(), nullptr, s));
+        acc[l].n += lv.n;
+        acc[l].sum_y += lv.sum_y;
+        acc[l].sum_y2 += lv.sum_y2;
+        acc[l].cost_s += lv.cost_s;
+        acc[l].steps += lv.steps;
+        acc[l].bond_updates += lv.bond_updates;
+        qf[l].insert(qf[l].end(), f.begin(), f.end());
+        qc[l].insert(qc[l].end(), c.begin(), c.end());
+        return PD_OK;
+    };
+    auto mean_of = [&](int l) { return acc[l].n ? acc[l].sum_y / (double)acc[l].n : 0.0; };
+    auto var_of = [&](int l) {
+        const double m = mean_of(l);
+        return acc[l].n ? acc[l].sum_y2 / (double)acc[l].n - m * m : 0.0;
+    };
+    int rc = PD_OK;
+    int L = 0;
+    double eb = 0.0;
+    while (rc == PD_OK) {
+        if ((rc = take(L, ad->n_star))) break;
+        std::vector<double> V(L + 1), C(L + 1);
+        std::vector<int64_t> Nh(L + 1);
+        for (int l = 0; l <= L; ++l) {
+            V[l] = std::max(var_of(l), 0.0);
+            C[l] = ad->cost_model ? ad->cost_model[l] : std::max(acc[l].cost_s / (double)acc[l].n, 1e-12);
+        }
+        if ((rc = pd_mlmc_allocation(L + 1, V.data(), C.data(), ad->eps_s, Nh.data()))) break;
+        for (int l = 0; l <= L && rc == PD_OK; ++l)
+            if (Nh[l] > acc[l].n) rc = take(l, Nh[l] - acc[l].n);
+        if (rc) break;
+        eb = std::fabs(mean_of(L)) / (std::pow(ad->m_dof, ad->alpha) - 1.0);
+        if (eb < ad->eps_b || L >= Lmax) break;
+        ++L;
+    }
+    pd_field_destroy(field);
+    if (rc != PD_OK) return rc;
+    pd_mlmc_result r;
+    memset(&r, 0, sizeof(r));
+    r.n_levels = L + 1;
+    int64_t total = 0;
+    for (int l = 0; l <= L; ++l) {
+        pd_mlmc_level &lv = acc[l];
+        lv.mean = mean_of(l);
+        lv.var = var_of(l);
+        lv.var_unbiased = lv.n > 1 ? lv.var * (double)lv.n / (double)(lv.n - 1) : 0.0;
+        r.level[l] = lv;
+        r.q_ml += lv.mean;
+        r.var_ml += lv.var / (double)lv.n;
+        total += lv.n;
+    }
+    *out = r;
+    if (L_used) *L_used = L;
+    if (bias) *bias = eb;
+    if (q_fine || q_coarse) {
+        if (total > cap) {
+            set_error("the run took %lld samples, more than cap = %lld", (long long)total, (long long)cap);
+            return PD_ERR_CAP;
+        }
+        int64_t o = 0;
+        for (int l = 0; l <= L; ++l)
+            for (size_t k = 0; k < qf[l].size(); ++k, ++o) {
+                if (q_fine) q_fine[o] = qf[l][k];
+                if (q_coarse) q_coarse[o] = qc[l][k];
+            }
+    }
+    return PD_OK;
+}

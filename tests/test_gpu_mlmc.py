@@ -126,3 +126,44 @@ def test_states_of_two_meshes_coexist(pd):
     assert torch.isfinite(R).all() and (nd == 70).all()
     big.close()
     small.close()
+
+
+def test_adaptive_mlmc_against_oracle(pd):
+    """Algorithm MLMC on the two-level small beam with a fixed cost model: the
+    GPU run and the oracle's adaptive run (on the oracle's own coupled-pair
+    physics, same sample ids) take the same decisions (last level, samples per
+    level within one), and every sample's peak loads agree within 1e-3."""
+    levels = W.small_beam_levels()
+    a = _args(levels)
+    del a["n_samples"]
+    cost = [1.0, 8.0]
+    settings = dict(eps_s=1.5, eps_b=10.0, m_dof=8.0, alpha=1.0, n_star=8)
+    res = pd.mlmc_adaptive(batch=16, cost_model=cost, cap=4096, **settings, **a)
+    print("GPU adaptive: L", res["L"], "N", [lv["n"] for lv in res["levels"]], "bias", res["bias"],
+          "Q", res["q_ml"])
+
+    taken = [0, 0]
+
+    def sampler(l, n):
+        ids = list(range(taken[l], taken[l] + n))
+        taken[l] += n
+        qf, qc = _oracle_pairs(levels, l, ids)
+        return qf - qc, cost[l]
+    ora = omlmc.adaptive(sampler, settings["eps_s"], settings["eps_b"], settings["m_dof"], settings["alpha"],
+                         n_star=settings["n_star"], L_max=len(levels) - 1)
+    print("oracle adaptive: L", ora["L"], "N", ora["N"], "bias", ora["bias"], "Q", ora["Q"])
+    assert res["L"] == ora["L"] == 1  # the bias test added the second level and then passed
+    for l in range(res["L"] + 1):
+        assert abs(res["levels"][l]["n"] - ora["N"][l]) <= 1
+        assert res["levels"][l]["n"] >= settings["n_star"]
+        # every sample of the GPU run against the oracle's run of the same id
+        qf, qc = res["samples"][l]
+        of, oc = _oracle_pairs(levels, l, list(range(len(qf))))
+        assert np.all(np.abs(qf - of) <= 1e-3 * np.abs(of))
+        if l > 0:
+            assert np.all(np.abs(qc - oc) <= 1e-3 * np.abs(oc))
+    assert abs(res["q_ml"] - ora["Q"]) <= 2e-3 * abs(ora["Q"])
+    # the same samples through the fixed-allocation estimator give the same level sums
+    fixed = pd.mlmc_estimate(n_samples=[lv["n"] for lv in res["levels"]], batch=16, **a)
+    for l in range(2):
+        assert fixed["levels"][l]["sum_y"] == pytest.approx(res["levels"][l]["sum_y"], rel=1e-12)
