@@ -359,6 +359,27 @@ PD_API int mlmc_estimate(const pd_mlmc_cfg *cfg, pd_mlmc_result *out, double *q_
 PD_API int pd_mlmc_allocation(int32_t n_levels, const double *V, const double *C, double eps_s,
                        int64_t *N);
 
+/* Multilevel inverse CDF of the peak load (Section 7):
+ * F_L^-1(u) = R_0^[N_0 u] + sum_{l>=1} (R_l^[N_l u] - R~_{l-1}^[N_l u]), with R_l
+ * and R~_{l-1} the fine and coarse members of level l's pairs sorted
+ * ascending and R^[k] the k-th smallest. Readings: [N u] = ceil(N u),
+ * 1-based, clamped to [1, N]; the coarse term of level l uses N_l.
+ * n_per_level: host int64[n_levels] (>= 1 each); q_fine, q_coarse: device
+ * double[sum N_l], level-major as mlmc_estimate returns them (q_coarse may be
+ * NULL with one level; its level-0 entries are not read); values must be
+ * finite. u, out: device double[n_u]. Host-synchronous (sorted copies are
+ * allocated per call). */
+PD_API int pd_ml_inverse_cdf(int32_t n_levels, const int64_t *n_per_level, const double *q_fine,
+                             const double *q_coarse, int32_t n_u, const double *u, double *out,
+                             pd_stream stream);
+
+/* Multilevel CDF: F(x) = (1/n_u) #{i < n_u : F_L^-1((i + 1/2) / n_u) <= x} for
+ * every x (device double[n_x]) into F (device double[n_x]); inputs as for
+ * pd_ml_inverse_cdf. Host-synchronous. */
+PD_API int pd_ml_cdf(int32_t n_levels, const int64_t *n_per_level, const double *q_fine,
+                     const double *q_coarse, int32_t n_u, int32_t n_x, const double *x, double *F,
+                     pd_stream stream);
+
 /* Settings of the adaptive estimator (Algorithm MLMC, Section 4.2). */
 typedef struct pd_mlmc_adaptive_cfg {
     double eps_s;              /* sampling tolerance of Eq. sample_allocation [units of Q] */

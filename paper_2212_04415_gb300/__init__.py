@@ -102,6 +102,8 @@ _SIGS = {
     "pd_field_info": (C.c_int, [_VP, C.POINTER(C.c_int32), _VP]),
     "pd_sample_field": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, _VP, _VP, _VP]),
     "mlmc_estimate": (C.c_int, [C.POINTER(MlmcCfg), C.POINTER(MlmcResult), _VP, _VP, _VP, _VP]),
+    "pd_ml_inverse_cdf": (C.c_int, [C.c_int32, _VP, _VP, _VP, C.c_int32, _VP, _VP, _VP]),
+    "pd_ml_cdf": (C.c_int, [C.c_int32, _VP, _VP, _VP, C.c_int32, C.c_int32, _VP, _VP, _VP]),
     "mlmc_adaptive": (C.c_int, [C.POINTER(MlmcCfg), C.POINTER(AdaptiveCfg), C.POINTER(MlmcResult),
                                 C.POINTER(C.c_int32), C.POINTER(C.c_double), _VP, _VP, C.c_int64, _VP]),
     "pd_adjoint": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
@@ -419,6 +421,38 @@ def mlmc_adaptive(grids, bcs, max_steps, mat, field, seed, batch, eps_s, eps_b, 
         q.append((qf[o:o + lv.n].copy(), qc[o:o + lv.n].copy()))
         o += lv.n
     return dict(L=Lu.value, bias=eb.value, levels=levels, q_ml=res.q_ml, var_ml=res.var_ml, samples=q)
+
+
+def _levels_flat(levels):
+    """[q0, (fine1, coarse1), ...] (device tensors) -> counts, flat fine, flat coarse."""
+    import torch
+    n = [int(levels[0].numel())] + [int(f.numel()) for f, _ in levels[1:]]
+    qf = torch.cat([levels[0].double()] + [f.double() for f, _ in levels[1:]]).contiguous()
+    qc = torch.cat([torch.zeros_like(levels[0], dtype=torch.float64)] +
+                   [c.double() for _, c in levels[1:]]).contiguous()
+    return (C.c_int64 * len(n))(*n), qf, qc
+
+
+def ml_inverse_cdf(levels, u, stream=None):
+    """F_L^-1(u) (pd_ml_inverse_cdf): levels = [Q_0, (Q_1, Q~_0), ...] device tensors."""
+    import torch
+    n, qf, qc = _levels_flat(levels)
+    u = u.double().contiguous()
+    out = torch.empty_like(u)
+    _check(lib().pd_ml_inverse_cdf(len(levels), C.cast(n, C.c_void_p), _ptr(qf), _ptr(qc), u.numel(), _ptr(u),
+                                   _ptr(out), _stream(stream)))
+    return out
+
+
+def ml_cdf(levels, x, n_u=1000, stream=None):
+    """F(x) (pd_ml_cdf) on the points F_L^-1((i + 1/2) / n_u)."""
+    import torch
+    n, qf, qc = _levels_flat(levels)
+    x = x.double().contiguous()
+    F = torch.empty_like(x)
+    _check(lib().pd_ml_cdf(len(levels), C.cast(n, C.c_void_p), _ptr(qf), _ptr(qc), n_u, x.numel(), _ptr(x),
+                           _ptr(F), _stream(stream)))
+    return F
 
 
 def mlmc_allocation(V, Cst, eps_s):
