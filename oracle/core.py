@@ -61,7 +61,7 @@ class Problem(C.Structure):
                 ("s_ratio", C.c_double), ("k", C.c_double), ("alpha", C.c_double),
                 ("dt", C.c_double), ("zeta", C.c_double), ("s0", C.c_void_p),
                 ("kappa", C.c_void_p), ("bc", C.c_void_p), ("u_max", C.c_double),
-                ("n_ramp", C.c_int32)]
+                ("n_ramp", C.c_int32), ("gf_A", C.c_double)]
 
 
 def lib():
@@ -91,6 +91,10 @@ def lib():
                                    C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_max_threads.restype = C.c_int
+        L.or_gf_coefficient.argtypes = [C.c_int32] + [C.c_double] * 5
+        L.or_gf_coefficient.restype = C.c_double
+        L.or_fracture_energy.argtypes = [C.c_int32] + [C.c_double] * 6
+        L.or_fracture_energy.restype = C.c_double
         L.or_adjoint.argtypes = [C.POINTER(Problem), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]
     return _lib
@@ -136,6 +140,17 @@ def micromodulus(E: float, delta: float) -> float:
     return lib().or_micromodulus_3d(E, delta)
 
 
+def gf_coefficient(law: int, c: float, delta: float, G_F: float, k: float = 25.0, alpha: float = 0.25) -> float:
+    """A of s_crit = s0 + A / s0 for a fracture energy G_F (or_gf_coefficient)."""
+    return lib().or_gf_coefficient(law, c, delta, G_F, k, alpha)
+
+
+def fracture_energy(law: int, c: float, delta: float, s0: float, sc: float, k: float = 25.0,
+                    alpha: float = 0.25) -> float:
+    """G_F of Eq. exp_fracture_energy (exp-linear) or of the bilinear law."""
+    return lib().or_fracture_energy(law, c, delta, s0, sc, k, alpha)
+
+
 def damage_law(law: int, s: float, s0: float, sc: float, k: float = 25.0,
                alpha: float = 0.25) -> float:
     return lib().or_damage_law(law, s, s0, sc, k, alpha)
@@ -167,9 +182,10 @@ class Model:
 
     def _mk(self):
         g, m, bc = self.w.grid, self.w.mat, self.w.bc
+        gfA = gf_coefficient(m.law, self.c, g.m_ratio * g.dx, m.G_F, m.k, m.alpha) if m.G_F > 0 else 0.0
         self.P = Problem(g.nx, g.ny, g.nz, g.dx, _p(self.row), _p(self.col), self.c, m.rho,
                          m.law, m.s_ratio, m.k, m.alpha, self.dt, m.zeta, _p(self.s0),
-                         _p(self.kappa), _p(self.codes), bc.u_max, bc.n_ramp)
+                         _p(self.kappa), _p(self.codes), bc.u_max, bc.n_ramp, gfA)
 
     def set_field(self, s0, kappa=None):
         self.s0 = np.ascontiguousarray(np.asarray(s0, np.float64))

@@ -26,7 +26,9 @@
  *   - the bilinear law d = 1 - s0 (sf - s) / (s (sf - s0)) on (s0, sf);
  *   - irreversibility d_n = max(d_{n-1}, d_law(s_n)); compression uses the
  *     stored d;
- *   - per-bond properties s0_ij = (s0_i + s0_j)/2, s_crit_ij = ratio * s0_ij,
+ *   - per-bond properties s0_ij = (s0_i + s0_j)/2, s_crit_ij = ratio * s0_ij
+ *     or, calibrated to a fracture energy G_F, s_crit_ij = s0_ij + A / s0_ij
+ *     (Eq. exp_fracture_energy solved for s_c; see or_gf_coefficient),
  *     c_ij = c (kappa_i + kappa_j)/2;
  *   - damped leapfrog (velocity-Verlet positions) integrator with
  *     mass-proportional damping zeta; stable step from the Silling-Askari
@@ -79,6 +81,8 @@ typedef struct {
     const uint8_t *bc;    /* per-DOF codes, N*3: 0 free, 1 fixed, 2 +U(n), 3 -U(n) */
     double u_max;
     int32_t n_ramp;
+    double gf_A;          /* > 0: s_crit = s0 + gf_A / s0 (from the fracture energy,
+                             or_gf_coefficient); 0: s_crit = s_ratio * s0 */
 } or_problem;
 
 /* ---------------------------------------------------------------- grid */
@@ -254,6 +258,38 @@ double or_damage_law(int32_t law, double s, double s0, double sc,
     return 1.0 - (s0 / s) * bracket / (1.0 + alpha);
 }
 
+/* Fracture-energy calibration of the critical stretch. The energy a bond
+ * absorbs while softening, w = xi * int_{s0}^{s_c} f ds (Eq. exp_bond_energy),
+ * integrated over the bonds crossing a unit area of a plane (the quadruple
+ * integral of the three-dimensional case, equal to pi delta^5 / 5 times the
+ * coefficient of xi in w) gives G_F:
+ *   exp-linear (Eq. exp_fracture_energy):
+ *     G_F = pi c s0 delta^5 (s0 - s_c) P / (10 k (e^k - 1) (1 + alpha)),
+ *     P = 2k - 2e^k + alpha k - alpha k e^k + 2;
+ *   bilinear (force c s0 at s0 falling linearly to 0 at s_c, w = c s0 xi (s_c - s0)/2):
+ *     G_F = pi c s0 delta^5 (s_c - s0) / 10.
+ * Both solve to s_c = s0 + A / s0; this returns A. Reading: the printed
+ * Eq. exp_sc has (1 + alpha) s0 where Eq. exp_fracture_energy gives s0 (the
+ * two-dimensional Eq. exp_sc_2D is consistent); the form that satisfies
+ * Eq. exp_fracture_energy is used. */
+double or_gf_coefficient(int32_t law, double c, double delta, double G_F, double k, double alpha) {
+    double d5 = delta * delta * delta * delta * delta;
+    if (law == 0) return 10.0 * G_F / (M_PI * c * d5);
+    double ek = exp(k);
+    double P = 2.0 * k - 2.0 * ek + alpha * k - alpha * k * ek + 2.0;
+    return -10.0 * k * (ek - 1.0) * (1.0 + alpha) * G_F / (M_PI * c * d5 * P);
+}
+
+/* G_F of a bond family with elastic limit s0 and critical stretch s_c (the
+ * closed forms above, before solving for s_c). */
+double or_fracture_energy(int32_t law, double c, double delta, double s0, double sc, double k, double alpha) {
+    double d5 = delta * delta * delta * delta * delta;
+    if (law == 0) return M_PI * c * s0 * d5 * (sc - s0) / 10.0;
+    double ek = exp(k);
+    double P = 2.0 * k - 2.0 * ek + alpha * k - alpha * k * ek + 2.0;
+    return M_PI * c * s0 * d5 * (s0 - sc) * P / (10.0 * k * (ek - 1.0) * (1.0 + alpha));
+}
+
 /* Stable time step, Silling-Askari bound with uniform c, times safety. */
 double or_stable_dt(const or_grid *g, const int32_t *row_ptr, const int32_t *col,
                     double c, double rho, double safety) {
@@ -310,7 +346,7 @@ static void forces(const or_problem *p, const double *u, double *d, double *F,
             double s = (L - L0) / L0;
             if (s > sm) sm = s;
             double s0 = 0.5 * (p->s0[i] + p->s0[j]);
-            double sc = p->s_ratio * s0;
+            double sc = p->gf_A > 0.0 ? s0 + p->gf_A / s0 : p->s_ratio * s0;
             double dl = or_damage_law(p->law, s, s0, sc, p->k, p->alpha);
             if (dl > d[q]) d[q] = dl;
             double cij = p->c;
@@ -444,35 +480,41 @@ int or_max_threads(void) {
 
 /* ------------------------------------------------------------ adjoint */
 
-/* Derivatives of the softening law d = D(s; s0, sc = ratio s0) on (s0, sc):
- * dD/ds and the total dD/ds0 (sc moves with s0). Zero outside (s0, sc),
- * where D is flat (0 or 1).
- *   bilinear:  D = 1 - (r s0 / s - 1) / (r - 1)
- *              dD/ds = r s0 / ((r - 1) s^2),  dD/ds0 = -r / ((r - 1) s)
+/* Derivatives of the softening law d = D(s; s0, sc) on (s0, sc), where the
+ * critical stretch follows s0 with slope dsc_ds0 (ratio r, or 1 - A/s0^2 for
+ * the fracture-energy calibration): dD/ds and the total dD/ds0 =
+ * dD/ds0|sc + dsc_ds0 dD/dsc. Zero outside (s0, sc), where D is flat.
+ *   bilinear:  D = 1 - s0 (sc - s) / (s (sc - s0))
+ *              dD/ds = s0 sc / (s^2 (sc - s0))
+ *              dD/ds0|sc = -(sc / s - 1) sc / (sc - s0)^2
+ *              dD/dsc|s0 = -s0 (1 - s0 / s) / (sc - s0)^2
  *   exp-linear (Eq. exp_damage_parameter): D = 1 - (s0/s) beta(t) / (1 + alpha),
- *              t = (s - s0) / ((r - 1) s0),
+ *              t = (s - s0) / (sc - s0),
  *              beta(t) = 1 - (1 - e^{-k t}) / (1 - e^{-k}) + alpha (1 - t),
  *              beta'(t) = -k e^{-k t} / (1 - e^{-k}) - alpha,
- *              dt/ds = 1 / ((r - 1) s0),  dt/ds0 = -s / ((r - 1) s0^2). */
-static void law_derivs(int32_t law, double s, double s0, double r, double k, double alpha,
+ *              dt/ds = 1 / (sc - s0), dt/ds0 = (s - sc) / (sc - s0)^2,
+ *              dt/dsc = -(s - s0) / (sc - s0)^2. */
+static void law_derivs(int32_t law, double s, double s0, double sc, double dsc_ds0, double k, double alpha,
                        double *dDds, double *dDds0) {
-    double sc = r * s0;
     *dDds = 0.0;
     *dDds0 = 0.0;
     if (s <= s0 || s >= sc) return;
+    double w = sc - s0;
     if (law == 0) {
-        *dDds = r * s0 / ((r - 1.0) * s * s);
-        *dDds0 = -r / ((r - 1.0) * s);
+        *dDds = s0 * sc / (s * s * w);
+        double d_s0 = -(sc / s - 1.0) * sc / (w * w);
+        double d_sc = -s0 * (1.0 - s0 / s) / (w * w);
+        *dDds0 = d_s0 + dsc_ds0 * d_sc;
         return;
     }
-    double t = (s - s0) / ((r - 1.0) * s0);
+    double t = (s - s0) / w;
     double beta = 1.0 - (1.0 - exp(-k * t)) / (1.0 - exp(-k)) + alpha * (1.0 - t);
     double dbeta = -k * exp(-k * t) / (1.0 - exp(-k)) - alpha;
-    double dtds = 1.0 / ((r - 1.0) * s0);
-    double dtds0 = -s / ((r - 1.0) * s0 * s0);
-    /* D = 1 - s0 beta / ((1 + alpha) s) */
+    double dtds = 1.0 / w, dtds0 = (s - sc) / (w * w), dtdsc = -(s - s0) / (w * w);
     *dDds = (s0 * beta / (s * s) - (s0 / s) * dbeta * dtds) / (1.0 + alpha);
-    *dDds0 = -(beta / s + (s0 / s) * dbeta * dtds0) / (1.0 + alpha);
+    double d_s0 = -(beta / s + (s0 / s) * dbeta * dtds0) / (1.0 + alpha);
+    double d_sc = -(s0 / s) * dbeta * dtdsc / (1.0 + alpha);
+    *dDds0 = d_s0 + dsc_ds0 * d_sc;
 }
 
 /* Reverse-mode derivative of J = sum_o w[o] R^{obs_step[o]} over a run of
@@ -590,12 +632,14 @@ int or_adjoint(const or_problem *p, int32_t n_steps, int32_t n_obs, const int32_
                 double s0 = 0.5 * (p->s0[i] + p->s0[j]);
                 double cij = p->c;
                 if (p->kappa) cij = p->c * 0.5 * (p->kappa[i] + p->kappa[j]);
-                double dD = or_damage_law(p->law, sv, s0, p->s_ratio * s0, p->k, p->alpha);
+                double sc = p->gf_A > 0.0 ? s0 + p->gf_A / s0 : p->s_ratio * s0;
+                double dsc = p->gf_A > 0.0 ? 1.0 - p->gf_A / (s0 * s0) : p->s_ratio;
+                double dD = or_damage_law(p->law, sv, s0, sc, p->k, p->alpha);
                 int active = dD > dprev[q];
                 double d = dcur[q];
                 double lamd_tot = ld[q] + cij * V * h * ydl;
                 double dDds = 0.0, dDds0 = 0.0;
-                if (active) law_derivs(p->law, sv, s0, p->s_ratio, p->k, p->alpha, &dDds, &dDds0);
+                if (active) law_derivs(p->law, sv, s0, sc, dsc, p->k, p->alpha, &dDds, &dDds0);
                 for (int c = 0; c < 3; ++c) {
                     double dh = y[c] / (L * L * L0) - sv * y[c] / (L * L * L);
                     double lamy = -cij * V * (1.0 - d) * (ydl * dh + h * dl[c]);

@@ -78,6 +78,7 @@ class Material:
     alpha: float = 0.25         # exp-linear transition (Section 6.2)
     dt_safety: float = 0.5      # fraction of the stable time step
     zeta: float = 0.0           # mass-proportional damping rate [1/s]
+    G_F: float = 0.0            # fracture energy [N/m]; > 0: s_crit from G_F per bond, s_ratio unused
 
 
 @dataclass(frozen=True)
