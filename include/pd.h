@@ -90,7 +90,18 @@ typedef struct pd_material {
     double dt_safety;
     double zeta;
     int32_t precision;
+    double G_F;         /* fracture energy [N/m]; > 0: per-bond critical stretch
+                           s_c = s0 + A / s0 with A from pd_gf_coefficient (s_ratio unused) */
 } pd_material;
+
+/* A of the fracture-energy calibration s_c = s0 + A / s0 (Appendix A): Eq.
+ * exp_fracture_energy solved for s_c for the exp-linear law (k, alpha), and
+ * the same construction (bond energy c s0 xi (s_c - s0) / 2 over the bonds
+ * crossing a unit plane, pi delta^5 / 5) for the bilinear law; c = 12E /
+ * (pi delta^4). Reading: the printed Eq. exp_sc has (1 + alpha) s0 where Eq.
+ * exp_fracture_energy gives s0; the consistent form is used. Host only. */
+PD_API int pd_gf_coefficient(int32_t law, double E, double delta, double G_F, double k, double alpha,
+                             double *A);
 
 /* Displacement control: prescribed magnitude U(n) = u_max min(n, n_ramp) / n_ramp.
  * PD_BC_BAR_TENSION: the first grip_planes x-planes are fixed; the last

@@ -33,7 +33,7 @@ class Grid(C.Structure):
 class Material(C.Structure):
     _fields_ = [("E", C.c_double), ("rho", C.c_double), ("law", C.c_int32), ("s_ratio", C.c_double),
                 ("k", C.c_double), ("alpha", C.c_double), ("dt", C.c_double), ("dt_safety", C.c_double),
-                ("zeta", C.c_double), ("precision", C.c_int32)]
+                ("zeta", C.c_double), ("precision", C.c_int32), ("G_F", C.c_double)]
 
 
 class BC(C.Structure):
@@ -102,6 +102,8 @@ _SIGS = {
     "pd_field_info": (C.c_int, [_VP, C.POINTER(C.c_int32), _VP]),
     "pd_sample_field": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, _VP, _VP, _VP]),
     "mlmc_estimate": (C.c_int, [C.POINTER(MlmcCfg), C.POINTER(MlmcResult), _VP, _VP, _VP, _VP]),
+    "pd_gf_coefficient": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                    C.POINTER(C.c_double)]),
     "pd_ml_inverse_cdf": (C.c_int, [C.c_int32, _VP, _VP, _VP, C.c_int32, _VP, _VP, _VP]),
     "pd_ml_cdf": (C.c_int, [C.c_int32, _VP, _VP, _VP, C.c_int32, C.c_int32, _VP, _VP, _VP]),
     "mlmc_adaptive": (C.c_int, [C.POINTER(MlmcCfg), C.POINTER(AdaptiveCfg), C.POINTER(MlmcResult),
@@ -160,7 +162,8 @@ def grid_struct(g) -> Grid:
 
 
 def material_struct(m, precision: int, dt: float = 0.0) -> Material:
-    return Material(m.E, m.rho, m.law, m.s_ratio, m.k, m.alpha, dt, m.dt_safety, m.zeta, precision)
+    return Material(m.E, m.rho, m.law, m.s_ratio, m.k, m.alpha, dt, m.dt_safety, m.zeta, precision,
+                    getattr(m, "G_F", 0.0))
 
 
 def bc_struct(b) -> BC:
@@ -271,6 +274,13 @@ class State:
                                 _ptr(dJ_dR), _ptr(s0), _ptr(kappa), _ptr(gs), _ptr(gk), _ptr(R),
                                 _stream(stream)))
         return gs, gk, R
+
+
+def gf_coefficient(law, E, delta, G_F, k=25.0, alpha=0.25):
+    """A of s_crit = s0 + A / s0 for a fracture energy G_F (pd_gf_coefficient)."""
+    A = C.c_double()
+    _check(lib().pd_gf_coefficient(law, E, delta, G_F, k, alpha, C.byref(A)))
+    return A.value
 
 
 def autotune(g, row, col, mat, bc, batch=1, precision=PREC_MIXED, trial_steps=20, dt=0.0):

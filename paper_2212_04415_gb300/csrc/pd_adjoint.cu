@@ -41,7 +41,7 @@ struct AdjArgs {
     int nx, ny;
     double dx, c, V, dt, rho, a, b;
     int law;
-    double s_ratio, k, alpha;
+    double s_ratio, k, alpha, gfA;
     const int32_t *row_ptr, *col;
     const uint8_t *codes;
     const float *s0, *kappa;
@@ -50,25 +50,33 @@ struct AdjArgs {
     const double *w;     // [B][n_obs]
 };
 
-// dD/ds and the total dD/ds0 (s_crit = ratio s0) on (s0, s_crit); zero outside.
+// dD/ds and the total dD/ds0 = dD/ds0|sc + (dsc/ds0) dD/dsc on (s0, sc),
+// zero outside; sc = ratio s0 (dsc/ds0 = ratio) or s0 + A/s0 (1 - A/s0^2).
+//   bilinear D = 1 - s0 (sc - s) / (s (sc - s0)):
+//     dD/ds = s0 sc / (s^2 w), dD/ds0|sc = -(sc/s - 1) sc / w^2,
+//     dD/dsc|s0 = -s0 (1 - s0/s) / w^2, w = sc - s0
+//   exp-linear D = 1 - (s0/s) beta(t) / (1 + alpha), t = (s - s0) / w:
+//     dt/ds = 1/w, dt/ds0 = (s - sc)/w^2, dt/dsc = -(s - s0)/w^2,
+//     beta' = -k e^{-kt} / (1 - e^{-k}) - alpha
 __device__ __forceinline__ void law_derivs(const AdjArgs &a, double s, double s0, double &dDds, double &dDds0) {
-    const double r = a.s_ratio;
+    const double sc = a.gfA > 0.0 ? s0 + a.gfA / s0 : a.s_ratio * s0;
+    const double dsc = a.gfA > 0.0 ? 1.0 - a.gfA / (s0 * s0) : a.s_ratio;
     dDds = 0.0;
     dDds0 = 0.0;
-    if (s <= s0 || s >= r * s0) return;
-    if (a.law == PD_LAW_BILINEAR) {  // D = 1 - (r s0 / s - 1) / (r - 1)
-        dDds = r * s0 / ((r - 1.0) * s * s);
-        dDds0 = -r / ((r - 1.0) * s);
+    if (s <= s0 || s >= sc) return;
+    const double w = sc - s0;
+    if (a.law == PD_LAW_BILINEAR) {
+        dDds = s0 * sc / (s * s * w);
+        dDds0 = -(sc / s - 1.0) * sc / (w * w) + dsc * (-s0 * (1.0 - s0 / s) / (w * w));
         return;
     }
-    // D = 1 - (s0 / s) beta(t) / (1 + alpha), t = (s - s0) / ((r - 1) s0)
-    const double t = (s - s0) / ((r - 1.0) * s0);
+    const double t = (s - s0) / w;
     const double e = exp(-a.k * t), ek = 1.0 - exp(-a.k);
     const double beta = 1.0 - (1.0 - e) / ek + a.alpha * (1.0 - t);
     const double dbeta = -a.k * e / ek - a.alpha;
-    const double dtds = 1.0 / ((r - 1.0) * s0), dtds0 = -s / ((r - 1.0) * s0 * s0);
+    const double dtds = 1.0 / w, dtds0 = (s - sc) / (w * w), dtdsc = -(s - s0) / (w * w);
     dDds = (s0 * beta / (s * s) - (s0 / s) * dbeta * dtds) / (1.0 + a.alpha);
-    dDds0 = -(beta / s + (s0 / s) * dbeta * dtds0) / (1.0 + a.alpha);
+    dDds0 = (-(beta / s + (s0 / s) * dbeta * dtds0) - dsc * (s0 / s) * dbeta * dtdsc) / (1.0 + a.alpha);
 }
 
 // Integrator adjoint of local step `ls`: lamF, lamv (in place) and the carried
@@ -322,6 +330,7 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
     a.s_ratio = st->mat.s_ratio;
     a.k = st->mat.k;
     a.alpha = st->mat.alpha;
+    a.gfA = st->gfA;
     a.row_ptr = st->row_ptr;
     a.col = st->col_csr;
     a.codes = st->codes;

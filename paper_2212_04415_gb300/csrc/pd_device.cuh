@@ -75,6 +75,8 @@ struct StepArgs {
     // the same constants rounded to FP32 on the host: a conversion from FP64
     // in the kernel would run on the FP64 pipe, which is narrow on this part
     float cVf, s_ratio_f, k_f, alpha_f, inv_1mek_f, inv_1pa_f;
+    double gfA;   // > 0: s_crit = s0 + gfA / s0, else s_ratio s0
+    float gfA_f;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -147,6 +149,15 @@ __device__ __forceinline__ double law_damage<double>(int law, double s, double s
     const double t = (s - s0) / (sc - s0);
     const double br = 1.0 - (1.0 - exp(-k * t)) * inv_1mek + alpha * (1.0 - t);
     return 1.0 - (s0 / s) * br * inv_1pa;
+}
+
+// Critical stretch of a bond with elastic limit s0: the fixed ratio, or the
+// fracture-energy calibration s0 + A / s0.
+__device__ __forceinline__ float crit_stretch(float s0, float ratio, float A) {
+    return A > 0.f ? s0 + __fdividef(A, s0) : ratio * s0;
+}
+__device__ __forceinline__ double crit_stretch(double s0, double ratio, double A) {
+    return A > 0.0 ? s0 + A / s0 : ratio * s0;
 }
 
 __device__ __forceinline__ double ramp(const StepArgs &a, int n) {

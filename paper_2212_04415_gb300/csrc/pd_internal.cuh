@@ -76,6 +76,7 @@ struct pd_state {
     int64_t N;
     int64_t nb;
     double dt, c, V;
+    double gfA;             // > 0: s_crit = s0 + gfA / s0 (fracture-energy calibration)
     // neighbour list: CSR copy and a brick-ordered SELL-8 layout of stencil ids
     int32_t *row_ptr;
     int32_t by, bz;         // brick = 8 x by x bz nodes; one slice = 8 x-consecutive nodes

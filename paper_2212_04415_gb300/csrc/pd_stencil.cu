@@ -61,7 +61,7 @@ __host__ __device__ constexpr I3 half_off(int m) {
 template <int LAW, bool KAPPA>
 __device__ __forceinline__ void stencil_bond(int m, float d, const float4 *tab, const int *offb, const char *own,
                                              float4 hi, float4 lo, float *dm, float cV, float sr, float kf, float af,
-                                             float i1, float i2, float &px, float &py, float &pz) {
+                                             float i1, float i2, float gfa, float &px, float &py, float &pz) {
     const float4 k = tab[m];
     const char *rj = own + offb[m];
     const float4 hj = *(const float4 *)rj;
@@ -76,7 +76,7 @@ __device__ __forceinline__ void stencil_bond(int m, float d, const float4 *tab, 
     const float s = __fdividef(2.0f * (k.x * ex + k.y * ey + k.z * ez) + (ex * ex + ey * ey + ez * ez), k.w * (L + k.w));
     const float s0 = 0.5f * (hi.w + hj.w);
     if (s > s0) {
-        const float dl = law_damage<float>(LAW, s, s0, sr * s0, kf, af, i1, i2);
+        const float dl = law_damage<float>(LAW, s, s0, crit_stretch(s0, sr, gfa), kf, af, i1, i2);
         if (dl > d) {
             d = dl;
             dm[32 * m] = d;
@@ -99,7 +99,7 @@ __device__ __forceinline__ void stencil_bond(int m, float d, const float4 *tab, 
 template <int G, int LAW, bool KAPPA>
 __device__ __forceinline__ void bond_span(int m0, const float4 *tab, const int *offb, const char *own, float4 hi,
                                           float4 lo, float *dm, float cV, float sr, float kf, float af, float i1,
-                                          float i2, float *acc) {
+                                          float i2, float gfa, float *acc) {
     static_assert(G % 2 == 0, "even number of groups");
     float da[8], db[8];
 #pragma unroll
@@ -112,7 +112,7 @@ __device__ __forceinline__ void bond_span(int m0, const float4 *tab, const int *
         float px = 0.f, py = 0.f, pz = 0.f;
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-            stencil_bond<LAW, KAPPA>(ma + u, da[u], tab, offb, own, hi, lo, dm, cV, sr, kf, af, i1, i2, px, py, pz);
+            stencil_bond<LAW, KAPPA>(ma + u, da[u], tab, offb, own, hi, lo, dm, cV, sr, kf, af, i1, i2, gfa, px, py, pz);
         two_sum_acc(acc[0], acc[3], px);
         two_sum_acc(acc[1], acc[4], py);
         two_sum_acc(acc[2], acc[5], pz);
@@ -123,7 +123,7 @@ __device__ __forceinline__ void bond_span(int m0, const float4 *tab, const int *
         px = py = pz = 0.f;
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-            stencil_bond<LAW, KAPPA>(mb + u, db[u], tab, offb, own, hi, lo, dm, cV, sr, kf, af, i1, i2, px, py, pz);
+            stencil_bond<LAW, KAPPA>(mb + u, db[u], tab, offb, own, hi, lo, dm, cV, sr, kf, af, i1, i2, gfa, px, py, pz);
         two_sum_acc(acc[0], acc[3], px);
         two_sum_acc(acc[1], acc[4], py);
         two_sum_acc(acc[2], acc[5], pz);
@@ -215,7 +215,8 @@ __global__ void __launch_bounds__(512, 2) k_step_stencil(const StepArgs a) {
             constexpr int R = kRounds / Q;
             float *dm = (float *)a.dmg + (size_t)b * a.sell_len + ((size_t)brick * wpb + rp) * (kRounds * 32) + lane;
             bond_span<R / 8, LAW, KAPPA>(part * R, s_tab[t], s_offb[t], (const char *)(s_rec + 2 * il), hi, lo, dm,
-                                         a.cVf, a.s_ratio_f, a.k_f, a.alpha_f, a.inv_1mek_f, a.inv_1pa_f, acc);
+                                         a.cVf, a.s_ratio_f, a.k_f, a.alpha_f, a.inv_1mek_f, a.inv_1pa_f, a.gfA_f,
+                                         acc);
         }
         // add the two sub-lane partials in double-float (TwoSum is exact, so
         // both sub-lanes end with the same total)

@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
                         double d = dm[32 * m];
                         if (s > s0) {
                             const double dl =
-                                law_damage<double>(LAW, s, s0, a.s_ratio * s0, a.k, a.alpha, a.inv_1mek, a.inv_1pa);
+                                law_damage<double>(LAW, s, s0, crit_stretch(s0, a.s_ratio, a.gfA), a.k, a.alpha,
+                                                   a.inv_1mek, a.inv_1pa);
                             if (dl > d) {
                                 d = dl;
                                 dm[32 * m] = d;
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
                                 const float s0 = 0.5f * (hi.w + hj.w);
                                 float d = dm[32 * m];
                                 if (s > s0) {
-                                    const float dl = law_damage<float>(LAW, s, s0, sr * s0, kf, af, i1, i2);
+                                    const float dl = law_damage<float>(LAW, s, s0, crit_stretch(s0, sr, a.gfA_f), kf, af, i1, i2);
                                     if (dl > d) {
                                         d = dl;
                                         dm[32 * m] = d;
@@ -665,6 +666,8 @@ static StepArgs make_args(const pd_state *st) {
     a.alpha = st->mat.alpha;
     a.inv_1mek = 1.0 / (1.0 - std::exp(-st->mat.k));
     a.inv_1pa = 1.0 / (1.0 + st->mat.alpha);
+    a.gfA = st->gfA;
+    a.gfA_f = (float)st->gfA;
     a.cVf = (float)a.cV;
     a.s_ratio_f = (float)a.s_ratio;
     a.k_f = (float)a.k;
@@ -1042,12 +1045,39 @@ extern "C" int pd_state_create_sched(const pd_grid *g, const int32_t *row_ptr, c
     const double delta = g->m_ratio * g->dx;
     st->c = 12.0 * mat->E / (M_PI * delta * delta * delta * delta);
     st->V = g->dx * g->dx * g->dx;
+    st->gfA = 0.0;
+    if (mat->G_F > 0.0) {
+        const int grc = pd_gf_coefficient(mat->law, mat->E, delta, mat->G_F, mat->k, mat->alpha, &st->gfA);
+        if (grc != PD_OK) {
+            delete st;
+            return grc;
+        }
+    }
     int rc = build_state(st, row_ptr, col);
     if (rc != PD_OK) {
         free_state(st);
         return rc;
     }
     *out = st;
+    return PD_OK;
+}
+
+extern "C" int pd_gf_coefficient(int32_t law, double E, double delta, double G_F, double k, double alpha,
+                                 double *A) {
+    PD_REQUIRE(A != nullptr, "A is NULL");
+    PD_REQUIRE(law == PD_LAW_BILINEAR || law == PD_LAW_EXPLINEAR, "unknown law %d", law);
+    PD_REQUIRE(E > 0 && delta > 0 && G_F >= 0, "E, delta > 0 and G_F >= 0 required");
+    PD_REQUIRE(law == PD_LAW_BILINEAR || (k > 0 && k < 700 && alpha >= 0), "0 < k < 700 and alpha >= 0 required");
+    const double c = 12.0 * E / (M_PI * delta * delta * delta * delta);
+    const double pc5 = M_PI * c * delta * delta * delta * delta * delta;  // pi c delta^5
+    if (law == PD_LAW_BILINEAR) {
+        *A = 10.0 * G_F / pc5;  // G_F = pi c s0 delta^5 (s_c - s0) / 10
+        return PD_OK;
+    }
+    const double ek = std::exp(k);
+    const double P = 2.0 * k - 2.0 * ek + alpha * k - alpha * k * ek + 2.0;  // < 0
+    // G_F = pi c s0 delta^5 (s0 - s_c) P / (10 k (e^k - 1)(1 + alpha))
+    *A = 10.0 * k * (ek - 1.0) * (1.0 + alpha) * G_F / (pc5 * -P);
     return PD_OK;
 }
 

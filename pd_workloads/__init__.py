@@ -150,6 +150,22 @@ def beam(dx_mm: float = 2.5, n_steps: int = 5000, seed: int = 1,
     return Workload(f"notched_beam_175x50x50_dx{dx_mm}mm", g, mat, bc, n_steps, fld, seed)
 
 
+def beam_type1(dx_mm: float = 2.5, n_steps: int = 5000, seed: int = 5, G_F: float = 20.0) -> Workload:
+    """Unnotched (Type 1) three-point-bending beam 175x50x50 mm (Section 6.3's
+    specimen type), exp-linear law with the critical stretch calibrated per
+    bond from a fracture energy G_F [N/m] (Appendix A), same strength field."""
+    D, L, T = 50.0, 175.0, 50.0
+    g = _beam_grid(D, dx_mm, L, T, False)
+    span = 2.5 * D
+    sx = ((L - span) / 2.0, (L + span) / 2.0)
+    bc = BC(BC_BEAM_3PT, u_max=6e-5, n_ramp=n_steps,
+            support_x2=(round(2 * sx[0] / dx_mm), round(2 * sx[1] / dx_mm)),
+            load_x2=round(2 * (L / 2.0) / dx_mm))
+    mat = Material(E=30e9, law=LAW_EXPLINEAR, s0=1e-4, s_ratio=25.0, zeta=5e4, G_F=G_F)
+    fld = FieldCfg(COV_SQEXP, 10e-3, 64, MARG_LOGNORMAL, 1e-4, 0.1)
+    return Workload(f"unnotched_beam_175x50x50_dx{dx_mm}mm_GF{G_F:g}", g, mat, bc, n_steps, fld, seed)
+
+
 def beam_levels():
     """MLMC hierarchy: the notched beam at dx = 5 / 2.5 / 1.25 mm; N_l = 1024 / 128 / 16.
 
