@@ -61,7 +61,7 @@ class Problem(C.Structure):
                 ("s_ratio", C.c_double), ("k", C.c_double), ("alpha", C.c_double),
                 ("dt", C.c_double), ("zeta", C.c_double), ("s0", C.c_void_p),
                 ("kappa", C.c_void_p), ("bc", C.c_void_p), ("u_max", C.c_double),
-                ("n_ramp", C.c_int32), ("gf_A", C.c_double)]
+                ("n_ramp", C.c_int32), ("gf_A", C.c_double), ("vol", C.c_double)]
 
 
 def lib():
@@ -91,6 +91,13 @@ def lib():
                                    C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_max_threads.restype = C.c_int
+        L.or_micromodulus_2d.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32]
+        L.or_micromodulus_2d.restype = C.c_double
+        L.or_gf_coefficient_2d.argtypes = [C.c_int32] + [C.c_double] * 6
+        L.or_gf_coefficient_2d.restype = C.c_double
+        L.or_stable_dt_vol.argtypes = [C.POINTER(Grid), C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
+                                       C.c_double]
+        L.or_stable_dt_vol.restype = C.c_double
         L.or_gf_coefficient.argtypes = [C.c_int32] + [C.c_double] * 5
         L.or_gf_coefficient.restype = C.c_double
         L.or_fracture_energy.argtypes = [C.c_int32] + [C.c_double] * 6
@@ -156,9 +163,20 @@ def damage_law(law: int, s: float, s0: float, sc: float, k: float = 25.0,
     return lib().or_damage_law(law, s, s0, sc, k, alpha)
 
 
-def stable_dt(g, row, col, c, rho, safety):
+def stable_dt(g, row, col, c, rho, safety, vol=0.0):
     G = make_grid(g)
+    if vol > 0:
+        return lib().or_stable_dt_vol(C.byref(G), _p(row), _p(col), c, rho, safety, vol)
     return lib().or_stable_dt(C.byref(G), _p(row), _p(col), c, rho, safety)
+
+
+def micromodulus_2d(E: float, delta: float, t: float, plane_strain: bool) -> float:
+    return lib().or_micromodulus_2d(E, delta, t, 1 if plane_strain else 0)
+
+
+def gf_coefficient_2d(law: int, c: float, delta: float, t: float, G_F: float, k: float = 25.0,
+                      alpha: float = 0.25) -> float:
+    return lib().or_gf_coefficient_2d(law, c, delta, t, G_F, k, alpha)
 
 
 class Model:
@@ -172,9 +190,15 @@ class Model:
         self.row, self.col = np.ascontiguousarray(row), np.ascontiguousarray(col)
         self.n = g.nx * g.ny * g.nz
         self.nb = int(self.row[-1])
-        self.c = micromodulus(m.E, g.m_ratio * g.dx)
+        model = getattr(m, "model", 0)
+        if model == 0:
+            self.c = micromodulus(m.E, g.m_ratio * g.dx)
+            self.vol = 0.0
+        else:
+            self.c = micromodulus_2d(m.E, g.m_ratio * g.dx, m.thickness, model == 2)
+            self.vol = g.dx * g.dx * m.thickness
         self.codes = np.ascontiguousarray(bc_codes(g, bc))
-        self.dt = stable_dt(g, self.row, self.col, self.c, m.rho, m.dt_safety) if dt is None else dt
+        self.dt = stable_dt(g, self.row, self.col, self.c, m.rho, m.dt_safety, self.vol) if dt is None else dt
         self.s0 = np.ascontiguousarray(
             np.full(self.n, np.float32(m.s0), np.float64) if s0 is None else np.asarray(s0, np.float64))
         self.kappa = None if kappa is None else np.ascontiguousarray(np.asarray(kappa, np.float64))
@@ -182,10 +206,15 @@ class Model:
 
     def _mk(self):
         g, m, bc = self.w.grid, self.w.mat, self.w.bc
-        gfA = gf_coefficient(m.law, self.c, g.m_ratio * g.dx, m.G_F, m.k, m.alpha) if m.G_F > 0 else 0.0
+        if m.G_F <= 0:
+            gfA = 0.0
+        elif getattr(m, "model", 0) == 0:
+            gfA = gf_coefficient(m.law, self.c, g.m_ratio * g.dx, m.G_F, m.k, m.alpha)
+        else:
+            gfA = gf_coefficient_2d(m.law, self.c, g.m_ratio * g.dx, m.thickness, m.G_F, m.k, m.alpha)
         self.P = Problem(g.nx, g.ny, g.nz, g.dx, _p(self.row), _p(self.col), self.c, m.rho,
                          m.law, m.s_ratio, m.k, m.alpha, self.dt, m.zeta, _p(self.s0),
-                         _p(self.kappa), _p(self.codes), bc.u_max, bc.n_ramp, gfA)
+                         _p(self.kappa), _p(self.codes), bc.u_max, bc.n_ramp, gfA, self.vol)
 
     def set_field(self, s0, kappa=None):
         self.s0 = np.ascontiguousarray(np.asarray(s0, np.float64))

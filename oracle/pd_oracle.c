@@ -83,6 +83,7 @@ typedef struct {
     int32_t n_ramp;
     double gf_A;          /* > 0: s_crit = s0 + gf_A / s0 (from the fracture energy,
                              or_gf_coefficient); 0: s_crit = s_ratio * s0 */
+    double vol;           /* node volume; 0: dx^3 (3D). Plane models: dx^2 t */
 } or_problem;
 
 /* ---------------------------------------------------------------- grid */
@@ -258,6 +259,26 @@ double or_damage_law(int32_t law, double s, double s0, double sc,
     return 1.0 - (s0 / s) * bracket / (1.0 + alpha);
 }
 
+/* Plane models (Eq. bond_stiffness_constant): c = 9E / (pi t delta^3) for
+ * plane stress, 48E / (5 pi t delta^3) for plane strain; t the thickness. The
+ * grid has one node layer (nz = 1) and every node volume is dx^2 t. */
+double or_micromodulus_2d(double E, double delta, double t, int32_t plane_strain) {
+    double d3 = delta * delta * delta;
+    return plane_strain ? 48.0 * E / (5.0 * M_PI * t * d3) : 9.0 * E / (M_PI * t * d3);
+}
+
+/* Two-dimensional calibration, Eq. exp_sc_2D as printed (it is consistent
+ * with Eq. exp_fracture_energy_2D): its G_F term over s0 is A of
+ * s_c = s0 + A / s0; for the bilinear law the same construction
+ * (G_F = h c s0 delta^4 (s_c - s0) / 4) gives A = 4 G_F / (h c delta^4). */
+double or_gf_coefficient_2d(int32_t law, double c, double delta, double h, double G_F, double k, double alpha) {
+    double d4 = delta * delta * delta * delta;
+    if (law == 0) return 4.0 * G_F / (h * c * d4);
+    double ek = exp(k);
+    double P = 2.0 * k - 2.0 * ek + alpha * k - alpha * k * ek + 2.0;
+    return 4.0 * k * (1.0 - ek) * (1.0 + alpha) * G_F / (h * c * d4 * P);
+}
+
 /* Fracture-energy calibration of the critical stretch. The energy a bond
  * absorbs while softening, w = xi * int_{s0}^{s_c} f ds (Eq. exp_bond_energy),
  * integrated over the bonds crossing a unit area of a plane (the quadruple
@@ -291,10 +312,9 @@ double or_fracture_energy(int32_t law, double c, double delta, double s0, double
 }
 
 /* Stable time step, Silling-Askari bound with uniform c, times safety. */
-double or_stable_dt(const or_grid *g, const int32_t *row_ptr, const int32_t *col,
-                    double c, double rho, double safety) {
+double or_stable_dt_vol(const or_grid *g, const int32_t *row_ptr, const int32_t *col,
+                        double c, double rho, double safety, double V) {
     int64_t n = (int64_t)g->nx * g->ny * g->nz;
-    double V = g->dx * g->dx * g->dx;
     double best = INFINITY;
     for (int64_t i = 0; i < n; ++i) {
         double xi_[3], xj[3];
@@ -315,6 +335,11 @@ double or_stable_dt(const or_grid *g, const int32_t *row_ptr, const int32_t *col
     return safety * best;
 }
 
+double or_stable_dt(const or_grid *g, const int32_t *row_ptr, const int32_t *col,
+                    double c, double rho, double safety) {
+    return or_stable_dt_vol(g, row_ptr, col, c, rho, safety, g->dx * g->dx * g->dx);
+}
+
 /* ------------------------------------------------------------- forces */
 
 /* Internal force density F_i = sum_j f_ij V_j (Eq. PD_EOM_Dynamic, b = 0),
@@ -325,7 +350,7 @@ static void forces(const or_problem *p, const double *u, double *d, double *F,
                    double *smax) {
     int64_t n = (int64_t)p->nx * p->ny * p->nz;
     or_grid g = {p->nx, p->ny, p->nz, p->dx, 0.0, 0, 0, 0};
-    double V = p->dx * p->dx * p->dx;
+    double V = p->vol > 0.0 ? p->vol : p->dx * p->dx * p->dx;
     double sm = -INFINITY;
     for (int64_t i = 0; i < n; ++i) {
         double xi_[3];
@@ -393,7 +418,7 @@ int or_run(const or_problem *p, int32_t step0, int32_t n_steps, int32_t use_stop
            double *u, double *v, double *d, double *reaction, double *smax,
            double *peak, int32_t *peak_step, int32_t *n_done) {
     int64_t n = (int64_t)p->nx * p->ny * p->nz;
-    double V = p->dx * p->dx * p->dx;
+    double V = p->vol > 0.0 ? p->vol : p->dx * p->dx * p->dx;
     double *F = (double *)malloc(sizeof(double) * 3 * (size_t)n);
     if (!F) return OR_ERR_ARG;
     double Q = *peak;
@@ -541,7 +566,7 @@ int or_adjoint(const or_problem *p, int32_t n_steps, int32_t n_obs, const int32_
                const double *w, double *grad_s0, double *grad_kappa) {
     int64_t n = (int64_t)p->nx * p->ny * p->nz;
     int64_t nb = p->row_ptr[n];
-    double V = p->dx * p->dx * p->dx;
+    double V = p->vol > 0.0 ? p->vol : p->dx * p->dx * p->dx;
     double a = 1.0 - 0.5 * p->zeta * p->dt;
     double b = 1.0 + 0.5 * p->zeta * p->dt;
     if (n_steps < 0 || (grad_kappa && !p->kappa)) return OR_ERR_ARG;

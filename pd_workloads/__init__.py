@@ -49,6 +49,9 @@ COV_EXP = 1     # exp(-r / l)  (the paper's Eq. for the exponential correlation)
 
 MARG_LOGNORMAL = 0
 MARG_WEIBULL = 1
+MODEL_3D = 0
+MODEL_PLANE_STRESS = 1
+MODEL_PLANE_STRAIN = 2
 
 
 @dataclass(frozen=True)
@@ -79,6 +82,8 @@ class Material:
     dt_safety: float = 0.5      # fraction of the stable time step
     zeta: float = 0.0           # mass-proportional damping rate [1/s]
     G_F: float = 0.0            # fracture energy [N/m]; > 0: s_crit from G_F per bond, s_ratio unused
+    model: int = 0              # MODEL_3D, MODEL_PLANE_STRESS or MODEL_PLANE_STRAIN (grid with nz = 1)
+    thickness: float = 0.0      # plane models: out-of-plane thickness t [m]
 
 
 @dataclass(frozen=True)
