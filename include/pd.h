@@ -92,7 +92,13 @@ typedef struct pd_material {
     int32_t precision;
     double G_F;         /* fracture energy [N/m]; > 0: per-bond critical stretch
                            s_c = s0 + A / s0 with A from pd_gf_coefficient (s_ratio unused) */
+    int32_t model;      /* PD_MODEL_3D, or a plane model on a one-layer grid (nz = 1) */
+    double thickness;   /* plane models: out-of-plane thickness t [m] */
 } pd_material;
+
+/* Plane models (Eq. bond_stiffness_constant): c = 9E / (pi t delta^3) (plane
+ * stress) or 48E / (5 pi t delta^3) (plane strain), node volume dx^2 t. */
+enum { PD_MODEL_3D = 0, PD_MODEL_PLANE_STRESS = 1, PD_MODEL_PLANE_STRAIN = 2 };
 
 /* A of the fracture-energy calibration s_c = s0 + A / s0 (Appendix A): Eq.
  * exp_fracture_energy solved for s_c for the exp-linear law (k, alpha), and
@@ -102,6 +108,13 @@ typedef struct pd_material {
  * exp_fracture_energy gives s0; the consistent form is used. Host only. */
 PD_API int pd_gf_coefficient(int32_t law, double E, double delta, double G_F, double k, double alpha,
                              double *A);
+
+/* The same for a plane model of thickness t: Eq. exp_sc_2D,
+ * A = 4k (e^k - 1)(1 + alpha) G_F / (t c delta^4 (-P)), P = 2k - 2e^k + alpha k
+ * - alpha k e^k + 2 (exp-linear), A = 4 G_F / (t c delta^4) (bilinear), with c
+ * the plane model's micromodulus. */
+PD_API int pd_gf_coefficient_plane(int32_t law, int32_t model, double E, double delta, double t, double G_F,
+                                   double k, double alpha, double *A);
 
 /* Displacement control: prescribed magnitude U(n) = u_max min(n, n_ramp) / n_ramp.
  * PD_BC_BAR_TENSION: the first grip_planes x-planes are fixed; the last

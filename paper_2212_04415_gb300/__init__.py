@@ -33,7 +33,8 @@ class Grid(C.Structure):
 class Material(C.Structure):
     _fields_ = [("E", C.c_double), ("rho", C.c_double), ("law", C.c_int32), ("s_ratio", C.c_double),
                 ("k", C.c_double), ("alpha", C.c_double), ("dt", C.c_double), ("dt_safety", C.c_double),
-                ("zeta", C.c_double), ("precision", C.c_int32), ("G_F", C.c_double)]
+                ("zeta", C.c_double), ("precision", C.c_int32), ("G_F", C.c_double),
+                ("model", C.c_int32), ("thickness", C.c_double)]
 
 
 class BC(C.Structure):
@@ -104,6 +105,7 @@ _SIGS = {
     "mlmc_estimate": (C.c_int, [C.POINTER(MlmcCfg), C.POINTER(MlmcResult), _VP, _VP, _VP, _VP]),
     "pd_gf_coefficient": (C.c_int, [C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                     C.POINTER(C.c_double)]),
+    "pd_gf_coefficient_plane": (C.c_int, [C.c_int32, C.c_int32] + [C.c_double] * 6 + [C.POINTER(C.c_double)]),
     "pd_ml_inverse_cdf": (C.c_int, [C.c_int32, _VP, _VP, _VP, C.c_int32, _VP, _VP, _VP]),
     "pd_ml_cdf": (C.c_int, [C.c_int32, _VP, _VP, _VP, C.c_int32, C.c_int32, _VP, _VP, _VP]),
     "mlmc_adaptive": (C.c_int, [C.POINTER(MlmcCfg), C.POINTER(AdaptiveCfg), C.POINTER(MlmcResult),
@@ -163,7 +165,7 @@ def grid_struct(g) -> Grid:
 
 def material_struct(m, precision: int, dt: float = 0.0) -> Material:
     return Material(m.E, m.rho, m.law, m.s_ratio, m.k, m.alpha, dt, m.dt_safety, m.zeta, precision,
-                    getattr(m, "G_F", 0.0))
+                    getattr(m, "G_F", 0.0), getattr(m, "model", 0), getattr(m, "thickness", 0.0))
 
 
 def bc_struct(b) -> BC:
@@ -280,6 +282,13 @@ def gf_coefficient(law, E, delta, G_F, k=25.0, alpha=0.25):
     """A of s_crit = s0 + A / s0 for a fracture energy G_F (pd_gf_coefficient)."""
     A = C.c_double()
     _check(lib().pd_gf_coefficient(law, E, delta, G_F, k, alpha, C.byref(A)))
+    return A.value
+
+
+def gf_coefficient_plane(law, model, E, delta, t, G_F, k=25.0, alpha=0.25):
+    """A of s_crit = s0 + A / s0 for a plane model of thickness t (pd_gf_coefficient_plane)."""
+    A = C.c_double()
+    _check(lib().pd_gf_coefficient_plane(law, model, E, delta, t, G_F, k, alpha, C.byref(A)))
     return A.value
 
 

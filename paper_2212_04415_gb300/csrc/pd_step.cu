@@ -1003,9 +1003,12 @@ extern "C" int pd_state_create_sched(const pd_grid *g, const int32_t *row_ptr, c
             const long long nodes = (long long)g->nx * g->ny * g->nz * batch;
             st->by = 4;
             st->bz = nodes >= 400000 ? 4 : 2;
-            if (g->ny < 4 || g->nz < 2) {
+            if (g->nz == 1) {  // one layer (plane models): bricks of 8 x by x 1
+                st->by = g->ny >= 8 ? 8 : (g->ny >= 4 ? 4 : 2);
+                st->bz = 1;
+            } else if (g->ny < 4 || g->nz < 2) {
                 st->by = 2;
-                st->bz = g->nz >= 2 ? 2 : 1;
+                st->bz = 2;
             }
         } else {
             // the largest brick that still gives at least two blocks per SM
@@ -1043,11 +1046,29 @@ extern "C" int pd_state_create_sched(const pd_grid *g, const int32_t *row_ptr, c
         }
     }
     const double delta = g->m_ratio * g->dx;
-    st->c = 12.0 * mat->E / (M_PI * delta * delta * delta * delta);
-    st->V = g->dx * g->dx * g->dx;
+    if (mat->model != PD_MODEL_3D) {
+        if ((mat->model != PD_MODEL_PLANE_STRESS && mat->model != PD_MODEL_PLANE_STRAIN) || g->nz != 1 ||
+            !(mat->thickness > 0)) {
+            delete st;
+            set_error("plane models need model 1 or 2, a one-layer grid (nz = 1) and thickness > 0");
+            return PD_ERR_ARG;
+        }
+    }
+    const double d3 = delta * delta * delta;
+    if (mat->model == PD_MODEL_3D) {
+        st->c = 12.0 * mat->E / (M_PI * d3 * delta);
+        st->V = g->dx * g->dx * g->dx;
+    } else {
+        st->c = mat->model == PD_MODEL_PLANE_STRESS ? 9.0 * mat->E / (M_PI * mat->thickness * d3)
+                                                    : 48.0 * mat->E / (5.0 * M_PI * mat->thickness * d3);
+        st->V = g->dx * g->dx * mat->thickness;
+    }
     st->gfA = 0.0;
     if (mat->G_F > 0.0) {
-        const int grc = pd_gf_coefficient(mat->law, mat->E, delta, mat->G_F, mat->k, mat->alpha, &st->gfA);
+        const int grc = mat->model == PD_MODEL_3D
+                            ? pd_gf_coefficient(mat->law, mat->E, delta, mat->G_F, mat->k, mat->alpha, &st->gfA)
+                            : pd_gf_coefficient_plane(mat->law, mat->model, mat->E, delta, mat->thickness,
+                                                      mat->G_F, mat->k, mat->alpha, &st->gfA);
         if (grc != PD_OK) {
             delete st;
             return grc;
@@ -1078,6 +1099,26 @@ extern "C" int pd_gf_coefficient(int32_t law, double E, double delta, double G_F
     const double P = 2.0 * k - 2.0 * ek + alpha * k - alpha * k * ek + 2.0;  // < 0
     // G_F = pi c s0 delta^5 (s0 - s_c) P / (10 k (e^k - 1)(1 + alpha))
     *A = 10.0 * k * (ek - 1.0) * (1.0 + alpha) * G_F / (pc5 * -P);
+    return PD_OK;
+}
+
+extern "C" int pd_gf_coefficient_plane(int32_t law, int32_t model, double E, double delta, double t, double G_F,
+                                       double k, double alpha, double *A) {
+    PD_REQUIRE(A != nullptr, "A is NULL");
+    PD_REQUIRE(law == PD_LAW_BILINEAR || law == PD_LAW_EXPLINEAR, "unknown law %d", law);
+    PD_REQUIRE(model == PD_MODEL_PLANE_STRESS || model == PD_MODEL_PLANE_STRAIN, "model must be a plane model");
+    PD_REQUIRE(E > 0 && delta > 0 && t > 0 && G_F >= 0, "E, delta, t > 0 and G_F >= 0 required");
+    PD_REQUIRE(law == PD_LAW_BILINEAR || (k > 0 && k < 700 && alpha >= 0), "0 < k < 700 and alpha >= 0 required");
+    const double d3 = delta * delta * delta;
+    const double c = model == PD_MODEL_PLANE_STRESS ? 9.0 * E / (M_PI * t * d3) : 48.0 * E / (5.0 * M_PI * t * d3);
+    const double tcd4 = t * c * d3 * delta;  // t c delta^4
+    if (law == PD_LAW_BILINEAR) {
+        *A = 4.0 * G_F / tcd4;  // G_F = t c s0 delta^4 (s_c - s0) / 4
+        return PD_OK;
+    }
+    const double ek = std::exp(k);
+    const double P = 2.0 * k - 2.0 * ek + alpha * k - alpha * k * ek + 2.0;
+    *A = 4.0 * k * (ek - 1.0) * (1.0 + alpha) * G_F / (tcd4 * -P);
     return PD_OK;
 }
 
