@@ -281,6 +281,18 @@ PD_API int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int32_t
                       const float *kappa, double *grad_s0, double *grad_kappa, double *R_obs,
                       pd_stream stream);
 
+/* pd_run_to_peak for several states at once (meshes of different sizes, such as
+ * the fine and coarse members of an MLMC level): each 64-step chunk is one
+ * captured graph whose branches are the states' step launches, so the small
+ * meshes' launches overlap the large ones'; one host poll per chunk covers
+ * every state. Per state i: max_steps[i] and device outputs peak[i],
+ * peak_step[i], n_done[i] (the pointer arrays are host arrays; each may be
+ * NULL). Results equal n_states calls of pd_run_to_peak bit for bit.
+ * Host-synchronous; 1 <= n_states <= 16, no state twice. */
+PD_API int pd_run_to_peak_multi(pd_state *const *states, int32_t n_states, const int32_t *max_steps,
+                                double *const *peak, int32_t *const *peak_step, int32_t *const *n_done,
+                                pd_stream stream);
+
 /* ---------------------------------------------------------- random field */
 
 /* KL coefficients xi (device double[B][K]) of samples sample_ids (device

@@ -97,6 +97,7 @@ _SIGS = {
     "pd_force": (C.c_int, [_VP, _VP, _VP]),
     "pd_step": (C.c_int, [_VP, C.c_int32, _VP, _VP]),
     "pd_run_to_peak": (C.c_int, [_VP, C.c_int32, _VP, _VP, _VP, _VP]),
+    "pd_run_to_peak_multi": (C.c_int, [_VP, C.c_int32, _VP, _VP, _VP, _VP, _VP]),
     "pd_draw_xi": (C.c_int, [C.c_uint64, C.c_int32, _VP, C.c_int32, C.c_int32, _VP, _VP]),
     "pd_field_create": (C.c_int, [C.POINTER(Grid), C.c_int32, C.POINTER(FieldCfg), C.POINTER(_VP)]),
     "pd_field_destroy": (C.c_int, [_VP]),
@@ -290,6 +291,23 @@ def gf_coefficient_plane(law, model, E, delta, t, G_F, k=25.0, alpha=0.25):
     A = C.c_double()
     _check(lib().pd_gf_coefficient_plane(law, model, E, delta, t, G_F, k, alpha, C.byref(A)))
     return A.value
+
+
+def run_to_peak_multi(states, max_steps, stream=None):
+    """pd_run_to_peak_multi: run several states to their peaks together; returns
+    [(peak, peak_step, n_done)] per state."""
+    import torch
+    n = len(states)
+    outs = [(torch.empty(st.B, dtype=torch.float64, device="cuda"), torch.empty(st.B, dtype=torch.int32, device="cuda"),
+             torch.empty(st.B, dtype=torch.int32, device="cuda")) for st in states]
+    hs = (C.c_void_p * n)(*[st.h.value for st in states])
+    ms = (C.c_int32 * n)(*max_steps)
+    pk = (C.c_void_p * n)(*[o[0].data_ptr() for o in outs])
+    ps = (C.c_void_p * n)(*[o[1].data_ptr() for o in outs])
+    nd = (C.c_void_p * n)(*[o[2].data_ptr() for o in outs])
+    _check(lib().pd_run_to_peak_multi(C.cast(hs, C.c_void_p), n, C.cast(ms, C.c_void_p), C.cast(pk, C.c_void_p),
+                                      C.cast(ps, C.c_void_p), C.cast(nd, C.c_void_p), _stream(stream)))
+    return outs
 
 
 def autotune(g, row, col, mat, bc, batch=1, precision=PREC_MIXED, trial_steps=20, dt=0.0):

@@ -66,7 +66,7 @@ struct Buffers {
     uint64_t *ids = nullptr;
     double *xi = nullptr, *qf = nullptr, *qc = nullptr, *y = nullptr, *sums = nullptr;
     float *ff = nullptr, *fc = nullptr;
-    int32_t *ps = nullptr, *nd = nullptr, *ndc = nullptr;
+    int32_t *ps = nullptr, *psc = nullptr, *nd = nullptr, *ndc = nullptr;
     ~Buffers() {
         cudaFree(ids);
         cudaFree(xi);
@@ -77,6 +77,7 @@ struct Buffers {
         cudaFree(ff);
         cudaFree(fc);
         cudaFree(ps);
+        cudaFree(psc);
         cudaFree(nd);
         cudaFree(ndc);
     }
@@ -108,6 +109,7 @@ static int run_level(const pd_mlmc_cfg *cfg, pd_field *field, int l, pd_mlmc_lev
     PD_TRY(dalloc(&bf.ff, (size_t)Bmax * Nf));
     if (l > 0) PD_TRY(dalloc(&bf.fc, (size_t)Bmax * Nc));
     PD_TRY(dalloc(&bf.ps, Bmax));
+    PD_TRY(dalloc(&bf.psc, Bmax));
     PD_TRY(dalloc(&bf.nd, Bmax));
     PD_TRY(dalloc(&bf.ndc, Bmax));
     pd_state *sf = nullptr, *sc = nullptr;
@@ -145,10 +147,17 @@ static int run_level(const pd_mlmc_cfg *cfg, pd_field *field, int l, pd_mlmc_lev
         if ((rc = pd_draw_xi(cfg->seed, l, bf.ids, b, K, bf.xi, (pd_stream)s))) break;
         if ((rc = pd_sample_field(field, l, bf.xi, b, bf.ff, l > 0 ? bf.fc : nullptr, (pd_stream)s))) break;
         if ((rc = pd_state_reset(sf, bf.ff, nullptr, (pd_stream)s))) break;
-        if ((rc = pd_run_to_peak(sf, cfg->max_steps[l], bf.qf, bf.ps, bf.nd, (pd_stream)s))) break;
-        if (l > 0) {
+        if (l == 0) {
+            if ((rc = pd_run_to_peak(sf, cfg->max_steps[l], bf.qf, bf.ps, bf.nd, (pd_stream)s))) break;
+        } else {
+            // the pair's fine and coarse members run together (one chunk graph, two branches)
             if ((rc = pd_state_reset(sc, bf.fc, nullptr, (pd_stream)s))) break;
-            if ((rc = pd_run_to_peak(sc, cfg->max_steps[l - 1], bf.qc, bf.ps, bf.ndc, (pd_stream)s))) break;
+            pd_state *both[2] = {sf, sc};
+            const int32_t ms[2] = {cfg->max_steps[l], cfg->max_steps[l - 1]};
+            double *pk[2] = {bf.qf, bf.qc};
+            int32_t *ps2[2] = {bf.ps, bf.psc};
+            int32_t *nd[2] = {bf.nd, bf.ndc};
+            if ((rc = pd_run_to_peak_multi(both, 2, ms, pk, ps2, nd, (pd_stream)s))) break;
         }
         k_level_sums<<<1, 256, 0, s>>>(b, bf.qf, l > 0 ? bf.qc : nullptr, bf.y, bf.sums);
         double sums[2];

@@ -1331,3 +1331,138 @@ extern "C" int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int
         }
     return PD_OK;
 }
+
+// Several states (meshes of different sizes, e.g. the fine and coarse members
+// of an MLMC level) run to their peaks together: one captured graph per 64-step
+// chunk holds every state's step launches as independent branches, so the
+// GPU overlaps the small meshes' launches with the large ones', and one host
+// poll per chunk covers all states.
+extern "C" int pd_run_to_peak_multi(pd_state *const *states, int32_t n_states, const int32_t *max_steps,
+                                    double *const *peak, int32_t *const *peak_step, int32_t *const *n_done,
+                                    pd_stream stream) {
+    PD_REQUIRE(states && max_steps && n_states >= 1 && n_states <= 16, "1 to 16 states and max_steps required");
+    for (int i = 0; i < n_states; ++i) {
+        PD_REQUIRE(states[i] != nullptr, "state %d is NULL", i);
+        PD_REQUIRE(max_steps[i] >= 0, "max_steps[%d] must be >= 0", i);
+        for (int j = 0; j < i; ++j) PD_REQUIRE(states[j] != states[i], "state %d appears twice", i);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int chunk = 64;
+    int rc = PD_OK;
+    cudaStream_t cs = nullptr, br[16] = {};
+    cudaEvent_t fork = nullptr, join[16] = {};
+    cudaGraphExec_t exec = nullptr;
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (int i = 0; i < n_states; ++i) {
+            if (br[i]) cudaStreamDestroy(br[i]);
+            if (join[i]) cudaEventDestroy(join[i]);
+        }
+        if (fork) cudaEventDestroy(fork);
+        if (cs) cudaStreamDestroy(cs);
+    };
+    bool ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 1; i < n_states && ok; ++i)
+        ok = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cleanup();
+        set_error("stream or event creation failed");
+        return PD_ERR_CUDA;
+    }
+    // the chunk graph: state 0 on the capture stream, the others on forked branches
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        int lrc = PD_OK;
+        if (n_states > 1) cudaEventRecord(fork, cs);
+        for (int i = 0; i < n_states && lrc == PD_OK; ++i) {
+            pd_state *st = states[i];
+            cudaStream_t ls = i == 0 ? cs : br[i];
+            if (i > 0) cudaStreamWaitEvent(ls, fork, 0);
+            StepArgs a = make_args(st);
+            a.use_stop = 1;
+            a.max_steps = max_steps[i];
+            for (int q = 0; q < chunk && lrc == PD_OK; ++q) {
+                a.par = st->bk_par ^ (q & 1);  // even chunk: ends on the parity it starts from
+                lrc = launch_step(st, a, false, ls);
+            }
+            if (i > 0) {
+                cudaEventRecord(join[i], ls);
+                cudaStreamWaitEvent(cs, join[i], 0);
+            }
+        }
+        e = cudaStreamEndCapture(cs, &graph);
+        if (lrc != PD_OK) rc = lrc;
+    }
+    if (rc == PD_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc == PD_OK && e != cudaSuccess) {
+        set_error("chunk graph of %d states: %s", n_states, cudaGetErrorString(e));
+        rc = PD_ERR_CUDA;
+    }
+    if (rc != PD_OK) {
+        cleanup();
+        return rc;
+    }
+    for (int i = 0; i < n_states; ++i) {
+        pd_state *st = states[i];
+        k_run_init<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->step + st->bk_par * st->B,
+                                                     st->done + st->bk_par * st->B, max_steps[i]);
+    }
+    int max_all = 0;
+    for (int i = 0; i < n_states; ++i) max_all = std::max(max_all, (int)max_steps[i]);
+    const int n_chunks = max_all / chunk + 1;
+    for (int c = 0; c < n_chunks && rc == PD_OK; ++c) {
+        if (cudaGraphLaunch(exec, s) != cudaSuccess) {
+            rc = PD_ERR_CUDA;
+            break;
+        }
+        for (int i = 0; i < n_states; ++i) {
+            pd_state *st = states[i];
+            k_count_active<<<1, 256, 0, s>>>(st->B, st->done + st->bk_par * st->B, st->host_flag_dev + (c & 1));
+        }
+        if (cudaEventRecord(states[0]->ev[c & 1], s) != cudaSuccess) {
+            rc = PD_ERR_CUDA;
+            break;
+        }
+        if (c >= 1) {
+            if (cudaEventSynchronize(states[0]->ev[(c - 1) & 1]) != cudaSuccess) {
+                rc = PD_ERR_CUDA;
+                break;
+            }
+            int live = 0;
+            for (int i = 0; i < n_states; ++i) live += ((volatile int32_t *)states[i]->host_flag)[(c - 1) & 1];
+            if (live == 0) break;
+        }
+    }
+    if (rc != PD_OK) {
+        set_error("multi-state run failed: %s", cudaGetErrorString(cudaGetLastError()));
+        cudaStreamSynchronize(s);
+        cleanup();
+        return rc;
+    }
+    for (int i = 0; i < n_states; ++i) {
+        pd_state *st = states[i];
+        k_copy_out<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->peak, st->peak_step, st->step + st->bk_par * st->B,
+                                                      peak ? peak[i] : nullptr, peak_step ? peak_step[i] : nullptr,
+                                                      n_done ? n_done[i] : nullptr);
+    }
+    std::vector<std::vector<int32_t>> status(n_states);
+    for (int i = 0; i < n_states; ++i) {
+        status[i].resize(states[i]->B);
+        cudaMemcpyAsync(status[i].data(), states[i]->status, states[i]->B * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                        s);
+    }
+    const cudaError_t se = cudaStreamSynchronize(s);
+    cleanup();
+    PD_CHECK_CUDA(se);
+    for (int i = 0; i < n_states; ++i)
+        for (int b = 0; b < states[i]->B; ++b)
+            if (status[i][b] & 1) {
+                set_error("non-finite reaction in sample %d of state %d", b, i);
+                return PD_ERR_NAN;
+            }
+    return PD_OK;
+}

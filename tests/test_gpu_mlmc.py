@@ -167,3 +167,34 @@ def test_adaptive_mlmc_against_oracle(pd):
     fixed = pd.mlmc_estimate(n_samples=[lv["n"] for lv in res["levels"]], batch=16, **a)
     for l in range(2):
         assert fixed["levels"][l]["sum_y"] == pytest.approx(res["levels"][l]["sum_y"], rel=1e-12)
+
+
+def test_multi_state_run_equals_separate_runs(pd):
+    """The fine and coarse members run together in one chunk graph give the
+    same peaks, steps and final states as two separate runs, bit for bit."""
+    import torch
+    levels = W.small_beam_levels()
+    fw, cw = levels[1], levels[0]
+    rf, cf = pd.build_neighbours(fw.grid)
+    rc, cc = pd.build_neighbours(cw.grid)
+    fld = pd.Field(fw.grid, 2, fw.field)
+    xi = pd.draw_xi(fw.seed, 1, torch.arange(3, dtype=torch.int64, device="cuda"), fw.field.n_modes)
+    ff, fc = fld.sample(1, xi, coarse=True)
+    sf = pd.State(fw.grid, rf, cf, fw.mat, fw.bc, batch=3)
+    sc = pd.State(cw.grid, rc, cc, cw.mat, cw.bc, batch=3)
+    sf.reset(ff)
+    sc.reset(fc)
+    sep = [sf.run_to_peak(fw.n_steps), sc.run_to_peak(cw.n_steps)]
+    u_sep = [sf.store()[0], sc.store()[0]]
+    sf.reset(ff)
+    sc.reset(fc)
+    multi = pd.run_to_peak_multi([sf, sc], [fw.n_steps, cw.n_steps])
+    u_multi = [sf.store()[0], sc.store()[0]]
+    for a, b in zip(sep, multi):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+    for a, b in zip(u_sep, u_multi):
+        assert torch.equal(a, b)
+    sf.close()
+    sc.close()
+    fld.close()
