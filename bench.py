@@ -221,6 +221,47 @@ def mlmc_leg(pd, W, dist, tune_steps: int = 10, tol: float = 1e-3):
     }
 
 
+def sweep_leg(pd, W, hbm, steps: int = 10, warmup: int = 3):
+    """Size-effect sweep, batched (64 samples per launch): geometrically similar
+    notched beams D = 50 ... 400 mm at dx = 2.5 mm (up to 1.79M nodes, 204M
+    bonds per sample). The working set (up to ~70 GB) is far above L2, so
+    these launches show the step in the HBM regime. A bounded number of steps
+    from rest is timed per size (the first steps are elastic: few history
+    writes)."""
+    import torch
+    out = []
+    for D in (50.0, 100.0, 200.0, 400.0):
+        w = W.sweep(D)
+        g = w.grid
+        row, col = pd.build_neighbours(g)
+        nb = int(col.numel())
+        B = w.batch
+        fld = pd.Field(g, 1, w.field)
+        xi = pd.draw_xi(w.seed, 0, torch.arange(B, dtype=torch.int64, device="cuda"), w.field.n_modes)
+        s0 = fld.sample(0, xi)
+        st = pd.State(g, row, col, w.mat, w.bc, batch=B)
+        st.reset(s0)
+        st.step(warmup, reaction=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        st.step(steps, reaction=False)
+        e1.record()
+        torch.cuda.synchronize()
+        per = e0.elapsed_time(e1) * 1e-3 / steps
+        alg = B * (nb * (4.0 + 4.0 / B) + g.n_nodes * 108.0)
+        out.append({"D_mm": D, "nodes": g.n_nodes, "bonds": nb, "samples_per_launch": B, "ms_per_step": 1e3 * per,
+                    "bond_updates_per_s": B * nb / per, "algorithmic_gbs": alg / per / 1e9,
+                    "hbm_frac": alg / per / 1e9 / hbm})
+        st.close()
+        fld.close()
+        del row, col, xi, s0, st, fld
+        torch.cuda.empty_cache()
+    return {"workload": "size-effect sweep, notched beams D = 50/100/200/400 mm (span 3D, length 3.5D, "
+                        "thickness 50 mm), dx 2.5 mm, 64 samples per launch",
+            "timed": f"{steps} explicit steps after {warmup} from rest, per size", "sizes": out}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -261,6 +302,7 @@ def main():
     ap.add_argument("--batched", type=int, default=32, help="samples per launch for the batched comparison (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mlmc", action="store_true", help="skip the MLMC hierarchy leg")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the size-effect sweep leg")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -423,6 +465,8 @@ def main():
     }
     if not args.no_mlmc:
         line["mlmc"] = mlmc_leg(pd, W, dist)
+    if not args.no_sweep and ws == 1:
+        line["sweep"] = sweep_leg(pd, W, hbm)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg()
     if rank == 0:
