@@ -26,7 +26,8 @@
 // copies compute the same value), and the node sums are fixed xor trees, so
 // the gradient is deterministic. Arithmetic is FP64 throughout (the adjoint
 // is an offline gradient study; its states come from the state's own
-// forward path, FP64 or mixed).
+// forward path, FP64 or mixed). For mixed-path states the per-bond terms run
+// in FP32 (k_adj_bonds_f32) with FP64 sums.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -180,6 +181,109 @@ __global__ void __launch_bounds__(256) k_adj_bonds(const AdjArgs a, const double
     }
 }
 
+// FP32 variant for states of the mixed path (their trajectory is FP32-class
+// already): the same terms per bond in FP32 on FP32 copies of u^n and lamF^n;
+// per-lane partial sums in FP32 (a lane takes ~4 of a node's bonds), warp sums
+// and the carried damage adjoint in FP64. GB300 runs FP64 at a small fraction
+// of the FP32 rate, so this keeps the FP64 pipe to a few operations per bond.
+__device__ __forceinline__ void law_derivs_f(const AdjArgs &a, float s, float s0, float &dDds, float &dDds0) {
+    const float sc = a.gfA > 0.0 ? s0 + (float)a.gfA / s0 : (float)a.s_ratio * s0;
+    const float dsc = a.gfA > 0.0 ? 1.0f - (float)a.gfA / (s0 * s0) : (float)a.s_ratio;
+    dDds = 0.0f;
+    dDds0 = 0.0f;
+    if (s <= s0 || s >= sc) return;
+    const float w = sc - s0;
+    if (a.law == PD_LAW_BILINEAR) {
+        dDds = s0 * sc / (s * s * w);
+        dDds0 = -(sc / s - 1.0f) * sc / (w * w) + dsc * (-s0 * (1.0f - s0 / s) / (w * w));
+        return;
+    }
+    const float k = (float)a.k, al = (float)a.alpha;
+    const float t = (s - s0) / w;
+    const float e = expf(-k * t), ek = 1.0f - expf(-k);
+    const float beta = 1.0f - (1.0f - e) / ek + al * (1.0f - t);
+    const float dbeta = -k * e / ek - al;
+    const float dtds = 1.0f / w, dtds0 = (s - sc) / (w * w), dtdsc = -(s - s0) / (w * w);
+    dDds = (s0 * beta / (s * s) - (s0 / s) * dbeta * dtds) / (1.0f + al);
+    dDds0 = (-(beta / s + (s0 / s) * dbeta * dtds0) - dsc * (s0 / s) * dbeta * dtdsc) / (1.0f + al);
+}
+
+__global__ void k_to_float(long long n, const double *x, float *y) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) y[t] = (float)x[t];
+}
+
+__global__ void __launch_bounds__(256) k_adj_bonds_f32(const AdjArgs a, float cf, const float *u,
+                                                       const double *dprev, const double *dcur, const float *lF,
+                                                       double *ld, double *lun, double *g_s0, double *g_k) {
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= (long long)a.B * a.N) return;  // warp-uniform
+    const int b = (int)(gw / a.N);
+    const long long i = gw % a.N;
+    const int ix = (int)(i % a.nx), iy = (int)((i / a.nx) % a.ny), iz = (int)(i / ((long long)a.nx * a.ny));
+    const float *ub = u + (size_t)b * a.N * 3;
+    const float *lFb = lF + (size_t)b * a.N * 3;
+    const float *s0b = a.s0 + (size_t)b * a.N;
+    const float *kb = a.kappa ? a.kappa + (size_t)b * a.N : nullptr;
+    const size_t db = (size_t)b * a.nb;
+    const float dxf = (float)a.dx;
+    const float ui[3] = {ub[3 * i], ub[3 * i + 1], ub[3 * i + 2]};
+    const float li[3] = {lFb[3 * i], lFb[3 * i + 1], lFb[3 * i + 2]};
+    const float s0i = s0b[i], ki = kb ? kb[i] : 1.0f;
+    float acc[3] = {0.f, 0.f, 0.f}, gs = 0.f, gk = 0.f;
+    for (int q = a.row_ptr[i] + lane; q < a.row_ptr[i + 1]; q += 32) {
+        const long long j = a.col[q];
+        const int jx = (int)(j % a.nx), jy = (int)((j / a.nx) % a.ny), jz = (int)(j / ((long long)a.nx * a.ny));
+        const float xi[3] = {(float)(jx - ix) * dxf, (float)(jy - iy) * dxf, (float)(jz - iz) * dxf};
+        float y[3], dl[3], L0 = 0.f, L = 0.f, ydl = 0.f, xe = 0.f, ee = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float eta = ub[3 * j + c] - ui[c];
+            y[c] = xi[c] + eta;
+            dl[c] = lFb[3 * j + c] - li[c];
+            L0 += xi[c] * xi[c];
+            xe += xi[c] * eta;
+            ee += eta * eta;
+            ydl += y[c] * dl[c];
+        }
+        L0 = sqrtf(L0);
+        L = sqrtf(L0 * L0 + 2.f * xe + ee);
+        const float s = (2.f * xe + ee) / (L0 * (L + L0)), h = s / L;  // cancellation-free stretch
+        const float s0 = 0.5f * (s0i + s0b[j]);
+        const float cij = kb ? cf * 0.5f * (ki + kb[j]) : cf;
+        const double dp = dprev[db + q], dc = dcur[db + q];
+        const bool active = dc > dp;
+        const float dcf = (float)dc;
+        const double lamd = ld[db + q] + (double)(cij * (float)a.V * h * ydl);
+        float dDds = 0.f, dDds0 = 0.f;
+        if (active) law_derivs_f(a, s, s0, dDds, dDds0);
+        const float lamdf = (float)lamd;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float dh = y[c] / (L * L * L0) - s * y[c] / (L * L * L);
+            float lamy = -cij * (float)a.V * (1.0f - dcf) * (ydl * dh + h * dl[c]);
+            if (active) lamy += lamdf * dDds * y[c] / (L * L0);
+            acc[c] -= lamy;
+        }
+        if (active) gs += 0.5f * lamdf * dDds0;
+        gk += 0.5f * cf * (-(float)a.V * (1.0f - dcf) * h * ydl);
+        ld[db + q] = active ? 0.0 : lamd;
+    }
+    double accd[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) accd[c] = warp_sum_fixed((double)acc[c]);
+    const double gsd = warp_sum_fixed((double)gs), gkd = warp_sum_fixed((double)gk);
+    if (lane == 0) {
+        double *lb = lun + (size_t)b * a.N * 3 + 3 * i;
+        lb[0] += accd[0];
+        lb[1] += accd[1];
+        lb[2] += accd[2];
+        g_s0[(size_t)b * a.N + i] += gsd;
+        if (g_k) g_k[(size_t)b * a.N + i] += gkd;
+    }
+}
+
 // R_obs[b][o] = reaction[b][m] for the observations inside a segment.
 __global__ void k_gather_obs(int B, int len, int start, int n_obs, const int32_t *obs, const double *reaction,
                              double *R_obs) {
@@ -284,6 +388,8 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
     PD_CHECK_CUDA(cudaMemcpy(&n0, st->step + st->bk_par * B, sizeof(int32_t), cudaMemcpyDeviceToHost));
 
     DevBuf<double> ck_u, ck_v, ck_d, tr_u, tr_d, lu, lun, lv, lF, ld, rbuf;
+    DevBuf<float> u32, lF32;  // FP32 copies for the mixed path's bond adjoint
+    const bool f32 = st->mat.precision == PD_PREC_MIXED;
     DevBuf<int32_t> obs;
     PD_TRY(dalloc(&ck_u.p, (size_t)(nseg + 1) * U3));  // checkpoints + the final state
     PD_TRY(dalloc(&ck_v.p, (size_t)(nseg + 1) * U3));
@@ -296,6 +402,10 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
     PD_TRY(dalloc(&lF.p, U3));
     PD_TRY(dalloc(&ld.p, D1));
     PD_TRY(dalloc(&rbuf.p, (size_t)B * k));
+    if (f32) {
+        PD_TRY(dalloc(&u32.p, U3));
+        PD_TRY(dalloc(&lF32.p, U3));
+    }
     PD_TRY(dalloc(&obs.p, std::max(n_obs, 1)));
     if (n_obs) PD_CHECK_CUDA(cudaMemcpyAsync(obs.p, obs_steps, n_obs * sizeof(int32_t), cudaMemcpyHostToDevice, s));
 
@@ -359,9 +469,17 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
         for (int m = len - 1; m >= 0; --m) {
             k_adj_nodes<<<nblk_dof, 256, 0, s>>>(a, start + m, plu, lv.p, lF.p, plun);
             PD_CHECK_LAUNCH();
-            k_adj_bonds<<<nblk_bond, 256, 0, s>>>(a, tr_u.p + (size_t)m * U3, tr_d.p + (size_t)m * D1,
-                                                  tr_d.p + (size_t)(m + 1) * D1, lF.p, ld.p, plun, grad_s0,
-                                                  grad_kappa);
+            if (f32) {
+                k_to_float<<<nblk_dof, 256, 0, s>>>(U3, tr_u.p + (size_t)m * U3, u32.p);
+                k_to_float<<<nblk_dof, 256, 0, s>>>(U3, lF.p, lF32.p);
+                k_adj_bonds_f32<<<nblk_bond, 256, 0, s>>>(a, (float)a.c, u32.p,
+                                                          tr_d.p + (size_t)m * D1, tr_d.p + (size_t)(m + 1) * D1,
+                                                          lF32.p, ld.p, plun, grad_s0, grad_kappa);
+            } else {
+                k_adj_bonds<<<nblk_bond, 256, 0, s>>>(a, tr_u.p + (size_t)m * U3, tr_d.p + (size_t)m * D1,
+                                                      tr_d.p + (size_t)(m + 1) * D1, lF.p, ld.p, plun, grad_s0,
+                                                      grad_kappa);
+            }
             PD_CHECK_LAUNCH();
             std::swap(plu, plun);
         }
