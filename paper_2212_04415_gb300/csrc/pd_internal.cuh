@@ -100,6 +100,7 @@ struct pd_state {
     int32_t st_wpb;         // row pairs per brick (2 brick rows per warp)
     int32_t st_q;           // warps sharing a row pair (parts of the half-stencil)
     int32_t q_req;          // requested st_q (schedule), 0 = built-in choice
+    int32_t st_dim;         // 3, or 2 for a one-layer grid (planar 28-offset stencil)
     int64_t st_len;         // damage slots per sample
     float *st_tmpl;         // [st_len]: 0 for real bonds, 1 for absent (broken) slots
     int16_t *st_box;        // [7^3]: stencil code 2 m + t of an offset, -1 outside

@@ -12,12 +12,16 @@
 // copies of a bond are computed by identical instruction sequences on exactly
 // negated operands (bitwise-symmetric stretch and damage).
 //
-// Layout per sample: [brick][warp][61 rounds][32 lanes] damage words; lane
-// L = 16 t + 8 r + c serves node (x0 + c, brick row 2 w + r) and sub-lane t.
-// A block (one brick of 8 x BY x BZ nodes, one sample) stages the brick's
-// gather records and a 3-cell halo in shared memory (cells outside the grid
-// read as zero displacement), so all gathers are shared-memory loads with
-// compile-time offsets.
+// Layout per sample: [brick][warp][64 rounds][32 lanes] damage words (the 61
+// offsets padded to 64); lane L = 16 t + 8 r + c serves node (x0 + c, brick
+// row 2 w + r) and sub-lane t. A block (one brick of 8 x BY x BZ nodes, one
+// sample) stages the brick's gather records and a 3-cell halo in shared memory
+// (cells outside the grid read as zero displacement), so all gathers are
+// shared-memory loads with compile-time offsets.
+//
+// A one-layer grid (nz = 1, the plane models) has only the 28 in-plane
+// offsets: the same kernel is compiled for that shape (14 offsets per sign,
+// padded to 16 rounds, no z-halo), so a plane node costs 16 rounds, not 64.
 #include <cmath>
 #include <cstdlib>
 #include <mutex>
@@ -30,10 +34,23 @@ namespace pdi {
 
 namespace {
 
-constexpr int kHalf = 61;            // positive half of the 122-offset stencil
-constexpr int kRounds = 64;          // half-stencil padded to 64 (entries 61..63 point at the node itself)
-constexpr int kHalo = 3;             // largest offset component
+constexpr int kHalo = 3;             // largest offset component (x and y)
 constexpr int kWx = kSlice + 2 * kHalo;
+
+// Stencil shape by dimension: the positive half of the horizon (61 of the 122
+// offsets in 3D; 14 of the 28 offsets of a one-layer grid, where no bond
+// leaves the layer), padded to a multiple of 16 rounds (the padding points at
+// the node itself), and the z-halo staged in shared memory.
+template <int DIM>
+struct Sten;
+template <>
+struct Sten<3> {
+    static constexpr int kHalf = 61, kRounds = 64, kHaloZ = 3;
+};
+template <>
+struct Sten<2> {
+    static constexpr int kHalf = 14, kRounds = 16, kHaloZ = 0;
+};
 
 struct I3 {
     int x, y, z;
@@ -43,10 +60,12 @@ __host__ __device__ constexpr bool positive_half(int x, int y, int z) {
     return z > 0 || (z == 0 && (y > 0 || (y == 0 && x > 0)));
 }
 
-// m-th offset of the positive half-stencil, in ascending linear order (z, y, x).
+// m-th offset of the positive half-stencil, in ascending linear order (z, y, x);
+// the planar stencil is the z = 0 part of the same order.
+template <int DIM>
 __host__ __device__ constexpr I3 half_off(int m) {
     int cnt = 0;
-    for (int z = 0; z <= 3; ++z)
+    for (int z = 0; z <= (DIM == 3 ? 3 : 0); ++z)
         for (int y = -3; y <= 3; ++y)
             for (int x = -3; x <= 3; ++x)
                 if (positive_half(x, y, z) && x * x + y * y + z * z <= 9) {
@@ -132,8 +151,10 @@ __device__ __forceinline__ void bond_span(int m0, const float4 *tab, const int *
 
 // Warps of a block: wpb row pairs x Q parts of the half-stencil. Part 0's warp
 // of a row pair adds the other parts' sums (fixed order) and integrates.
-template <int Q, int LAW, bool KAPPA, bool FORCE_ONLY>
+template <int DIM, int Q, int LAW, bool KAPPA, bool FORCE_ONLY>
 __global__ void __launch_bounds__(512, 2) k_step_stencil(const StepArgs a) {
+    using S = Sten<DIM>;
+    constexpr int kHalf = S::kHalf, kRounds = S::kRounds, kHaloZ = S::kHaloZ;
     extern __shared__ float4 s_rec[];
     __shared__ float2 red[16];
     __shared__ float s_pre[4];  // U(n+1) and the prescribed velocity, double-float
@@ -164,7 +185,7 @@ __global__ void __launch_bounds__(512, 2) k_step_stencil(const StepArgs a) {
     const int bx = brick % a.nbx, by = (brick / a.nbx) % a.nby, bz = brick / (a.nbx * a.nby);
     const int x0 = kSlice * bx, y0 = a.BY * by, z0 = a.BZ * bz;
     const size_t BN = (size_t)a.B * a.N;
-    const int Wy = a.BY + 2 * kHalo, Wz = a.BZ + 2 * kHalo;
+    const int Wy = a.BY + 2 * kHalo, Wz = a.BZ + 2 * kHaloZ;
     const int Wtot = kWx * Wy * Wz;
     float *s_part = (float *)(s_rec + 2 * Wtot);  // [Q-1][wpb][16][6]
     for (int m = threadIdx.x; m < kRounds; m += blockDim.x) {
@@ -187,7 +208,7 @@ __global__ void __launch_bounds__(512, 2) k_step_stencil(const StepArgs a) {
         // at once (cells outside the grid are zero-filled)
         for (int q = threadIdx.x; q < Wtot; q += blockDim.x) {
             const int lx = q % kWx, ly = (q / kWx) % Wy, lz = q / (kWx * Wy);
-            const int gx = x0 - kHalo + lx, gy = y0 - kHalo + ly, gz = z0 - kHalo + lz;
+            const int gx = x0 - kHalo + lx, gy = y0 - kHalo + ly, gz = z0 - kHaloZ + lz;
             const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz;
             const int gi = in ? gx + a.nx * (gy + a.ny * gz) : 0;
             cp_async16(s_rec + 2 * q, rhi + gi, in ? 16 : 0);  // records interleaved: hi, lo
@@ -207,7 +228,7 @@ __global__ void __launch_bounds__(512, 2) k_step_stencil(const StepArgs a) {
     const bool own = gx < a.nx && gy < a.ny && gz < a.nz;
     const int ii = gx + a.nx * (gy + a.ny * gz);
     const size_t node = (size_t)b * a.N + ii;
-    const int il = (kHalo + c) + kWx * ((kHalo + ly) + Wy * (kHalo + lz));
+    const int il = (kHalo + c) + kWx * ((kHalo + ly) + Wy * (kHaloZ + lz));
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // sx, sy, sz, cx, cy, cz
     const float4 hi = s_rec[2 * il], lo = s_rec[2 * il + 1];
     if (!done) {
@@ -290,13 +311,13 @@ __global__ void __launch_bounds__(512, 2) k_step_stencil(const StepArgs a) {
 
 // Slot of node i, stencil code (2 m + t), in the per-sample damage array.
 __device__ __forceinline__ long long slot_of(int i, int code, int nx, int ny, int BY, int BZ, int nbx, int nby,
-                                             int wpb) {
+                                             int wpb, int rounds) {
     const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
     const long long brick = (ix / kSlice) + (long long)nbx * ((iy / BY) + (long long)nby * (iz / BZ));
     const int row = (iy % BY) + BY * (iz % BZ);
     const int w = row >> 1, rr = row & 1, c = ix % kSlice;
     const int m = code >> 1, t = code & 1;
-    return ((brick * wpb + w) * kRounds + m) * 32 + (16 * t + 8 * rr + c);
+    return ((brick * wpb + w) * rounds + m) * 32 + (16 * t + 8 * rr + c);
 }
 
 // code of the CSR neighbour j of i: 2 m + t, or -1 if not a stencil offset
@@ -309,8 +330,8 @@ __device__ __forceinline__ int code_of(const int32_t *coord, int i, int j, const
 
 // Damage template: 0 for every slot of a CSR bond, 1 (absent bond) elsewhere.
 __global__ void k_stencil_template(const int32_t *row_ptr, const int32_t *col, const int32_t *coord, long long N,
-                                   int nx, int ny, int BY, int BZ, int nbx, int nby, int wpb, const int16_t *box,
-                                   float *tmpl, int32_t *bad) {
+                                   int nx, int ny, int BY, int BZ, int nbx, int nby, int wpb, int rounds,
+                                   const int16_t *box, float *tmpl, int32_t *bad) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
@@ -319,7 +340,7 @@ __global__ void k_stencil_template(const int32_t *row_ptr, const int32_t *col, c
             *bad = 1;
             continue;
         }
-        tmpl[slot_of((int)i, code, nx, ny, BY, BZ, nbx, nby, wpb)] = 0.0f;
+        tmpl[slot_of((int)i, code, nx, ny, BY, BZ, nbx, nby, wpb, rounds)] = 0.0f;
     }
 }
 
@@ -336,8 +357,8 @@ __global__ void k_stencil_reset(long long len, int B, const float *tmpl, float *
 
 template <bool TO_STATE>
 __global__ void k_stencil_map(const int32_t *row_ptr, const int32_t *col, const int32_t *coord, long long N, int B,
-                              long long nb, int nx, int ny, int BY, int BZ, int nbx, int nby, int wpb, long long len,
-                              const int16_t *box, float *dmg, double *csr) {
+                              long long nb, int nx, int ny, int BY, int BZ, int nbx, int nby, int wpb, int rounds,
+                              long long len, const int16_t *box, float *dmg, double *csr) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N * B) return;
     const int b = (int)(t / N);
@@ -345,7 +366,7 @@ __global__ void k_stencil_map(const int32_t *row_ptr, const int32_t *col, const 
     for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
         const int code = code_of(coord, i, col[p], box);
         if (code < 0) continue;
-        const long long e = (long long)b * len + slot_of(i, code, nx, ny, BY, BZ, nbx, nby, wpb);
+        const long long e = (long long)b * len + slot_of(i, code, nx, ny, BY, BZ, nbx, nby, wpb, rounds);
         const long long q = (long long)b * nb + p;
         if (TO_STATE)
             dmg[e] = (float)csr[q];
@@ -356,20 +377,22 @@ __global__ void k_stencil_map(const int32_t *row_ptr, const int32_t *col, const 
 
 typedef void (*StencilKernel)(const StepArgs);
 
-template <int Q>
+template <int DIM, int Q>
 StencilKernel pick_q(int law, bool kappa, bool fo) {
     if (law == PD_LAW_BILINEAR) {
-        if (fo) return kappa ? k_step_stencil<Q, 0, true, true> : k_step_stencil<Q, 0, false, true>;
-        return kappa ? k_step_stencil<Q, 0, true, false> : k_step_stencil<Q, 0, false, false>;
+        if (fo) return kappa ? k_step_stencil<DIM, Q, 0, true, true> : k_step_stencil<DIM, Q, 0, false, true>;
+        return kappa ? k_step_stencil<DIM, Q, 0, true, false> : k_step_stencil<DIM, Q, 0, false, false>;
     }
-    if (fo) return kappa ? k_step_stencil<Q, 1, true, true> : k_step_stencil<Q, 1, false, true>;
-    return kappa ? k_step_stencil<Q, 1, true, false> : k_step_stencil<Q, 1, false, false>;
+    if (fo) return kappa ? k_step_stencil<DIM, Q, 1, true, true> : k_step_stencil<DIM, Q, 1, false, true>;
+    return kappa ? k_step_stencil<DIM, Q, 1, true, false> : k_step_stencil<DIM, Q, 1, false, false>;
 }
 
-StencilKernel pick_stencil(int q, int law, bool kappa, bool fo) {
-    if (q == 4) return pick_q<4>(law, kappa, fo);
-    if (q == 2) return pick_q<2>(law, kappa, fo);
-    return pick_q<1>(law, kappa, fo);
+// The planar stencil's 16 rounds make two groups of 8 at Q = 1 only.
+StencilKernel pick_stencil(int dim, int q, int law, bool kappa, bool fo) {
+    if (dim == 2) return pick_q<2, 1>(law, kappa, fo);
+    if (q == 4) return pick_q<3, 4>(law, kappa, fo);
+    if (q == 2) return pick_q<3, 2>(law, kappa, fo);
+    return pick_q<3, 1>(law, kappa, fo);
 }
 
 unsigned blocks_of(long long n) { return (unsigned)((n + 255) / 256); }
@@ -392,12 +415,13 @@ int stencil_set_attributes(size_t smem) {
     PD_CHECK_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(mu);
     if (dev >= 0 && dev < 64 && smem <= limit[dev]) return PD_OK;
-    for (int q = 1; q <= 4; q *= 2)
-        for (int law = 0; law < 2; ++law)
-            for (int kap = 0; kap < 2; ++kap)
-                for (int fo = 0; fo < 2; ++fo)
-                    PD_CHECK_CUDA(cudaFuncSetAttribute((const void *)pick_stencil(q, law, kap, fo),
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int dim = 2; dim <= 3; ++dim)
+        for (int q = 1; q <= 4; q *= 2)
+            for (int law = 0; law < 2; ++law)
+                for (int kap = 0; kap < 2; ++kap)
+                    for (int fo = 0; fo < 2; ++fo)
+                        PD_CHECK_CUDA(cudaFuncSetAttribute((const void *)pick_stencil(dim, q, law, kap, fo),
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (dev >= 0 && dev < 64) limit[dev] = smem;
     return PD_OK;
 }
@@ -405,7 +429,12 @@ int stencil_set_attributes(size_t smem) {
 int stencil_build(pd_state *st, const int32_t *col) {
     const long long N = st->N;
     st->st_wpb = st->by * st->bz / 2;
-    st->st_len = st->n_bricks * st->st_wpb * (long long)kRounds * 32;
+    st->st_dim = st->g.nz == 1 ? 2 : 3;  // a one-layer grid has only the planar offsets
+    const int rounds = st->st_dim == 3 ? Sten<3>::kRounds : Sten<2>::kRounds;
+    const int haloz = st->st_dim == 3 ? Sten<3>::kHaloZ : Sten<2>::kHaloZ;
+    st->st_len = st->n_bricks * st->st_wpb * (long long)rounds * 32;
+    // staged records of the brick and its halo: float4 hi and lo per node
+    st->smem_bytes = 2 * sizeof(float4) * (size_t)kWx * (st->by + 2 * kHalo) * (st->bz + 2 * haloz);
     // split the half-stencil over Q warps when the mesh gives too few warps per SM
     // (measured on GB300: Q = 2 for single samples of the 28k-node beam, 1 for batches)
     const long long warps1 = st->n_bricks * st->B * st->st_wpb;
@@ -415,11 +444,13 @@ int stencil_build(pd_state *st, const int32_t *col) {
         if (v == 1 || v == 2 || v == 4) st->st_q = v;
     }
     if (st->q_req) st->st_q = st->q_req;
+    if (st->st_dim == 2) st->st_q = 1;
     while (st->st_q > 1 && 32 * st->st_wpb * st->st_q > 512) st->st_q /= 2;
     st->smem_bytes += (size_t)(st->st_q - 1) * st->st_wpb * 16 * 6 * sizeof(float);
     std::vector<int16_t> box(343, -1);
-    for (int m = 0; m < kHalf; ++m) {
-        const I3 k = half_off(m);
+    const int half = st->st_dim == 3 ? Sten<3>::kHalf : Sten<2>::kHalf;
+    for (int m = 0; m < half; ++m) {
+        const I3 k = st->st_dim == 3 ? half_off<3>(m) : half_off<2>(m);
         box[(k.z + 3) * 49 + (k.y + 3) * 7 + (k.x + 3)] = (int16_t)(2 * m);
         box[(-k.z + 3) * 49 + (-k.y + 3) * 7 + (-k.x + 3)] = (int16_t)(2 * m + 1);
     }
@@ -433,7 +464,7 @@ int stencil_build(pd_state *st, const int32_t *col) {
     PD_TRY(dalloc(&bad, 1));
     cudaMemset(bad, 0, sizeof(int32_t));
     k_stencil_template<<<blocks_of(N), 256>>>(st->row_ptr, col, st->coord, N, st->g.nx, st->g.ny, st->by, st->bz,
-                                              st->nbx, st->nby, st->st_wpb, st->st_box, st->st_tmpl, bad);
+                                              st->nbx, st->nby, st->st_wpb, rounds, st->st_box, st->st_tmpl, bad);
     int32_t hbad = 0;
     const cudaError_t e = cudaMemcpy(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost);
     cudaFree(bad);
@@ -444,8 +475,9 @@ int stencil_build(pd_state *st, const int32_t *col) {
 
 void stencil_fill_args(const pd_state *st, StepArgs &a) {
     const float dxf = (float)st->g.dx;
-    for (int m = 0; m < kHalf; ++m) {
-        const I3 k = half_off(m);
+    const int half = st->st_dim == 3 ? Sten<3>::kHalf : Sten<2>::kHalf;
+    for (int m = 0; m < half; ++m) {
+        const I3 k = st->st_dim == 3 ? half_off<3>(m) : half_off<2>(m);
         const int q = k.x * k.x + k.y * k.y + k.z * k.z;
         a.half_tab[m] = make_float4((float)k.x * dxf, (float)k.y * dxf, (float)k.z * dxf,
                                     (float)(std::sqrt((double)q) * st->g.dx));
@@ -466,17 +498,19 @@ int stencil_map_damage(const pd_state *st, double *csr, bool to_state, cudaStrea
     if (to_state)
         k_stencil_map<true><<<blocks_of(NB), 256, 0, s>>>(st->row_ptr, st->col_csr, st->coord, st->N, st->B, st->nb,
                                                           st->g.nx, st->g.ny, st->by, st->bz, st->nbx, st->nby,
-                                                          st->st_wpb, st->st_len, st->st_box, (float *)st->dmg, csr);
+                                                          st->st_wpb, st->st_dim == 3 ? Sten<3>::kRounds : Sten<2>::kRounds,
+                                                          st->st_len, st->st_box, (float *)st->dmg, csr);
     else
         k_stencil_map<false><<<blocks_of(NB), 256, 0, s>>>(st->row_ptr, st->col_csr, st->coord, st->N, st->B, st->nb,
                                                            st->g.nx, st->g.ny, st->by, st->bz, st->nbx, st->nby,
-                                                           st->st_wpb, st->st_len, st->st_box, (float *)st->dmg, csr);
+                                                           st->st_wpb, st->st_dim == 3 ? Sten<3>::kRounds : Sten<2>::kRounds,
+                                                          st->st_len, st->st_box, (float *)st->dmg, csr);
     PD_CHECK_LAUNCH();
     return PD_OK;
 }
 
 int stencil_launch(const pd_state *st, const StepArgs &a, bool force_only, cudaStream_t s) {
-    StencilKernel k = pick_stencil(st->st_q, st->mat.law, st->has_kappa, force_only);
+    StencilKernel k = pick_stencil(st->st_dim, st->st_q, st->mat.law, st->has_kappa, force_only);
     const unsigned grid = (unsigned)st->n_bricks * (unsigned)st->B;
     k<<<grid, 32 * st->st_wpb * st->st_q, st->smem_bytes, s>>>(a);
     PD_CHECK_LAUNCH();

@@ -71,7 +71,7 @@ static std::vector<pd_schedule> candidates(const pd_grid *g, const pd_material *
             continue;
         }
         const int wpb = by * bz / 2;
-        for (int q = 1; q <= 4; q *= 2)
+        for (int q = 1; q <= (g->nz == 1 ? 1 : 4); q *= 2)  // the planar stencil runs at q = 1
             if (32 * wpb * q <= 512) out.push_back(pd_schedule{by, bz, q});
     }
     return out;
