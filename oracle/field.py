@@ -31,7 +31,8 @@ What is computed, step by step:
 4. Gaussian field g = Phi diag(sqrt(lambda)) xi.
 5. Level coupling (Section 4.2, "a coarsened version of the random sample"):
    the coarse-level field is the mean of the fine field over the 2x2x2 fine
-   children of each coarse node, before the marginal transform.
+   children of each coarse node (2x2 for a plane hierarchy of one-layer
+   grids), before the marginal transform.
 6. Marginal transform (copula, Section 5.2): lognormal
    s0 = exp(mu + sigma g), sigma^2 = ln(1 + COV^2), mu = ln(mean) - sigma^2/2;
    Weibull s0 = F_W^-1(Phi(g)) with modulus m and scale mean / Gamma(1 + 1/m).
@@ -198,9 +199,15 @@ def gaussian(Phi, lam, xi) -> np.ndarray:
 
 
 def restrict(g: np.ndarray, grid) -> np.ndarray:
-    """Mean over the 2x2x2 fine children of each coarse node; g is [B, N_fine]."""
+    """Mean over the fine children of each coarse node; g is [B, N_fine]: 2x2x2
+    children in 3D, 2x2 on a one-layer grid (a plane hierarchy keeps nz = 1)."""
     B = g.shape[0]
     a = g.reshape(B, grid.nz, grid.ny, grid.nx)
+    if grid.nz == 1:
+        a = a.reshape(B, grid.ny // 2, 2, grid.nx // 2, 2)
+        a = a[..., 0] + a[..., 1]
+        a = a[:, :, 0, :] + a[:, :, 1, :]
+        return (a * 0.25).reshape(B, -1)
     a = a.reshape(B, grid.nz // 2, 2, grid.ny // 2, 2, grid.nx // 2, 2)
     # sum in a fixed order: x pairs, then y pairs, then z pairs
     a = a[..., 0] + a[..., 1]

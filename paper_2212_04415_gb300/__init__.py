@@ -341,7 +341,9 @@ class Field:
         self.h = h
         self.K = cfg.n_modes
         # node counts per level, coarsest first (each coarser grid halves nx, ny, nz)
-        self.sizes = [(finest.nx >> s, finest.ny >> s, finest.nz >> s) for s in range(n_levels - 1, -1, -1)]
+        # (a one-layer hierarchy halves nx and ny only)
+        self.sizes = [(finest.nx >> s, finest.ny >> s, finest.nz if finest.nz == 1 else finest.nz >> s)
+                      for s in range(n_levels - 1, -1, -1)]
 
     def close(self):
         """Free the field; raises if a sampling launch had given up waiting (PD_ERR_TIMEOUT)."""

@@ -223,7 +223,9 @@ __global__ void k_assemble_dense(long long N, int K, const double *vec, const do
 }
 
 // Coarse basis = mean over the 2x2x2 fine children (fixed order: x, y, z pairs).
-__global__ void k_restrict_basis(int cnx, int cny, int cnz, int K, const float *fine, float *coarse) {
+// Coarse basis = mean over the fine children: 2x2x2 in 3D, 2x2 in a planar
+// hierarchy (one-layer grids, planar = 1), summed x pairs, then y, then z.
+__global__ void k_restrict_basis(int cnx, int cny, int cnz, int K, int planar, const float *fine, float *coarse) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long Nc = (long long)cnx * cny * cnz;
     if (t >= Nc * K) return;
@@ -232,11 +234,15 @@ __global__ void k_restrict_basis(int cnx, int cny, int cnz, int K, const float *
     const int X = (int)(I % cnx), Y = (int)((I / cnx) % cny), Z = (int)(I / ((long long)cnx * cny));
     const int fnx = 2 * cnx, fny = 2 * cny;
     float s[2][2];
-    for (int dz = 0; dz < 2; ++dz)
+    for (int dz = 0; dz < (planar ? 1 : 2); ++dz)
         for (int dy = 0; dy < 2; ++dy) {
             const long long f = (2 * X) + (long long)fnx * ((2 * Y + dy) + (long long)fny * (2 * Z + dz));
             s[dz][dy] = fine[f * K + k] + fine[(f + 1) * K + k];
         }
+    if (planar) {
+        coarse[t] = (s[0][0] + s[0][1]) * 0.25f;
+        return;
+    }
     const float yz0 = s[0][0] + s[0][1], yz1 = s[1][0] + s[1][1];
     coarse[t] = (yz0 + yz1) * 0.125f;
 }
@@ -359,7 +365,8 @@ static int build_field(pd_field *f) {
         const pd_grid &c = f->grid[l];
         const long long Nc = (long long)c.nx * c.ny * c.nz;
         PD_TRY(dalloc(&f->phi[l], (size_t)Nc * K));
-        k_restrict_basis<<<(unsigned)((Nc * K + 255) / 256), 256>>>(c.nx, c.ny, c.nz, K, f->phi[l + 1], f->phi[l]);
+        k_restrict_basis<<<(unsigned)((Nc * K + 255) / 256), 256>>>(c.nx, c.ny, c.nz, K, f->grid[l + 1].nz == 1 ? 1 : 0,
+                                                                    f->phi[l + 1], f->phi[l]);
         PD_CHECK_LAUNCH();
     }
     for (int l = 0; l < f->n_levels; ++l) {
@@ -393,14 +400,15 @@ extern "C" int pd_field_create(const pd_grid *finest, int32_t n_levels, const pd
     f->grid[n_levels - 1] = *finest;
     for (int l = n_levels - 2; l >= 0; --l) {
         pd_grid c = f->grid[l + 1];
-        if (c.nx % 2 || c.ny % 2 || c.nz % 2) {
+        const bool planar = c.nz == 1;  // one-layer hierarchy: halve in plane only
+        if (c.nx % 2 || c.ny % 2 || (!planar && c.nz % 2)) {
             delete f;
             set_error("grid of level %d cannot be halved (%d x %d x %d)", l + 1, c.nx, c.ny, c.nz);
             return PD_ERR_ARG;
         }
         c.nx /= 2;
         c.ny /= 2;
-        c.nz /= 2;
+        if (!planar) c.nz /= 2;
         c.dx *= 2.0;
         f->grid[l] = c;
     }

@@ -232,7 +232,7 @@ extern "C" int mlmc_estimate(const pd_mlmc_cfg *cfg, pd_mlmc_result *out, double
     }
     for (int l = 1; l < cfg->n_levels; ++l) {
         const pd_grid &f = cfg->grid[l], &c = cfg->grid[l - 1];
-        PD_REQUIRE(f.nx == 2 * c.nx && f.ny == 2 * c.ny && f.nz == 2 * c.nz &&
+        PD_REQUIRE(f.nx == 2 * c.nx && f.ny == 2 * c.ny && (f.nz == 2 * c.nz || (f.nz == 1 && c.nz == 1)) &&
                        std::fabs(f.dx * 2.0 - c.dx) <= 1e-12 * c.dx,
                    "grid %d is not the 2x refinement of grid %d", l, l - 1);
     }
@@ -277,7 +277,7 @@ extern "C" int mlmc_adaptive(const pd_mlmc_cfg *cfg, const pd_mlmc_adaptive_cfg 
     PD_REQUIRE(ad->n_star >= 2, "n_star must be >= 2");
     for (int l = 1; l < cfg->n_levels; ++l) {
         const pd_grid &f = cfg->grid[l], &c = cfg->grid[l - 1];
-        PD_REQUIRE(f.nx == 2 * c.nx && f.ny == 2 * c.ny && f.nz == 2 * c.nz &&
+        PD_REQUIRE(f.nx == 2 * c.nx && f.ny == 2 * c.ny && (f.nz == 2 * c.nz || (f.nz == 1 && c.nz == 1)) &&
                        std::fabs(f.dx * 2.0 - c.dx) <= 1e-12 * c.dx,
                    "grid %d is not the 2x refinement of grid %d", l, l - 1);
     }

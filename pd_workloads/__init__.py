@@ -203,6 +203,29 @@ def small_beam_levels():
     return out
 
 
+def small_plane_levels(u_max: float = 3e-5):
+    """A two-level plane-stress hierarchy (the paper's dimensionality): a notched
+    80 x 25 mm beam, t = 50 mm, delta = pi dx, dx = 5 / 2.5 mm (16 x 5 and
+    32 x 10 nodes), exp-linear law calibrated to G_F = 30 N/m, 6 / 4 samples,
+    600 / 1200 steps (the ramp scaled with the level)."""
+    import math
+    D, L = 25.0, 80.0
+    out = []
+    for lvl, (dxm, nl) in enumerate(((5.0, 6), (2.5, 4))):
+        n_steps = 600 * (2 ** lvl)
+        nx, ny = round(L / dxm), round(D / dxm)
+        g = Grid(nx, ny, 1, dxm * 1e-3, math.pi, 1, nx, round(2 * 0.2 * D / dxm))
+        span = 2.5 * D
+        sx = ((L - span) / 2.0, (L + span) / 2.0)
+        bc = BC(BC_BEAM_3PT, u_max=u_max, n_ramp=n_steps,
+                support_x2=(round(2 * sx[0] / dxm), round(2 * sx[1] / dxm)), load_x2=nx)
+        mat = Material(E=30e9, law=LAW_EXPLINEAR, s0=1e-4, zeta=5e4, G_F=30.0, model=MODEL_PLANE_STRESS,
+                       thickness=0.05)
+        fld = FieldCfg(COV_SQEXP, 5e-3, 16, MARG_LOGNORMAL, 1e-4, 0.1)
+        out.append(Workload(f"small_plane_beam_80x25_dx{dxm}mm", g, mat, bc, n_steps, fld, 3, batch=nl))
+    return out
+
+
 def sweep(D_mm: float, dx_mm: float = 2.5, n_steps: int = 5000) -> Workload:
     """Size-effect sweep member: depth D, span 3 D, length 3.5 D, thickness 50 mm."""
     L, T = 3.5 * D_mm, 50.0

@@ -198,3 +198,26 @@ def test_multi_state_run_equals_separate_runs(pd):
     sf.close()
     sc.close()
     fld.close()
+
+
+def test_plane_mlmc_against_oracle(pd):
+    """A two-level plane-stress hierarchy (one-layer grids, the field restricted
+    over 2 x 2 in-plane children): per-sample pairs and the estimator."""
+    levels = W.small_plane_levels()
+    a = _args(levels)
+    res = pd.mlmc_estimate(batch=4, return_samples=True, **a)
+    off = 0
+    Yh, V = [], []
+    for l, n in enumerate(a["n_samples"]):
+        qf, qc = res["q_fine"][off:off + n], res["q_coarse"][off:off + n]
+        off += n
+        of, oc = _oracle_pairs(levels, l, list(range(n)))
+        print(f"plane level {l}: Qf {qf} vs {of}; Qc {qc} vs {oc}")
+        assert np.all(np.abs(qf - of) <= 1e-3 * np.abs(of))
+        assert np.all(np.abs(qc - oc) <= 1e-3 * np.maximum(np.abs(oc), 1e-30))
+        mean, var_b, _ = omlmc.level_stats(of - oc)
+        assert abs(res["levels"][l]["mean"] - mean) <= 2e-3 * np.abs(of).max()
+        Yh.append(mean)
+        V.append(var_b)
+    q, _ = omlmc.mlmc_estimate(Yh, V, a["n_samples"])
+    assert abs(res["q_ml"] - q) <= 2e-3 * abs(q)

@@ -93,3 +93,14 @@ def test_restriction_is_child_mean():
                 expect.append(fine[2 * Z:2 * Z + 2, 2 * Y:2 * Y + 2, 2 * X:2 * X + 2].sum() / 8)
     assert c.shape == (1, 4)
     assert np.allclose(c[0], expect, rtol=1e-15, atol=0)
+
+
+def test_plane_restriction_is_in_plane_child_mean():
+    """A plane hierarchy keeps one layer: the coarse node is the mean of its 2x2 children."""
+    g = W.Grid(6, 4, 1, 1e-3, 3.01)
+    f = np.arange(24, dtype=np.float64)[None, :] ** 1.5
+    c = field.restrict(f, g)
+    fine = f.reshape(4, 6)  # (y, x)
+    expect = [fine[2 * Y:2 * Y + 2, 2 * X:2 * X + 2].sum() / 4 for Y in range(2) for X in range(3)]
+    assert c.shape == (1, 6)
+    assert np.allclose(c[0], expect, rtol=1e-15, atol=0)
