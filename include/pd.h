@@ -191,12 +191,15 @@ PD_API int pd_state_create(const pd_grid *g, const int32_t *row_ptr, const int32
                     pd_state **out);
 
 /* Launch schedule of a state: bricks of 8 x by x bz nodes per block (by bz
- * even and <= 32 on the compile-time stencil path) and q warps sharing each
- * row pair's half-stencil (1, 2 or 4; 0 = the built-in choice). A schedule
- * changes the summation grouping, not the method: results agree to rounding.
- * The paper has no counterpart. */
+ * even and <= 32 on the compile-time stencil path), q warps sharing each
+ * row pair's half-stencil (1, 2 or 4; 0 = the built-in choice) and ns
+ * samples per block on that path (1, or 2: a pair of samples computed
+ * together on the paired FP32 instructions, bit-identical per sample to
+ * ns = 1; 0 = the built-in choice, 1). A
+ * schedule changes the summation grouping, not the method: results agree to
+ * rounding. The paper has no counterpart. */
 typedef struct pd_schedule {
-    int32_t by, bz, q;
+    int32_t by, bz, q, ns;
 } pd_schedule;
 
 /* pd_state_create with an explicit schedule (NULL: the built-in choice). */

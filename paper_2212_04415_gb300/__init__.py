@@ -61,7 +61,7 @@ class AdaptiveCfg(C.Structure):
 
 
 class Schedule(C.Structure):
-    _fields_ = [("by", C.c_int32), ("bz", C.c_int32), ("q", C.c_int32)]
+    _fields_ = [("by", C.c_int32), ("bz", C.c_int32), ("q", C.c_int32), ("ns", C.c_int32)]
 
 
 class MlmcLevel(C.Structure):
@@ -204,7 +204,8 @@ class State:
     """B independent samples of the explicit peridynamic dynamics on one mesh."""
 
     def __init__(self, g, row, col, mat, bc, batch=1, precision=PREC_MIXED, dt=0.0, schedule=None):
-        """schedule: None (built-in choice) or (by, bz, q), e.g. from ``autotune``."""
+        """schedule: None (built-in choice) or (by, bz, q) / (by, bz, q, ns), e.g.
+        from ``autotune`` (ns: samples per block, 0 = built-in)."""
         import torch
         torch.cuda.synchronize()
         self.grid = g
@@ -311,14 +312,14 @@ def run_to_peak_multi(states, max_steps, stream=None):
 
 
 def autotune(g, row, col, mat, bc, batch=1, precision=PREC_MIXED, trial_steps=20, dt=0.0):
-    """Fastest launch schedule (by, bz, q) of a mesh and batch, and its time per
-    step in microseconds (pd_autotune; cached per process)."""
+    """Fastest launch schedule (by, bz, q, ns) of a mesh and batch, and its time
+    per step in microseconds (pd_autotune; cached per process)."""
     G, M, BCs = grid_struct(g), material_struct(mat, precision, dt), bc_struct(bc)
     best = Schedule()
     us = C.c_double()
     _check(lib().pd_autotune(C.byref(G), _ptr(row), _ptr(col), int(col.numel()), C.byref(M), C.byref(BCs), batch,
                              trial_steps, C.byref(best), C.byref(us)))
-    return (best.by, best.bz, best.q), us.value
+    return (best.by, best.bz, best.q, best.ns), us.value
 
 
 def draw_xi(seed, level, sample_ids, n_modes, stream=None, out=None):

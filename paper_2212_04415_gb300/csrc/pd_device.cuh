@@ -77,6 +77,7 @@ struct StepArgs {
     float cVf, s_ratio_f, k_f, alpha_f, inv_1mek_f, inv_1pa_f;
     double gfA;   // > 0: s_crit = s0 + gfA / s0, else s_ratio s0
     float gfA_f;
+    df cV_df, cVh_df;  // cV and cV / 2 as double-float (stencil path: applied to the node sums)
 };
 
 __device__ __forceinline__ double warp_sum(double v) {

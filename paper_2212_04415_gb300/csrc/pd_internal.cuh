@@ -101,6 +101,8 @@ struct pd_state {
     int32_t st_q;           // warps sharing a row pair (parts of the half-stencil)
     int32_t q_req;          // requested st_q (schedule), 0 = built-in choice
     int32_t st_dim;         // 3, or 2 for a one-layer grid (planar 28-offset stencil)
+    int32_t st_ns;          // samples per block (1, or 2 on the paired FP32 instructions)
+    int32_t ns_req;         // requested st_ns (schedule), 0 = built-in choice
     int64_t st_len;         // damage slots per sample
     float *st_tmpl;         // [st_len]: 0 for real bonds, 1 for absent (broken) slots
     int16_t *st_box;        // [7^3]: stencil code 2 m + t of an offset, -1 outside

@@ -669,6 +669,8 @@ static StepArgs make_args(const pd_state *st) {
     a.gfA = st->gfA;
     a.gfA_f = (float)st->gfA;
     a.cVf = (float)a.cV;
+    a.cV_df = df_split(a.cV);
+    a.cVh_df = df_split(0.5 * a.cV);
     a.s_ratio_f = (float)a.s_ratio;
     a.k_f = (float)a.k;
     a.alpha_f = (float)a.alpha;
@@ -1040,8 +1042,16 @@ extern "C" int pd_state_create_sched(const pd_grid *g, const int32_t *row_ptr, c
         }
         st->q_req = sched ? sched->q : 0;
         if (st->q_req != 0 && st->q_req != 1 && st->q_req != 2 && st->q_req != 4) {
+            const int q = st->q_req;
             delete st;
-            set_error("schedule q = %d is not 0, 1, 2 or 4", st->q_req);
+            set_error("schedule q = %d is not 0, 1, 2 or 4", q);
+            return PD_ERR_ARG;
+        }
+        st->ns_req = sched ? sched->ns : 0;
+        if (st->ns_req < 0 || st->ns_req > 2) {
+            const int v = st->ns_req;
+            delete st;
+            set_error("schedule ns = %d is not 0, 1 or 2", v);
             return PD_ERR_ARG;
         }
     }

@@ -40,8 +40,9 @@ static double slot_ratio(const pd_grid *g, int by, int bz) {
 
 // Candidates: the five bricks with the least ragged-edge waste (larger bricks
 // first among equals: they stage fewer halo records per node), each with
-// every warp split that fits a block.
-static std::vector<pd_schedule> candidates(const pd_grid *g, const pd_material *mat) {
+// every warp split that fits a block and, for batches on the stencil path,
+// one or two samples per block.
+static std::vector<pd_schedule> candidates(const pd_grid *g, const pd_material *mat, int batch) {
     std::vector<pd_schedule> out;
     const double m2 = g->m_ratio * g->m_ratio;
     const bool stencil = mat->precision == PD_PREC_MIXED && m2 >= 9.0 && m2 < 10.0;
@@ -67,12 +68,16 @@ static std::vector<pd_schedule> candidates(const pd_grid *g, const pd_material *
         ++kept;
         const int by = b.second.first, bz = b.second.second;
         if (!stencil) {
-            out.push_back(pd_schedule{by, bz, 0});
+            out.push_back(pd_schedule{by, bz, 0, 0});
             continue;
         }
         const int wpb = by * bz / 2;
-        for (int q = 1; q <= (g->nz == 1 ? 1 : 4); q *= 2)  // the planar stencil runs at q = 1
-            if (32 * wpb * q <= 512) out.push_back(pd_schedule{by, bz, q});
+        const int zhalo = g->nz == 1 ? 0 : 6;
+        for (int ns = batch >= 2 ? 2 : 1; ns >= 1; --ns) {
+            if ((size_t)14 * (by + 6) * (bz + zhalo) * 32 * ns > 200 * 1024) continue;
+            for (int q = 1; q <= (g->nz == 1 ? 1 : 4); q *= 2)  // the planar stencil runs at q = 1
+                if (32 * wpb * q <= 512) out.push_back(pd_schedule{by, bz, q, ns});
+        }
     }
     return out;
 }
@@ -98,14 +103,14 @@ extern "C" int pd_autotune(const pd_grid *g, const int32_t *row_ptr, const int32
             return PD_OK;
         }
     }
-    const std::vector<pd_schedule> cand = candidates(g, mat);
+    const std::vector<pd_schedule> cand = candidates(g, mat, batch);
     PD_REQUIRE(!cand.empty(), "no candidate schedule for this grid");
     cudaStream_t s;
     PD_CHECK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    TuneEntry win{{0, 0, 0}, INFINITY};
+    TuneEntry win{{0, 0, 0, 0}, INFINITY};
     for (const pd_schedule &c : cand) {
         pd_state *st = nullptr;
         if (pd_state_create_sched(g, row_ptr, col, n_bonds, mat, bc, batch, &c, &st) != PD_OK) continue;
