@@ -195,11 +195,15 @@ PD_API int pd_state_create(const pd_grid *g, const int32_t *row_ptr, const int32
  * row pair's half-stencil (1, 2 or 4; 0 = the built-in choice) and ns
  * samples per block on that path (1, or 2: a pair of samples computed
  * together on the paired FP32 instructions, bit-identical per sample to
- * ns = 1; 0 = the built-in choice, 1). A
- * schedule changes the summation grouping, not the method: results agree to
- * rounding. The paper has no counterpart. */
+ * ns = 1; 0 = the built-in choice, 1) and where each step's reaction force
+ * is reduced on that path (1: in the step's own launch; 2: by every block of
+ * the next launch, before it steps, so a single-wave launch has no serial
+ * reduction tail; the last launch of every call reduces its own; results are
+ * bit-identical; 0 = the built-in choice, 2 for launches of at most four
+ * blocks per SM). A schedule changes the summation grouping, not the method:
+ * results agree to rounding. The paper has no counterpart. */
 typedef struct pd_schedule {
-    int32_t by, bz, q, ns;
+    int32_t by, bz, q, ns, reduce;
 } pd_schedule;
 
 /* pd_state_create with an explicit schedule (NULL: the built-in choice). */

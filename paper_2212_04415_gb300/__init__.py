@@ -61,7 +61,7 @@ class AdaptiveCfg(C.Structure):
 
 
 class Schedule(C.Structure):
-    _fields_ = [("by", C.c_int32), ("bz", C.c_int32), ("q", C.c_int32), ("ns", C.c_int32)]
+    _fields_ = [("by", C.c_int32), ("bz", C.c_int32), ("q", C.c_int32), ("ns", C.c_int32), ("reduce", C.c_int32)]
 
 
 class MlmcLevel(C.Structure):
@@ -204,8 +204,9 @@ class State:
     """B independent samples of the explicit peridynamic dynamics on one mesh."""
 
     def __init__(self, g, row, col, mat, bc, batch=1, precision=PREC_MIXED, dt=0.0, schedule=None):
-        """schedule: None (built-in choice) or (by, bz, q) / (by, bz, q, ns), e.g.
-        from ``autotune`` (ns: samples per block, 0 = built-in)."""
+        """schedule: None (built-in choice) or (by, bz, q[, ns[, reduce]]), e.g.
+        from ``autotune`` (ns: samples per block; reduce: 1 = each step's
+        reaction in its own launch, 2 = in the next launch; 0 = built-in)."""
         import torch
         torch.cuda.synchronize()
         self.grid = g

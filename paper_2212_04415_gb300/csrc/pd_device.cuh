@@ -45,12 +45,17 @@ struct StepArgs {
     const uint8_t *codes;
     int32_t *step;         // [2][B]: step index, double-buffered by launch parity
     int32_t *done;         // [2][B]: stop flags, double-buffered the same way
+    int32_t *pend;         // [2][B]: the launch that wrote this buffer left its reaction partials pending
+    double *pk2;           // [2][B]: peak reaction so far, double-buffered the same way
+    int32_t *ps2;          // [2][B]: its step
     int par;               // this launch reads buffer par and writes buffer 1 - par
+    int defer;             // stencil path: leave this step's reaction to the next launch
+    int pendable;          // stencil path: some launch of this state may defer (blocks build run views)
     const int32_t *brick_ridx;  // [n_bricks]: index among the reaction bricks, or -1
     int32_t *status;
     double *peak;
     int32_t *peak_step;
-    double *partial;
+    double *partial;       // [2][B][nblk] block partials (double-float), by launch parity
     unsigned int *ticket;
     double *reaction;
     int n_react;
@@ -197,13 +202,126 @@ __device__ __forceinline__ void prescribed(const StepArgs &a, int n, df &U1, df 
     vp = df_mul(a.dudt_df, df{(float)(m1 - m0), 0.f});
 }
 
-// Bookkeeping of a step launch. Blocks read step/done from buffer par and the
-// last reaction block of a sample writes buffer 1 - par, so no block has to
-// wait for the others to have read the step index. A sample that is already
-// done is carried over by brick 0.
+// Bookkeeping of a step launch. Blocks read step/done (and the peak so far)
+// from buffer par and the launch writes buffer 1 - par, so no block has to
+// wait for the others to have read them.
+//
+// The reaction of a step is reduced either in its own launch (the last
+// reaction block to finish adds the block partials: a fence and a ticket,
+// "finish") or, on the stencil path, in the next launch ("defer"): the step's
+// reaction blocks store their partials with plain stores, and every block of
+// the next launch adds them in the same fixed order before it does anything
+// else, so all blocks reach the same peak and stop decision from the same
+// bits; the kernel boundary orders the stores before those loads. The stop
+// rule then applies at the same step either way. The last launch of every
+// call (and of every captured chunk) finishes, so the host sees final values.
+
+// Run bookkeeping of one sample as a launch sees it.
+struct RunView {
+    int n;      // the step this launch would compute
+    int dn;     // the sample is done (this launch computes nothing for it)
+    double Q;   // peak so far
+    int np;     // its step
+    double Rp;  // reaction of step n - 1, when this launch reduced it (have)
+    int have;
+};
+
+// Read the bookkeeping of sample b, adding the pending reaction of the
+// previous launch (one warp, all lanes; every lane ends with the same view).
+// The bookkeeping and the partials are all requested at once (one L2 round
+// trip; the partials are read whether or not they are pending).
+__device__ __forceinline__ RunView run_view(const StepArgs &a, int b, int lane) {
+    const int i = a.par * a.B + b;
+    const float2 *part = (const float2 *)a.partial + ((size_t)(1 - a.par) * a.B + b) * a.nblk;
+    RunView r;
+    const int pe = a.pend[i];
+    r.dn = a.done[i];
+    r.n = a.step[i];
+    r.Q = a.pk2[i];
+    r.np = a.ps2[i];
+    const float2 p0 = lane < a.nblk ? __ldcg(part + lane) : make_float2(0.f, 0.f);
+    r.Rp = 0.0;
+    r.have = 0;
+    if (r.dn || !pe) return r;
+    df acc = {p0.x, p0.y};
+    for (int q = lane + 32; q < a.nblk; q += 32) {
+        const float2 pv = __ldcg(part + q);
+        acc = df_add(acc, df{pv.x, pv.y});
+    }
+    acc = warp_sum_df(acc);
+    const double R = a.V * ((double)acc.hi + (double)acc.lo);
+    r.Rp = R;
+    r.have = 1;
+    if (R > r.Q) {
+        r.Q = R;
+        r.np = r.n - 1;
+    }
+    r.dn = (a.use_stop && ((r.Q > 0.0 && (r.n - 1) - r.np >= 100 && R < 0.5 * r.Q) || r.n >= a.max_steps)) ||
+                   !isfinite(R)
+               ? 1
+               : 0;
+    return r;
+}
+
+// Outputs of the reaction this launch reduced for the previous step.
+__device__ __forceinline__ void publish_pending(const StepArgs &a, int b, const RunView &r) {
+    if (!r.have) return;
+    a.peak[b] = r.Q;
+    a.peak_step[b] = r.np;
+    if (!isfinite(r.Rp)) a.status[b] |= 1;
+    if (a.reaction && a.k_local >= 1) a.reaction[(size_t)b * a.n_react + a.k_local - 1] = r.Rp;
+}
+
+// Buffer 1 - par of a sample this launch does not step (done before, or done
+// by the reaction it just reduced); brick 0 writes it.
+__device__ __forceinline__ void write_done(const StepArgs &a, int b, const RunView &r) {
+    const int o = (1 - a.par) * a.B + b;
+    a.step[o] = r.n;
+    a.done[o] = 1;
+    a.pend[o] = 0;
+    a.pk2[o] = r.Q;
+    a.ps2[o] = r.np;
+    publish_pending(a, b, r);
+}
+
+// Buffer 1 - par of a live sample whose reaction is left to the next launch.
+__device__ __forceinline__ void write_deferred(const StepArgs &a, int b, const RunView &r) {
+    const int o = (1 - a.par) * a.B + b;
+    a.step[o] = r.n + 1;
+    a.done[o] = 0;
+    a.pend[o] = 1;
+    a.pk2[o] = r.Q;
+    a.ps2[o] = r.np;
+    publish_pending(a, b, r);
+}
+
+// A sample that is already done is carried over by brick 0.
 __device__ __forceinline__ void carry_done(const StepArgs &a, int b) {
-    a.step[(1 - a.par) * a.B + b] = a.step[a.par * a.B + b];
-    a.done[(1 - a.par) * a.B + b] = 1;
+    const int i = a.par * a.B + b;
+    RunView r;
+    r.n = a.step[i];
+    r.Q = a.pk2[i];
+    r.np = a.ps2[i];
+    r.dn = 1;
+    r.Rp = 0.0;
+    r.have = 0;
+    write_done(a, b, r);
+}
+
+// Deferred reaction: the block's partial (sum over its prescribed DOFs of
+// -F sign, double-float, warp then the block's warps in order) is stored for
+// the next launch. Called by every thread of a reaction block.
+__device__ __forceinline__ void reaction_defer(const StepArgs &a, df Rloc, int b, int blk, int warp, int lane,
+                                               int nwarps, float2 *red) {
+    if (__any_sync(0xffffffffu, Rloc.hi != 0.f || Rloc.lo != 0.f)) Rloc = warp_sum_df(Rloc);
+    if (lane == 0) red[warp] = make_float2(Rloc.hi, Rloc.lo);
+    __syncthreads();
+    if (warp == 0) {
+        df v = {0.f, 0.f};
+        if (lane < nwarps) v = df{red[lane].x, red[lane].y};
+        if (__any_sync(0xffffffffu, v.hi != 0.f || v.lo != 0.f)) v = warp_sum_df(v);
+        if (lane == 0) ((float2 *)a.partial)[((size_t)a.par * a.B + b) * a.nblk + blk] = make_float2(v.hi, v.lo);
+    }
 }
 
 // End of a step kernel in a reaction brick (one holding prescribed DOFs, or
@@ -211,10 +329,12 @@ __device__ __forceinline__ void carry_done(const StepArgs &a, int b) {
 // reaction sum (sum over prescribed DOFs of -F sign, double-float) is reduced
 // along fixed trees -- warp, the block's warps in order (by the block's last
 // warp to finish), the reaction bricks of the sample in order (by the
-// sample's last reaction block) -- which then updates the run bookkeeping.
+// sample's last reaction block) -- which then updates the run bookkeeping
+// from the run view that every block of the launch holds (and publishes the
+// previous step's reaction if this launch reduced it).
 // FP64 appears only in the final conversion R = V (hi + lo) and the peak test.
 __device__ __forceinline__ void reaction_finish(const StepArgs &a, df Rloc, int b, int blk, int warp, int lane,
-                                                int nwarps, float2 *red, unsigned *s_cnt, int n) {
+                                                int nwarps, float2 *red, unsigned *s_cnt, const RunView &rv) {
     if (__any_sync(0xffffffffu, Rloc.hi != 0.f || Rloc.lo != 0.f)) Rloc = warp_sum_df(Rloc);
     unsigned flag = 0u;
     if (lane == 0) {
@@ -232,7 +352,7 @@ __device__ __forceinline__ void reaction_finish(const StepArgs &a, df Rloc, int 
     }
     // (shared-memory partials: one round trip)
     if (__any_sync(0xffffffffu, v.hi != 0.f || v.lo != 0.f)) v = warp_sum_df(v);
-    float2 *part = (float2 *)a.partial + (size_t)b * a.nblk;
+    float2 *part = (float2 *)a.partial + ((size_t)a.par * a.B + b) * a.nblk;
     if (lane == 0) {
         part[blk] = make_float2(v.hi, v.lo);
         __threadfence();
@@ -256,18 +376,26 @@ __device__ __forceinline__ void reaction_finish(const StepArgs &a, df Rloc, int 
     }
     acc = warp_sum_df(acc);
     if (lane == 0) {
+        const int n = rv.n;
+        double Q = rv.have ? rv.Q : a.pk2[a.par * a.B + b];  // no view built: the buffer as read
+        int np = rv.have ? rv.np : a.ps2[a.par * a.B + b];
+        if (rv.have) {
+            if (!isfinite(rv.Rp)) a.status[b] |= 1;
+            if (a.reaction && a.k_local >= 1) a.reaction[(size_t)b * a.n_react + a.k_local - 1] = rv.Rp;
+        }
         const double R = a.V * ((double)acc.hi + (double)acc.lo);
         if (!isfinite(R)) a.status[b] |= 1;
         if (a.reaction) a.reaction[(size_t)b * a.n_react + a.k_local] = R;
-        double Q = a.peak[b];
-        int np = a.peak_step[b];
         if (R > Q) {
             Q = R;
             np = n;
-            a.peak[b] = Q;
-            a.peak_step[b] = np;
         }
+        a.peak[b] = Q;
+        a.peak_step[b] = np;
         const int out = (1 - a.par) * a.B + b;
+        a.pk2[out] = Q;
+        a.ps2[out] = np;
+        a.pend[out] = 0;
         a.step[out] = n + 1;
         a.done[out] = (a.use_stop && ((Q > 0.0 && n - np >= 100 && R < 0.5 * Q) || n + 1 >= a.max_steps)) ||
                               !isfinite(R)

@@ -102,7 +102,9 @@ struct pd_state {
     int32_t q_req;          // requested st_q (schedule), 0 = built-in choice
     int32_t st_dim;         // 3, or 2 for a one-layer grid (planar 28-offset stencil)
     int32_t st_ns;          // samples per block (1, or 2 on the paired FP32 instructions)
+    int32_t st_defer;       // launches may leave their reaction to the next launch (few blocks per SM)
     int32_t ns_req;         // requested st_ns (schedule), 0 = built-in choice
+    int32_t reduce_req;     // requested reaction reduction (schedule): 0 built-in, 1 own launch, 2 deferred
     int64_t st_len;         // damage slots per sample
     float *st_tmpl;         // [st_len]: 0 for real bonds, 1 for absent (broken) slots
     int16_t *st_box;        // [7^3]: stencil code 2 m + t of an offset, -1 outside
@@ -121,6 +123,9 @@ struct pd_state {
     // run bookkeeping (device)
     int32_t *step;      // [2][B], double-buffered by launch parity
     int32_t *done;      // [2][B]
+    int32_t *pend;      // [2][B]: reaction partials left pending by the launch that wrote this buffer
+    double *pk2;        // [2][B]: peak so far, double-buffered like step
+    int32_t *ps2;       // [2][B]: its step
     int32_t bk_par;     // buffer holding the current step/done
     int32_t chunk_par;  // parity the captured chunk starts from
     int32_t *brick_ridx;  // [n_bricks]: index among reaction bricks, or -1
@@ -128,7 +133,7 @@ struct pd_state {
     int32_t *status;    // [B] bit 0: non-finite reaction
     double *peak;       // [B]
     int32_t *peak_step; // [B]
-    double *partial;    // [B][nblk]
+    double *partial;    // [2][B][nblk]: reaction block partials (double-float), by launch parity
     uint32_t *ticket;   // [B]
     int32_t nblk;
     // run_to_peak chunk graph

@@ -318,6 +318,7 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
     __shared__ float2 red[NS][16];
     __shared__ float s_pre[NS][4];  // U(n+1) and the prescribed velocity, double-float
     __shared__ unsigned s_cnt[NS];
+    __shared__ RunView s_rv[NS];               // run bookkeeping per sample, with the pending reaction added
     __shared__ float4 s_tab[2][NS * kRounds];  // per sub-lane sign
     __shared__ V s_kw2[kRounds];
     __shared__ int s_offb[2][kRounds];          // per sign: byte offset of the neighbour's staged record
@@ -327,6 +328,7 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
     const int ngrp = (a.B + NS - 1) / NS;
     const int grp = blockIdx.x % ngrp;
     const int brick = blockIdx.x / ngrp;
+    const int ridx = FORCE_ONLY ? -1 : a.brick_ridx[brick];  // requested early: read at the end
     int bs[NS], ns[NS];
     bool live[NS];
     bool any = false;
@@ -342,6 +344,26 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
         any = any || live[s];
     }
     if (!any) return;  // block-uniform
+    // the run view (with the previous launch's reaction, if it left it
+    // pending) is built by warp s for sample s while the staging copies fly
+    const auto build_views = [&]() {
+        if (FORCE_ONLY || !a.pendable) return;
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        for (int s = w; s < NS; s += nwarps) {
+            RunView rv;
+            if (live[s]) {
+                rv = run_view(a, bs[s], l);
+            } else {
+                rv.n = ns[s];
+                rv.dn = 1;
+                rv.Q = 0.0;
+                rv.np = 0;
+                rv.Rp = 0.0;
+                rv.have = 0;
+            }
+            if (l == 0) s_rv[s] = rv;
+        }
+    };
     if (threadIdx.x < 16 * NS) (&red[0][0])[threadIdx.x] = make_float2(0.f, 0.f);
     if (threadIdx.x < NS) {
         df U1, vp;
@@ -393,6 +415,7 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
             cp_async16(dst, rhi + gi, in ? 16 : 0);
             cp_async16(dst + kChunkB, rlo + gi, in ? 16 : 0);
         }
+        build_views();
         cp_async_wait_all();
     } else {
         const float4 *rh0 = (const float4 *)((ns[0] & 1) ? a.rec1 : a.rec0) + (size_t)bs[0] * a.N;
@@ -415,8 +438,22 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
             *(float4 *)(dst + 2 * kChunkB) = make_float4(l0.x, l1.x, l0.y, l1.y);
             *(float4 *)(dst + 3 * kChunkB) = make_float4(l0.z, l1.z, l0.w, l1.w);
         }
+        build_views();
     }
     __syncthreads();
+    if (!FORCE_ONLY && a.pendable) {
+        // samples that the reduced reaction stops are not stepped (every
+        // block reaches the same decision); brick 0 records them
+        bool anyl = false;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const bool stop = live[s] && s_rv[s].dn;
+            if (stop && brick == 0 && threadIdx.x == 0) write_done(a, bs[s], s_rv[s]);
+            live[s] = live[s] && !stop;
+            anyl = anyl || live[s];
+        }
+        if (!anyl) return;  // block-uniform
+    }
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rp = warp % wpb, part = warp / wpb;
@@ -540,11 +577,27 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
     }
     if (FORCE_ONLY) return;
 
-    const int ridx = a.brick_ridx[brick];
-    if (ridx < 0) return;
 #pragma unroll
-    for (int s = 0; s < NS; ++s)
-        if (live[s]) reaction_finish(a, Rloc[s], bs[s], ridx, warp, lane, nwarps, red[s], &s_cnt[s], ns[s]);
+    for (int s = 0; s < NS; ++s) {
+        if (!live[s]) continue;  // block-uniform
+        RunView rv;
+        if (a.pendable) {
+            rv = s_rv[s];
+        } else {  // nothing is ever pending: the finishing block reads the peak itself
+            rv.n = ns[s];
+            rv.dn = 0;
+            rv.Q = 0.0;
+            rv.np = 0;
+            rv.Rp = 0.0;
+            rv.have = 0;
+        }
+        if (a.defer) {
+            if (brick == 0 && threadIdx.x == 0) write_deferred(a, bs[s], rv);
+            if (ridx >= 0) reaction_defer(a, Rloc[s], bs[s], ridx, warp, lane, nwarps, red[s]);
+        } else if (ridx >= 0) {
+            reaction_finish(a, Rloc[s], bs[s], ridx, warp, lane, nwarps, red[s], &s_cnt[s], rv);
+        }
+    }
 }
 
 // Slot of node i, stencil code (2 m + t), in the per-sample damage array.
@@ -695,6 +748,18 @@ int stencil_build(pd_state *st, const int32_t *col) {
     if (st->q_req) st->st_q = st->q_req;
     if (st->st_dim == 2) st->st_q = 1;
     while (st->st_q > 1 && 32 * st->st_wpb * st->st_q > 512) st->st_q /= 2;
+    // Deferring the reaction to the next launch pays when a launch is a
+    // single wave of a few blocks per SM, whose reduction tail would
+    // otherwise stand alone at the end (measured on GB300: 28k-node beam,
+    // one sample, 19.3 -> 18 us per step); with many waves the tail overlaps
+    // other blocks and the deferred read only adds to each block's start.
+    {
+        int dev = 0, sms = 0;
+        PD_CHECK_CUDA(cudaGetDevice(&dev));
+        PD_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        st->st_defer = st->n_bricks * ((st->B + st->st_ns - 1) / st->st_ns) <= 4ll * sms;
+        if (st->reduce_req) st->st_defer = st->reduce_req == 2;
+    }
     // the one-sample kernel (force-only evaluations) needs no more than this
     st->smem_bytes = 2 * sizeof(float4) * st->st_ns * cells +
                      (size_t)(st->st_q - 1) * st->st_wpb * 16 * 6 * st->st_ns * sizeof(float);

@@ -313,7 +313,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
     if (FORCE_ONLY || done) return;  // uniform per block
 
     const int ridx = a.brick_ridx[brick];
-    if (ridx >= 0) reaction_finish(a, Rloc, b, ridx, warp, lane, kWarps, red, &s_cnt, n);
+    if (ridx >= 0) {
+        // this path never defers its reaction: the view is the buffer as read
+        RunView rv;
+        rv.n = n;
+        rv.dn = 0;
+        rv.Q = 0.0;  // read from the buffer by the finishing block
+        rv.np = 0;
+        rv.Rp = 0.0;
+        rv.have = 0;
+        reaction_finish(a, Rloc, b, ridx, warp, lane, kWarps, red, &s_cnt, rv);
+    }
 }
 
 // ---------------------------------------------------------------- set-up
@@ -428,14 +438,17 @@ __global__ void k_reset(long long N, int B, const float *s0, const float *kappa,
     }
 }
 
-__global__ void k_reset_run(int B, int32_t *step, int32_t *done, int32_t *status, double *peak, int32_t *peak_step,
-                            unsigned *ticket, int step0) {
+__global__ void k_reset_run(int B, int32_t *step, int32_t *done, int32_t *pend, double *pk2, int32_t *ps2,
+                            int32_t *status, double *peak, int32_t *peak_step, unsigned *ticket, int step0) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    step[b] = step0;
-    step[B + b] = step0;
-    done[b] = 0;
-    done[B + b] = 0;
+    for (int p = 0; p < 2; ++p) {
+        step[p * B + b] = step0;
+        done[p * B + b] = 0;
+        pend[p * B + b] = 0;
+        pk2[p * B + b] = -INFINITY;
+        ps2[p * B + b] = -1;
+    }
     status[b] = 0;
     peak[b] = -INFINITY;
     peak_step[b] = -1;
@@ -636,6 +649,11 @@ static StepArgs make_args(const pd_state *st) {
     a.codes = st->codes;
     a.step = st->step;
     a.done = st->done;
+    a.pend = st->pend;
+    a.pk2 = st->pk2;
+    a.ps2 = st->ps2;
+    a.defer = 0;
+    a.pendable = st->stencil && st->st_defer;
     a.status = st->status;
     a.peak = st->peak;
     a.peak_step = st->peak_step;
@@ -738,6 +756,9 @@ static void free_state(pd_state *st) {
     cudaFree(st->coord);
     cudaFree(st->step);
     cudaFree(st->done);
+    cudaFree(st->pend);
+    cudaFree(st->pk2);
+    cudaFree(st->ps2);
     cudaFree(st->brick_ridx);
     cudaFree(st->status);
     cudaFree(st->peak);
@@ -927,6 +948,14 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
     st->nblk = (int)st->n_bricks;
     PD_TRY(dalloc(&st->step, 2 * B));
     PD_TRY(dalloc(&st->done, 2 * B));
+    PD_TRY(dalloc(&st->pend, 2 * B));
+    PD_TRY(dalloc(&st->pk2, 2 * B));
+    PD_TRY(dalloc(&st->ps2, 2 * B));
+    // a state steps only after pd_state_reset / pd_state_load; until then no
+    // reaction is pending and no sample counts as done
+    PD_CHECK_CUDA(cudaMemset(st->pend, 0, 2 * (size_t)B * sizeof(int32_t)));
+    PD_CHECK_CUDA(cudaMemset(st->done, 0, 2 * (size_t)B * sizeof(int32_t)));
+    PD_CHECK_CUDA(cudaMemset(st->step, 0, 2 * (size_t)B * sizeof(int32_t)));
     st->bk_par = 0;
     // reaction bricks: those holding a prescribed DOF, plus brick 0
     {
@@ -950,7 +979,7 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
     PD_TRY(dalloc(&st->status, B));
     PD_TRY(dalloc(&st->peak, B));
     PD_TRY(dalloc(&st->peak_step, B));
-    PD_TRY(dalloc(&st->partial, (size_t)B * st->nrb));
+    PD_TRY(dalloc(&st->partial, (size_t)2 * B * st->nrb));
     PD_TRY(dalloc(&st->ticket, B));
     PD_CHECK_CUDA(cudaHostAlloc((void **)&st->host_flag, 4 * sizeof(int32_t), cudaHostAllocMapped));
     PD_CHECK_CUDA(cudaHostGetDevicePointer((void **)&st->host_flag_dev, st->host_flag, 0));
@@ -1048,10 +1077,11 @@ extern "C" int pd_state_create_sched(const pd_grid *g, const int32_t *row_ptr, c
             return PD_ERR_ARG;
         }
         st->ns_req = sched ? sched->ns : 0;
-        if (st->ns_req < 0 || st->ns_req > 2) {
-            const int v = st->ns_req;
+        st->reduce_req = sched ? sched->reduce : 0;
+        if (st->ns_req < 0 || st->ns_req > 2 || st->reduce_req < 0 || st->reduce_req > 2) {
+            const int v = st->ns_req, w = st->reduce_req;
             delete st;
-            set_error("schedule ns = %d is not 0, 1 or 2", v);
+            set_error("schedule ns = %d / reduce = %d is not 0, 1 or 2", v, w);
             return PD_ERR_ARG;
         }
     }
@@ -1183,7 +1213,8 @@ extern "C" int pd_state_reset(pd_state *st, const float *s0, const float *kappa,
         cudaGraphExecDestroy(st->chunk_exec);
         st->chunk_exec = nullptr;
     }
-    k_reset_run<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->step, st->done, st->status, st->peak, st->peak_step,
+    k_reset_run<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->step, st->done, st->pend, st->pk2, st->ps2,
+                                                  st->status, st->peak, st->peak_step,
                                                   st->ticket, 0);
     PD_CHECK_LAUNCH();
     return PD_OK;
@@ -1196,7 +1227,8 @@ extern "C" int pd_state_load(pd_state *st, const double *u, const double *v, con
     cudaStream_t s = (cudaStream_t)stream;
     const long long NB = st->N * st->B;
     const bool f64 = st->mat.precision == PD_PREC_FP64;
-    k_reset_run<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->step, st->done, st->status, st->peak, st->peak_step,
+    k_reset_run<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->step, st->done, st->pend, st->pk2, st->ps2,
+                                                  st->status, st->peak, st->peak_step,
                                                   st->ticket, step);
     PD_CHECK_LAUNCH();
     if (f64)
@@ -1267,6 +1299,7 @@ extern "C" int pd_step(pd_state *st, int32_t n_steps, double *reaction, pd_strea
     for (int k = 0; k < n_steps; ++k) {
         a.k_local = k;
         a.par = st->bk_par;
+        a.defer = st->stencil && st->st_defer && k + 1 < n_steps;  // the last launch finishes every reaction
         PD_TRY(launch_step(st, a, false, (cudaStream_t)stream));
         st->bk_par ^= 1;
     }
@@ -1295,6 +1328,7 @@ extern "C" int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int
             int lrc = PD_OK;
             for (int q = 0; q < chunk && lrc == PD_OK; ++q) {
                 a.par = st->bk_par ^ (q & 1);  // the chunk is even, so it ends on the parity it starts from
+                a.defer = st->stencil && st->st_defer && q + 1 < chunk;  // the last launch finishes
                 lrc = launch_step(st, a, false, cs);
             }
             e = cudaStreamEndCapture(cs, &graph);
@@ -1396,6 +1430,7 @@ extern "C" int pd_run_to_peak_multi(pd_state *const *states, int32_t n_states, c
             a.max_steps = max_steps[i];
             for (int q = 0; q < chunk && lrc == PD_OK; ++q) {
                 a.par = st->bk_par ^ (q & 1);  // even chunk: ends on the parity it starts from
+                a.defer = st->stencil && st->st_defer && q + 1 < chunk;  // the last launch finishes
                 lrc = launch_step(st, a, false, ls);
             }
             if (i > 0) {

@@ -68,7 +68,7 @@ static std::vector<pd_schedule> candidates(const pd_grid *g, const pd_material *
         ++kept;
         const int by = b.second.first, bz = b.second.second;
         if (!stencil) {
-            out.push_back(pd_schedule{by, bz, 0, 0});
+            out.push_back(pd_schedule{by, bz, 0, 0, 0});
             continue;
         }
         const int wpb = by * bz / 2;
@@ -76,7 +76,7 @@ static std::vector<pd_schedule> candidates(const pd_grid *g, const pd_material *
         for (int ns = batch >= 2 ? 2 : 1; ns >= 1; --ns) {
             if ((size_t)14 * (by + 6) * (bz + zhalo) * 32 * ns > 200 * 1024) continue;
             for (int q = 1; q <= (g->nz == 1 ? 1 : 4); q *= 2)  // the planar stencil runs at q = 1
-                if (32 * wpb * q <= 512) out.push_back(pd_schedule{by, bz, q, ns});
+                if (32 * wpb * q <= 512) out.push_back(pd_schedule{by, bz, q, ns, 0});
         }
     }
     return out;
@@ -110,7 +110,7 @@ extern "C" int pd_autotune(const pd_grid *g, const int32_t *row_ptr, const int32
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    TuneEntry win{{0, 0, 0, 0}, INFINITY};
+    TuneEntry win{{0, 0, 0, 0, 0}, INFINITY};
     for (const pd_schedule &c : cand) {
         pd_state *st = nullptr;
         if (pd_state_create_sched(g, row_ptr, col, n_bonds, mat, bc, batch, &c, &st) != PD_OK) continue;

@@ -145,3 +145,32 @@ def test_paired_plane_samples_match_single_samples(pd):
     b = _full_run(pd, w, row, col, s0, (4, 1, 1, 2), n=300)
     for x, y in zip(a, b):
         assert torch.equal(x, y)
+
+
+def test_deferred_reaction_matches_reduction_in_the_launch(pd):
+    """Each step's reaction reduced in its own launch (reduce = 1) or by the
+    next launch (reduce = 2): the same per-step reactions, peaks, peak steps,
+    step counts and final states, bit for bit, including samples that stop at
+    different steps and a call that ends mid-run."""
+    w = W.small_beam_levels()[1]
+    row, col = pd.build_neighbours(w.grid)
+    s0 = _fields(w, 3)
+    s0[1] *= 0.8
+    for ns in (1, 2):
+        a = _full_run(pd, w, row, col, s0, (4, 2, 2, ns, 1), n=300)
+        b = _full_run(pd, w, row, col, s0, (4, 2, 2, ns, 2), n=300)
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+        (pk1, ps1, nd1), u1, v1, d1 = _full_run(pd, w, row, col, s0, (4, 2, 2, ns, 1))
+        (pk2, ps2, nd2), u2, v2, d2 = _full_run(pd, w, row, col, s0, (4, 2, 2, ns, 2))
+        assert len(set(nd1.tolist())) > 1
+        assert torch.equal(pk1, pk2) and torch.equal(ps1, ps2) and torch.equal(nd1, nd2)
+        assert torch.equal(u1, u2) and torch.equal(v1, v2) and torch.equal(d1, d2)
+    # steps split over several calls (each call's last launch reduces its own
+    # reaction) equal one call
+    st = pd.State(w.grid, row, col, w.mat, w.bc, batch=3, schedule=(4, 2, 2, 1, 2))
+    st.reset(s0)
+    R = torch.cat([st.step(k) for k in (1, 7, 64, 28)], dim=1)
+    st.close()
+    R1, _, _, _ = _full_run(pd, w, row, col, s0, (4, 2, 2, 1, 2), n=100)
+    assert torch.equal(R, R1)
