@@ -227,9 +227,10 @@ struct RunView {
 };
 
 // Read the bookkeeping of sample b, adding the pending reaction of the
-// previous launch (one warp, all lanes; every lane ends with the same view).
-// The bookkeeping and the partials are all requested at once (one L2 round
-// trip; the partials are read whether or not they are pending).
+// previous launch (one warp, all lanes; the view is complete in lane 0, the
+// only lane that runs the FP64 part). The bookkeeping and the partials are
+// all requested at once (one L2 round trip; the partials are read whether or
+// not they are pending).
 __device__ __forceinline__ RunView run_view(const StepArgs &a, int b, int lane) {
     const int i = a.par * a.B + b;
     const float2 *part = (const float2 *)a.partial + ((size_t)(1 - a.par) * a.B + b) * a.nblk;
@@ -249,9 +250,10 @@ __device__ __forceinline__ RunView run_view(const StepArgs &a, int b, int lane) 
         acc = df_add(acc, df{pv.x, pv.y});
     }
     acc = warp_sum_df(acc);
+    r.have = 1;
+    if (lane != 0) return r;
     const double R = a.V * ((double)acc.hi + (double)acc.lo);
     r.Rp = R;
-    r.have = 1;
     if (R > r.Q) {
         r.Q = R;
         r.np = r.n - 1;

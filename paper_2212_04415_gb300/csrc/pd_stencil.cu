@@ -319,6 +319,8 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
     __shared__ float s_pre[NS][4];  // U(n+1) and the prescribed velocity, double-float
     __shared__ unsigned s_cnt[NS];
     __shared__ RunView s_rv[NS];               // run bookkeeping per sample, with the pending reaction added
+    __shared__ int s_n[NS];                    // step index per sample
+    __shared__ int s_ridx;                     // the brick's index among the reaction bricks, or -1
     __shared__ float4 s_tab[2][NS * kRounds];  // per sub-lane sign
     __shared__ V s_kw2[kRounds];
     __shared__ int s_offb[2][kRounds];          // per sign: byte offset of the neighbour's staged record
@@ -328,22 +330,28 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
     const int ngrp = (a.B + NS - 1) / NS;
     const int grp = blockIdx.x % ngrp;
     const int brick = blockIdx.x / ngrp;
-    const int ridx = FORCE_ONLY ? -1 : a.brick_ridx[brick];  // requested early: read at the end
-    int bs[NS], ns[NS];
+    // per-block scalars that the end of the kernel needs live in shared
+    // memory or are recomputed there (fewer registers held across the bond loop)
+    const auto sample_of = [&](int s) {
+        const int b = NS * grp + s;
+        return b < a.B ? b : NS * grp;  // the second member of the last pair of an odd batch is a copy
+    };
+    int ns[NS];
     bool live[NS];
     bool any = false;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        const int b = NS * grp + s;
-        const bool real = b < a.B;  // the second member of the last pair of an odd batch is a copy
-        bs[s] = real ? b : NS * grp;
-        ns[s] = a.step[a.par * a.B + bs[s]];
-        const bool dn = FORCE_ONLY ? false : (a.done[a.par * a.B + bs[s]] != 0);
+        const bool real = NS * grp + s < a.B;
+        const int b = sample_of(s);
+        ns[s] = a.step[a.par * a.B + b];
+        const bool dn = FORCE_ONLY ? false : (a.done[a.par * a.B + b] != 0);
         live[s] = real && !dn;
-        if (!FORCE_ONLY && real && dn && brick == 0 && threadIdx.x == 0) carry_done(a, bs[s]);
+        if (!FORCE_ONLY && real && dn && brick == 0 && threadIdx.x == 0) carry_done(a, b);
         any = any || live[s];
     }
     if (!any) return;  // block-uniform
+    if (threadIdx.x == 0) s_ridx = FORCE_ONLY ? -1 : a.brick_ridx[brick];
+    if (threadIdx.x < NS) s_n[threadIdx.x] = ns[threadIdx.x];
     // the run view (with the previous launch's reaction, if it left it
     // pending) is built by warp s for sample s while the staging copies fly
     const auto build_views = [&]() {
@@ -352,7 +360,7 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
         for (int s = w; s < NS; s += nwarps) {
             RunView rv;
             if (live[s]) {
-                rv = run_view(a, bs[s], l);
+                rv = run_view(a, sample_of(s), l);
             } else {
                 rv.n = ns[s];
                 rv.dn = 1;
@@ -404,7 +412,7 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
     }
     // stage the brick and its halo (cells outside the grid read as zero)
     if constexpr (NS == 1) {
-        const float4 *rhi = (const float4 *)((ns[0] & 1) ? a.rec1 : a.rec0) + (size_t)bs[0] * a.N;
+        const float4 *rhi = (const float4 *)((ns[0] & 1) ? a.rec1 : a.rec0) + (size_t)sample_of(0) * a.N;
         const float4 *rlo = rhi + BN;
         for (int q = threadIdx.x; q < Wtot; q += blockDim.x) {  // asynchronous copies, all requested at once
             const int lx = q % kWx, ly = (q / kWx) % Wy, lz = q / (kWx * Wy);
@@ -418,8 +426,8 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
         build_views();
         cp_async_wait_all();
     } else {
-        const float4 *rh0 = (const float4 *)((ns[0] & 1) ? a.rec1 : a.rec0) + (size_t)bs[0] * a.N;
-        const float4 *rh1 = (const float4 *)((ns[1] & 1) ? a.rec1 : a.rec0) + (size_t)bs[1] * a.N;
+        const float4 *rh0 = (const float4 *)((ns[0] & 1) ? a.rec1 : a.rec0) + (size_t)sample_of(0) * a.N;
+        const float4 *rh1 = (const float4 *)((ns[NS - 1] & 1) ? a.rec1 : a.rec0) + (size_t)sample_of(NS - 1) * a.N;
         for (int q = threadIdx.x; q < Wtot; q += blockDim.x) {  // interleave the pair through registers
             const int lx = q % kWx, ly = (q / kWx) % Wy, lz = q / (kWx * Wy);
             const int gx = x0 - kHalo + lx, gy = y0 - kHalo + ly, gz = z0 - kHaloZ + lz;
@@ -448,7 +456,7 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const bool stop = live[s] && s_rv[s].dn;
-            if (stop && brick == 0 && threadIdx.x == 0) write_done(a, bs[s], s_rv[s]);
+            if (stop && brick == 0 && threadIdx.x == 0) write_done(a, sample_of(s), s_rv[s]);
             live[s] = live[s] && !stop;
             anyl = anyl || live[s];
         }
@@ -486,8 +494,8 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
         cx.nly = neg(me.ly);
         cx.nlz = neg(me.lz);
         cx.kap = me.lw;
-        cx.dm0 = (float *)a.dmg + (size_t)bs[0] * a.sell_len + ((size_t)brick * wpb + rp) * (kRounds * 32) + lane;
-        cx.dm1 = cx.dm0 + (size_t)(bs[NS - 1] - bs[0]) * a.sell_len;
+        cx.dm0 = (float *)a.dmg + (size_t)sample_of(0) * a.sell_len + ((size_t)brick * wpb + rp) * (kRounds * 32) + lane;
+        cx.dm1 = cx.dm0 + (size_t)(sample_of(NS - 1) - sample_of(0)) * a.sell_len;
         cx.w0 = live[0];
         cx.w1 = live[NS - 1];
         cx.lc = LawC{a.s_ratio_f, a.k_f, a.alpha_f, a.inv_1mek_f, a.inv_1pa_f, a.gfA_f};
@@ -540,7 +548,7 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             if (FORCE_ONLY ? (NS * grp + s >= a.B) : !live[s]) continue;
-            const size_t node = (size_t)bs[s] * a.N + ii;
+            const size_t node = (size_t)sample_of(s) * a.N + ii;
             for (int q = t; q < 3; q += 2) {
                 const float sq = el(q == 0 ? acc[0] : (q == 1 ? acc[1] : acc[2]), s);
                 const float cq = el(q == 0 ? acc[3] : (q == 1 ? acc[4] : acc[5]), s);
@@ -568,8 +576,8 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
                 }
                 vh[q] = v.hi;
                 vl[q] = v.lo;
-                float *oh = (float *)((float4 *)((ns[s] & 1) ? a.rec0 : a.rec1) + node);
-                float *ol = (float *)((float4 *)((ns[s] & 1) ? a.rec0 : a.rec1) + BN + node);
+                float *oh = (float *)((float4 *)((s_n[s] & 1) ? a.rec0 : a.rec1) + node);
+                float *ol = (float *)((float4 *)((s_n[s] & 1) ? a.rec0 : a.rec1) + BN + node);
                 oh[q] = u.hi;
                 ol[q] = u.lo;
             }
@@ -584,18 +592,19 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
         if (a.pendable) {
             rv = s_rv[s];
         } else {  // nothing is ever pending: the finishing block reads the peak itself
-            rv.n = ns[s];
+            rv.n = s_n[s];
             rv.dn = 0;
             rv.Q = 0.0;
             rv.np = 0;
             rv.Rp = 0.0;
             rv.have = 0;
         }
+        const int ridx = s_ridx;
         if (a.defer) {
-            if (brick == 0 && threadIdx.x == 0) write_deferred(a, bs[s], rv);
-            if (ridx >= 0) reaction_defer(a, Rloc[s], bs[s], ridx, warp, lane, nwarps, red[s]);
+            if (brick == 0 && threadIdx.x == 0) write_deferred(a, sample_of(s), rv);
+            if (ridx >= 0) reaction_defer(a, Rloc[s], sample_of(s), ridx, warp, lane, nwarps, red[s]);
         } else if (ridx >= 0) {
-            reaction_finish(a, Rloc[s], bs[s], ridx, warp, lane, nwarps, red[s], &s_cnt[s], rv);
+            reaction_finish(a, Rloc[s], sample_of(s), ridx, warp, lane, nwarps, red[s], &s_cnt[s], rv);
         }
     }
 }
