@@ -27,12 +27,14 @@
 // the gradient is deterministic. Arithmetic is FP64 throughout (the adjoint
 // is an offline gradient study; its states come from the state's own
 // forward path, FP64 or mixed). For mixed-path states the per-bond terms run
-// in FP32 (k_adj_bonds_f32) with FP64 sums.
+// in FP32 (k_adj_bonds_f32) on an FP32 trajectory (node records u, s0 and the
+// damage in CSR order), with the carried damage adjoint in double-float and
+// double-float warp sums added to FP64 node sums.
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
-#include "pd_internal.cuh"
+#include "pd_device.cuh"
 
 namespace pdi {
 
@@ -49,6 +51,12 @@ struct AdjArgs {
     int n_obs;
     const int32_t *obs;  // [n_obs] local step of each observation
     const double *w;     // [B][n_obs]
+    const int32_t *coord;  // packed grid coordinates per node
+    // FP32 constants of the mixed path, rounded on the host (the FP64 pipe is
+    // narrow on this part): c V, dx, and |xi| = sqrt(q) dx and its reciprocal
+    // for q = |k|^2 < 64
+    float cVf, dxf, s_ratio_f, gfA_f, k_f, alpha_f;
+    float L0q[64], iL0q[64];
 };
 
 // dD/ds and the total dD/ds0 = dD/ds0|sc + (dsc/ds0) dD/dsc on (s0, sc),
@@ -187,8 +195,8 @@ __global__ void __launch_bounds__(256) k_adj_bonds(const AdjArgs a, const double
 // and the carried damage adjoint in FP64. GB300 runs FP64 at a small fraction
 // of the FP32 rate, so this keeps the FP64 pipe to a few operations per bond.
 __device__ __forceinline__ void law_derivs_f(const AdjArgs &a, float s, float s0, float &dDds, float &dDds0) {
-    const float sc = a.gfA > 0.0 ? s0 + (float)a.gfA / s0 : (float)a.s_ratio * s0;
-    const float dsc = a.gfA > 0.0 ? 1.0f - (float)a.gfA / (s0 * s0) : (float)a.s_ratio;
+    const float sc = a.gfA_f > 0.f ? s0 + a.gfA_f / s0 : a.s_ratio_f * s0;
+    const float dsc = a.gfA_f > 0.f ? 1.0f - a.gfA_f / (s0 * s0) : a.s_ratio_f;
     dDds = 0.0f;
     dDds0 = 0.0f;
     if (s <= s0 || s >= sc) return;
@@ -198,7 +206,7 @@ __device__ __forceinline__ void law_derivs_f(const AdjArgs &a, float s, float s0
         dDds0 = -(sc / s - 1.0f) * sc / (w * w) + dsc * (-s0 * (1.0f - s0 / s) / (w * w));
         return;
     }
-    const float k = (float)a.k, al = (float)a.alpha;
+    const float k = a.k_f, al = a.alpha_f;
     const float t = (s - s0) / w;
     const float e = expf(-k * t), ek = 1.0f - expf(-k);
     const float beta = 1.0f - (1.0f - e) / ek + al * (1.0f - t);
@@ -213,74 +221,118 @@ __global__ void k_to_float(long long n, const double *x, float *y) {
     if (t < n) y[t] = (float)x[t];
 }
 
-__global__ void __launch_bounds__(256) k_adj_bonds_f32(const AdjArgs a, float cf, const float *u,
-                                                       const double *dprev, const double *dcur, const float *lF,
-                                                       double *ld, double *lun, double *g_s0, double *g_k) {
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (gw >= (long long)a.B * a.N) return;  // warp-uniform
-    const int b = (int)(gw / a.N);
-    const long long i = gw % a.N;
-    const int ix = (int)(i % a.nx), iy = (int)((i / a.nx) % a.ny), iz = (int)(i / ((long long)a.nx * a.ny));
-    const float *ub = u + (size_t)b * a.N * 3;
-    const float *lFb = lF + (size_t)b * a.N * 3;
-    const float *s0b = a.s0 + (size_t)b * a.N;
-    const float *kb = a.kappa ? a.kappa + (size_t)b * a.N : nullptr;
-    const size_t db = (size_t)b * a.nb;
-    const float dxf = (float)a.dx;
-    const float ui[3] = {ub[3 * i], ub[3 * i + 1], ub[3 * i + 2]};
-    const float li[3] = {lFb[3 * i], lFb[3 * i + 1], lFb[3 * i + 2]};
-    const float s0i = s0b[i], ki = kb ? kb[i] : 1.0f;
-    float acc[3] = {0.f, 0.f, 0.f}, gs = 0.f, gk = 0.f;
-    for (int q = a.row_ptr[i] + lane; q < a.row_ptr[i + 1]; q += 32) {
-        const long long j = a.col[q];
-        const int jx = (int)(j % a.nx), jy = (int)((j / a.nx) % a.ny), jz = (int)(j / ((long long)a.nx * a.ny));
-        const float xi[3] = {(float)(jx - ix) * dxf, (float)(jy - iy) * dxf, (float)(jz - iz) * dxf};
-        float y[3], dl[3], L0 = 0.f, L = 0.f, ydl = 0.f, xe = 0.f, ee = 0.f;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float eta = ub[3 * j + c] - ui[c];
-            y[c] = xi[c] + eta;
-            dl[c] = lFb[3 * j + c] - li[c];
-            L0 += xi[c] * xi[c];
-            xe += xi[c] * eta;
-            ee += eta * eta;
-            ydl += y[c] * dl[c];
-        }
-        L0 = sqrtf(L0);
-        L = sqrtf(L0 * L0 + 2.f * xe + ee);
-        const float s = (2.f * xe + ee) / (L0 * (L + L0)), h = s / L;  // cancellation-free stretch
-        const float s0 = 0.5f * (s0i + s0b[j]);
-        const float cij = kb ? cf * 0.5f * (ki + kb[j]) : cf;
-        const double dp = dprev[db + q], dc = dcur[db + q];
-        const bool active = dc > dp;
-        const float dcf = (float)dc;
-        const double lamd = ld[db + q] + (double)(cij * (float)a.V * h * ydl);
-        float dDds = 0.f, dDds0 = 0.f;
-        if (active) law_derivs_f(a, s, s0, dDds, dDds0);
-        const float lamdf = (float)lamd;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float dh = y[c] / (L * L * L0) - s * y[c] / (L * L * L);
-            float lamy = -cij * (float)a.V * (1.0f - dcf) * (ydl * dh + h * dl[c]);
-            if (active) lamy += lamdf * dDds * y[c] / (L * L0);
-            acc[c] -= lamy;
-        }
-        if (active) gs += 0.5f * lamdf * dDds0;
-        gk += 0.5f * cf * (-(float)a.V * (1.0f - dcf) * h * ydl);
-        ld[db + q] = active ? 0.0 : lamd;
+// Node records of the mixed path at one step: (u, s0) with u = u_hi + u_lo
+// rounded to FP32, from the state's double-float gather records.
+__global__ void k_rec_to_u4(long long BN, const float4 *rec, float4 *u4) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= BN) return;
+    const float4 h = rec[t], l = rec[BN + t];
+    u4[t] = make_float4(h.x + l.x, h.y + l.y, h.z + l.z, h.w);
+}
+
+// (lamF, kappa) per node in FP32 for the mixed path's bond adjoint.
+__global__ void k_lF_to_f4(long long BN, const double *lF, const float *kappa, float4 *lF4) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= BN) return;
+    lF4[t] = make_float4((float)lF[3 * t], (float)lF[3 * t + 1], (float)lF[3 * t + 2], kappa ? kappa[t] : 1.0f);
+}
+
+__device__ __forceinline__ float rsqrt_ap(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_ap(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Bond adjoint of one step for mixed-path states: one warp per (sample,
+// node), lanes over the node's CSR bonds, grid-stride over the nodes. Per
+// bond: y = xi + eta, s = eta.(y + xi) / (|xi| (|y| + |xi|)), h = s / |y|,
+// dh/dy = y (1/|xi| - s/|y|) / |y|^2 (|y| from the approximate reciprocal
+// square root); the damage adjoint carried in double-float; per-lane FP32
+// partials reduced along a fixed double-float xor tree and added to the FP64
+// node sums by lane 0.
+__global__ void __launch_bounds__(256) k_adj_bonds_f32(const AdjArgs a, const float4 *u4, const float *dprev,
+                                                       const float *dcur, const float4 *lF4, float2 *ld,
+                                                       double *lun, double *g_s0, double *g_k) {
+    __shared__ float s_L0[64], s_iL0[64];
+    if (threadIdx.x < 64) {
+        s_L0[threadIdx.x] = a.L0q[threadIdx.x];
+        s_iL0[threadIdx.x] = a.iL0q[threadIdx.x];
     }
-    double accd[3];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const float cV = a.cVf, dxf = a.dxf;
+    for (long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < (long long)a.B * a.N;
+         gw += nw) {  // warp-uniform
+        const int b = (int)(gw / a.N);
+        const int i = (int)(gw % a.N);
+        const float4 *ub = u4 + (size_t)b * a.N;
+        const float4 *lb4 = lF4 + (size_t)b * a.N;
+        const size_t db = (size_t)b * a.nb;
+        const int ci = a.coord[i];
+        const float4 me = ub[i], ml = lb4[i];
+        float acc[3] = {0.f, 0.f, 0.f}, gs = 0.f, gk = 0.f;
+        for (int q = a.row_ptr[i] + lane; q < a.row_ptr[i + 1]; q += 32) {
+            const int j = a.col[q];
+            const int cj = a.coord[j];
+            const int kx = (cj & 2047) - (ci & 2047), ky = ((cj >> 11) & 2047) - ((ci >> 11) & 2047),
+                      kz = (cj >> 22) - (ci >> 22);
+            const int q2 = kx * kx + ky * ky + kz * kz;
+            const float L0 = q2 < 64 ? s_L0[q2] : sqrtf((float)q2) * dxf;
+            const float iL0 = q2 < 64 ? s_iL0[q2] : 1.0f / L0;
+            const float xi[3] = {(float)kx * dxf, (float)ky * dxf, (float)kz * dxf};
+            const float4 nj = ub[j], lj = lb4[j];
+            const float eta[3] = {nj.x - me.x, nj.y - me.y, nj.z - me.z};
+            const float dl[3] = {lj.x - ml.x, lj.y - ml.y, lj.z - ml.z};
+            float y[3], y2 = 0.f, num = 0.f, ydl = 0.f;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) accd[c] = warp_sum_fixed((double)acc[c]);
-    const double gsd = warp_sum_fixed((double)gs), gkd = warp_sum_fixed((double)gk);
-    if (lane == 0) {
-        double *lb = lun + (size_t)b * a.N * 3 + 3 * i;
-        lb[0] += accd[0];
-        lb[1] += accd[1];
-        lb[2] += accd[2];
-        g_s0[(size_t)b * a.N + i] += gsd;
-        if (g_k) g_k[(size_t)b * a.N + i] += gkd;
+            for (int c = 0; c < 3; ++c) {
+                y[c] = xi[c] + eta[c];
+                y2 = fmaf(y[c], y[c], y2);
+                num = fmaf(eta[c], y[c] + xi[c], num);
+                ydl = fmaf(y[c], dl[c], ydl);
+            }
+            const float rL = rsqrt_ap(y2);
+            const float L = y2 * rL;
+            const float s = num * rcp_ap(fmaf(L0, L, L0 * L0));
+            const float h = s * rL;
+            const float s0 = 0.5f * (me.w + nj.w);
+            const float cijV = a.kappa ? cV * 0.5f * (ml.w + lj.w) : cV;
+            const float dp = dprev[db + q], dc = dcur[db + q];
+            const bool active = dc > dp;
+            const float2 l0 = ld[db + q];
+            const df lamd = df_add(df{l0.x, l0.y}, df{cijV * h * ydl, 0.f});
+            float dDds = 0.f, dDds0 = 0.f;
+            if (active) law_derivs_f(a, s, s0, dDds, dDds0);
+            const float lamdf = lamd.hi + lamd.lo;
+            const float om = 1.0f - dc;
+            const float dhk = rL * rL * (iL0 - s * rL);
+            const float act = active ? lamdf * dDds * rL * iL0 : 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float lamy = -cijV * om * (ydl * dhk * y[c] + h * dl[c]) + act * y[c];
+                acc[c] -= lamy;
+            }
+            if (active) gs += 0.5f * lamdf * dDds0;
+            gk += 0.5f * cV * (-om * h * ydl);
+            ld[db + q] = active ? make_float2(0.f, 0.f) : make_float2(lamd.hi, lamd.lo);
+        }
+        df t[5] = {{acc[0], 0.f}, {acc[1], 0.f}, {acc[2], 0.f}, {gs, 0.f}, {gk, 0.f}};
+#pragma unroll
+        for (int v = 0; v < 5; ++v) t[v] = warp_sum_df(t[v]);
+        if (lane == 0) {
+            double *lb = lun + (size_t)b * a.N * 3 + 3 * (size_t)i;
+            lb[0] += (double)t[0].hi + (double)t[0].lo;
+            lb[1] += (double)t[1].hi + (double)t[1].lo;
+            lb[2] += (double)t[2].hi + (double)t[2].lo;
+            g_s0[(size_t)b * a.N + i] += (double)t[3].hi + (double)t[3].lo;
+            if (g_k) g_k[(size_t)b * a.N + i] += (double)t[4].hi + (double)t[4].lo;
+        }
     }
 }
 
@@ -388,23 +440,40 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
     PD_CHECK_CUDA(cudaMemcpy(&n0, st->step + st->bk_par * B, sizeof(int32_t), cudaMemcpyDeviceToHost));
 
     DevBuf<double> ck_u, ck_v, ck_d, tr_u, tr_d, lu, lun, lv, lF, ld, rbuf;
-    DevBuf<float> u32, lF32;  // FP32 copies for the mixed path's bond adjoint
+    // the mixed path's FP32 trajectory: node records (u, s0) per step, damage
+    // in CSR order per step (+ the last), (lamF, kappa) per node, the damage
+    // adjoint in double-float, and the CSR slot of every bond in the state's
+    // stencil damage array
+    DevBuf<float4> tr_u4, lF4;
+    DevBuf<float> tr_d32;
+    DevBuf<float2> ld2;
+    DevBuf<int32_t> slot;
     const bool f32 = st->mat.precision == PD_PREC_MIXED;
+    const long long BN = (long long)B * N;
     DevBuf<int32_t> obs;
     PD_TRY(dalloc(&ck_u.p, (size_t)(nseg + 1) * U3));  // checkpoints + the final state
     PD_TRY(dalloc(&ck_v.p, (size_t)(nseg + 1) * U3));
     PD_TRY(dalloc(&ck_d.p, (size_t)(nseg + 1) * D1));
-    PD_TRY(dalloc(&tr_u.p, (size_t)k * U3));
-    PD_TRY(dalloc(&tr_d.p, (size_t)(k + 1) * D1));
     PD_TRY(dalloc(&lu.p, U3));
     PD_TRY(dalloc(&lun.p, U3));
     PD_TRY(dalloc(&lv.p, U3));
     PD_TRY(dalloc(&lF.p, U3));
-    PD_TRY(dalloc(&ld.p, D1));
     PD_TRY(dalloc(&rbuf.p, (size_t)B * k));
     if (f32) {
-        PD_TRY(dalloc(&u32.p, U3));
-        PD_TRY(dalloc(&lF32.p, U3));
+        PD_TRY(dalloc(&tr_u4.p, (size_t)k * BN));
+        PD_TRY(dalloc(&tr_d32.p, (size_t)(k + 1) * D1));
+        PD_TRY(dalloc(&lF4.p, BN));
+        PD_TRY(dalloc(&ld2.p, D1));
+        if (st->stencil) {
+            PD_TRY(dalloc(&slot.p, nb));
+            PD_TRY(stencil_slot_table(st, slot.p, s));
+        } else {
+            PD_TRY(dalloc(&tr_d.p, D1));  // staging for the generic layout's FP64 store
+        }
+    } else {
+        PD_TRY(dalloc(&tr_u.p, (size_t)k * U3));
+        PD_TRY(dalloc(&tr_d.p, (size_t)(k + 1) * D1));
+        PD_TRY(dalloc(&ld.p, D1));
     }
     PD_TRY(dalloc(&obs.p, std::max(n_obs, 1)));
     if (n_obs) PD_CHECK_CUDA(cudaMemcpyAsync(obs.p, obs_steps, n_obs * sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -449,32 +518,72 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
     a.n_obs = n_obs;
     a.obs = obs.p;
     a.w = dJ_dR;
+    a.coord = st->coord;
+    a.cVf = (float)(st->c * st->V);
+    a.dxf = (float)st->g.dx;
+    a.s_ratio_f = (float)st->mat.s_ratio;
+    a.gfA_f = (float)st->gfA;
+    a.k_f = (float)st->mat.k;
+    a.alpha_f = (float)st->mat.alpha;
+    for (int q = 0; q < 64; ++q) {
+        const double L0 = std::sqrt((double)q) * st->g.dx;
+        a.L0q[q] = (float)L0;
+        a.iL0q[q] = q ? (float)(1.0 / L0) : 0.f;
+    }
     PD_CHECK_CUDA(cudaMemsetAsync(lu.p, 0, U3 * sizeof(double), s));
     PD_CHECK_CUDA(cudaMemsetAsync(lv.p, 0, U3 * sizeof(double), s));
-    PD_CHECK_CUDA(cudaMemsetAsync(ld.p, 0, D1 * sizeof(double), s));
+    if (f32)
+        PD_CHECK_CUDA(cudaMemsetAsync(ld2.p, 0, D1 * sizeof(float2), s));
+    else
+        PD_CHECK_CUDA(cudaMemsetAsync(ld.p, 0, D1 * sizeof(double), s));
     PD_CHECK_CUDA(cudaMemsetAsync(grad_s0, 0, (size_t)B * N * sizeof(double), s));
     if (grad_kappa) PD_CHECK_CUDA(cudaMemsetAsync(grad_kappa, 0, (size_t)B * N * sizeof(double), s));
     const unsigned nblk_dof = (unsigned)((U3 + 255) / 256);
     const unsigned nblk_bond = (unsigned)(((long long)B * N * 32 + 255) / 256);
+    // the mixed bond adjoint strides over the nodes with a few blocks per SM
+    int sms = 0, dev = 0;
+    PD_CHECK_CUDA(cudaGetDevice(&dev));
+    PD_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned nblk_bond32 = (unsigned)std::min<long long>(nblk_bond, 8ll * sms);
+    const unsigned nblk_node = (unsigned)((BN + 255) / 256);
+    // FP32 trajectory of the mixed path at the state's current step n: the
+    // gather records of parity n and the damage in CSR order
+    auto snap_f32 = [&](int n, float4 *u4, float *d32) -> int {
+        if (u4) {
+            k_rec_to_u4<<<nblk_node, 256, 0, s>>>(BN, (const float4 *)st->rec[n & 1], u4);
+            PD_CHECK_LAUNCH();
+        }
+        if (st->stencil) return stencil_gather_damage_f32(st, slot.p, d32, s);
+        PD_TRY(pd_state_store(st, nullptr, nullptr, tr_d.p, stream));
+        k_to_float<<<(unsigned)((D1 + 255) / 256), 256, 0, s>>>(D1, tr_d.p, d32);
+        PD_CHECK_LAUNCH();
+        return PD_OK;
+    };
     double *plu = lu.p, *plun = lun.p;
     for (int g = nseg - 1; g >= 0; --g) {
         const int start = g * k, len = std::min(k, n_steps - start);
         PD_TRY(pd_state_load(st, ck_u.p + (size_t)g * U3, ck_v.p + (size_t)g * U3, ck_d.p + (size_t)g * D1,
                              n0 + start, stream));
         for (int m = 0; m < len; ++m) {
-            PD_TRY(pd_state_store(st, tr_u.p + (size_t)m * U3, nullptr, tr_d.p + (size_t)m * D1, stream));
+            if (f32)
+                PD_TRY(snap_f32(n0 + start + m, tr_u4.p + (size_t)m * BN, tr_d32.p + (size_t)m * D1));
+            else
+                PD_TRY(pd_state_store(st, tr_u.p + (size_t)m * U3, nullptr, tr_d.p + (size_t)m * D1, stream));
             PD_TRY(pd_step(st, 1, nullptr, stream));
         }
-        PD_TRY(pd_state_store(st, nullptr, nullptr, tr_d.p + (size_t)len * D1, stream));
+        if (f32)
+            PD_TRY(snap_f32(n0 + start + len, nullptr, tr_d32.p + (size_t)len * D1));
+        else
+            PD_TRY(pd_state_store(st, nullptr, nullptr, tr_d.p + (size_t)len * D1, stream));
         for (int m = len - 1; m >= 0; --m) {
             k_adj_nodes<<<nblk_dof, 256, 0, s>>>(a, start + m, plu, lv.p, lF.p, plun);
             PD_CHECK_LAUNCH();
             if (f32) {
-                k_to_float<<<nblk_dof, 256, 0, s>>>(U3, tr_u.p + (size_t)m * U3, u32.p);
-                k_to_float<<<nblk_dof, 256, 0, s>>>(U3, lF.p, lF32.p);
-                k_adj_bonds_f32<<<nblk_bond, 256, 0, s>>>(a, (float)a.c, u32.p,
-                                                          tr_d.p + (size_t)m * D1, tr_d.p + (size_t)(m + 1) * D1,
-                                                          lF32.p, ld.p, plun, grad_s0, grad_kappa);
+                k_lF_to_f4<<<nblk_node, 256, 0, s>>>(BN, lF.p, kappa, lF4.p);
+                PD_CHECK_LAUNCH();
+                k_adj_bonds_f32<<<nblk_bond32, 256, 0, s>>>(a, tr_u4.p + (size_t)m * BN, tr_d32.p + (size_t)m * D1,
+                                                            tr_d32.p + (size_t)(m + 1) * D1, lF4.p, ld2.p, plun,
+                                                            grad_s0, grad_kappa);
             } else {
                 k_adj_bonds<<<nblk_bond, 256, 0, s>>>(a, tr_u.p + (size_t)m * U3, tr_d.p + (size_t)m * D1,
                                                       tr_d.p + (size_t)(m + 1) * D1, lF.p, ld.p, plun, grad_s0,

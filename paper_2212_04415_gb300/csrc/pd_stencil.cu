@@ -675,6 +675,28 @@ __global__ void k_stencil_map(const int32_t *row_ptr, const int32_t *col, const 
     }
 }
 
+// Slot, in one sample's damage array, of every CSR bond (every CSR neighbour
+// is a stencil offset: checked when the template is built).
+__global__ void k_stencil_slots(const int32_t *row_ptr, const int32_t *col, const int32_t *coord, long long N,
+                                int nx, int ny, int BY, int BZ, int nbx, int nby, int wpb, int rounds,
+                                const int16_t *box, int32_t *slot) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+        const int code = code_of(coord, (int)i, col[p], box);
+        slot[p] = code < 0 ? 0 : (int32_t)slot_of((int)i, code, nx, ny, BY, BZ, nbx, nby, wpb, rounds);
+    }
+}
+
+// Damage of every sample in CSR order, FP32: out[b][p] = dmg[b][slot[p]].
+__global__ void k_stencil_gather_f32(long long nb, long long len, const int32_t *slot, const float *dmg,
+                                     float *out) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nb) return;
+    const int b = blockIdx.y;
+    out[(size_t)b * nb + p] = dmg[(size_t)b * len + slot[p]];
+}
+
 typedef void (*StencilKernel)(const StepArgs);
 
 template <int DIM, int NS, int Q>
@@ -832,6 +854,23 @@ int stencil_map_damage(const pd_state *st, double *csr, bool to_state, cudaStrea
                                                            st->g.nx, st->g.ny, st->by, st->bz, st->nbx, st->nby,
                                                            st->st_wpb, st->st_dim == 3 ? Sten<3>::kRounds : Sten<2>::kRounds,
                                                           st->st_len, st->st_box, (float *)st->dmg, csr);
+    PD_CHECK_LAUNCH();
+    return PD_OK;
+}
+
+int stencil_slot_table(const pd_state *st, int32_t *slot, cudaStream_t s) {
+    k_stencil_slots<<<blocks_of(st->N), 256, 0, s>>>(st->row_ptr, st->col_csr, st->coord, st->N, st->g.nx, st->g.ny,
+                                                     st->by, st->bz, st->nbx, st->nby, st->st_wpb,
+                                                     st->st_dim == 3 ? Sten<3>::kRounds : Sten<2>::kRounds,
+                                                     st->st_box, slot);
+    PD_CHECK_LAUNCH();
+    return PD_OK;
+}
+
+int stencil_gather_damage_f32(const pd_state *st, const int32_t *slot, float *out, cudaStream_t s) {
+    PD_REQUIRE(st->B <= 65535, "at most 65535 samples per state");
+    const dim3 grid((unsigned)((st->nb + 255) / 256), (unsigned)st->B);
+    k_stencil_gather_f32<<<grid, 256, 0, s>>>(st->nb, st->st_len, slot, (const float *)st->dmg, out);
     PD_CHECK_LAUNCH();
     return PD_OK;
 }
