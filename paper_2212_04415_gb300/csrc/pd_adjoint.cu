@@ -43,6 +43,7 @@ struct AdjArgs {
     long long N, nb;
     int nx, ny;
     double dx, c, V, dt, rho, a, b;
+    double dt_rb, a_b;  // dt / (rho b) and a / b (no FP64 division per DOF)
     int law;
     double s_ratio, k, alpha, gfA;
     const int32_t *row_ptr, *col;
@@ -91,15 +92,15 @@ __device__ __forceinline__ void law_derivs(const AdjArgs &a, double s, double s0
 // Integrator adjoint of local step `ls`: lamF, lamv (in place) and the carried
 // part of lamu^n (lun) from lamu^{n+1} (lu).
 __global__ void k_adj_nodes(const AdjArgs a, int ls, const double *lu, double *lv, double *lF, double *lun) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)a.B * a.N * 3) return;
-    const int b = (int)(t / (a.N * 3));
-    const long long q = t % (a.N * 3);
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;  // DOF of sample blockIdx.y
+    if (q >= a.N * 3) return;
+    const int b = blockIdx.y;
+    const long long t = (long long)b * a.N * 3 + q;
     const uint8_t code = a.codes[q];
     if (code == 0) {
         const double lvp = lv[t] + a.dt * lu[t];
-        lF[t] = a.dt * lvp / (a.rho * a.b);
-        lv[t] = a.a * lvp / a.b;
+        lF[t] = a.dt_rb * lvp;
+        lv[t] = a.a_b * lvp;
         lun[t] = lu[t];
     } else if (code == 1) {
         lF[t] = 0.0;
@@ -248,14 +249,65 @@ __device__ __forceinline__ float rcp_ap(float x) {
     return r;
 }
 
-// Bond adjoint of one step for mixed-path states: one warp per (sample,
-// node), lanes over the node's CSR bonds, grid-stride over the nodes. Per
-// bond: y = xi + eta, s = eta.(y + xi) / (|xi| (|y| + |xi|)), h = s / |y|,
-// dh/dy = y (1/|xi| - s/|y|) / |y|^2 (|y| from the approximate reciprocal
-// square root); the damage adjoint carried in double-float; per-lane FP32
-// partials reduced along a fixed double-float xor tree and added to the FP64
-// node sums by lane 0.
-__global__ void __launch_bounds__(256) k_adj_bonds_f32(const AdjArgs a, const float4 *u4, const float *dprev,
+// Sliced ELL layout of the CSR bonds for the mixed path's bond adjoint:
+// slices of 32 consecutive nodes, slot-major inside a slice (slot p of node
+// 32 sl + lane at off[sl] + 32 p + lane), rows padded to the slice's longest.
+// Rows are sorted, so at a slot the interior nodes of a slice take the same
+// stencil offset and their neighbour gathers are contiguous.
+__global__ void k_sell_fill(long long N, const int32_t *row_ptr, const int32_t *col, const long long *off,
+                            int32_t *q_of, int32_t *j_of) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const long long base = off[i >> 5] + (i & 31);
+    for (int q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
+        const long long x = base + 32ll * (q - row_ptr[i]);
+        q_of[x] = q;
+        j_of[x] = col[q];
+    }
+}
+
+// Damage of every sample in sliced-ELL order from the CSR-order slot table
+// of the stencil damage array (padding slots read slot 0 and are unused).
+__global__ void k_sell_slots(long long len, const int32_t *q_of, const int32_t *slot, int32_t *dslot) {
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= len) return;
+    const int q = q_of[x];
+    dslot[x] = q >= 0 ? slot[q] : 0;
+}
+
+__global__ void k_gather_dmg(long long len, long long dlen, const int32_t *dslot, const float *dmg, float *out) {
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= len) return;
+    const int b = blockIdx.y;
+    out[(size_t)b * len + x] = dmg[(size_t)b * dlen + dslot[x]];
+}
+
+// The same from an FP64 CSR-order array (the generic layout's store).
+__global__ void k_gather_csr(long long len, long long nb, const int32_t *q_of, const double *csr, float *out) {
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= len) return;
+    const int b = blockIdx.y;
+    const int q = q_of[x];
+    out[(size_t)b * len + x] = q >= 0 ? (float)csr[(size_t)b * nb + q] : 0.f;
+}
+
+// s + x accumulated with the rounding error carried in c (Knuth's TwoSum).
+__device__ __forceinline__ void fold(float &s, float &c, float x) {
+    const float t = s + x;
+    const float z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+}
+
+// Bond adjoint of one step for mixed-path states: one thread per (sample,
+// node), over its sliced-ELL row. Per bond: y = xi + eta, s = eta.(y + xi) /
+// (|xi| (|y| + |xi|)), h = s / |y|, dh/dy = y (1/|xi| - s/|y|) / |y|^2 (|y|
+// from the approximate reciprocal square root); the damage adjoint carried
+// in double-float. The node's terms are summed in FP32 over 8 slots at a
+// time and folded into compensated sums (fixed order), then added to the
+// FP64 node sums.
+__global__ void __launch_bounds__(256) k_adj_bonds_f32(const AdjArgs a, long long sl_len, const long long *off,
+                                                       const int32_t *j_of, const float4 *u4, const float *dprev,
                                                        const float *dcur, const float4 *lF4, float2 *ld,
                                                        double *lun, double *g_s0, double *g_k) {
     __shared__ float s_L0[64], s_iL0[64];
@@ -264,21 +316,22 @@ __global__ void __launch_bounds__(256) k_adj_bonds_f32(const AdjArgs a, const fl
         s_iL0[threadIdx.x] = a.iL0q[threadIdx.x];
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.y;
+    if (i >= a.N) return;
     const float cV = a.cVf, dxf = a.dxf;
-    for (long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < (long long)a.B * a.N;
-         gw += nw) {  // warp-uniform
-        const int b = (int)(gw / a.N);
-        const int i = (int)(gw % a.N);
-        const float4 *ub = u4 + (size_t)b * a.N;
-        const float4 *lb4 = lF4 + (size_t)b * a.N;
-        const size_t db = (size_t)b * a.nb;
-        const int ci = a.coord[i];
-        const float4 me = ub[i], ml = lb4[i];
-        float acc[3] = {0.f, 0.f, 0.f}, gs = 0.f, gk = 0.f;
-        for (int q = a.row_ptr[i] + lane; q < a.row_ptr[i + 1]; q += 32) {
-            const int j = a.col[q];
+    const float4 *ub = u4 + (size_t)b * a.N;
+    const float4 *lb4 = lF4 + (size_t)b * a.N;
+    const size_t db = (size_t)b * sl_len;
+    const int ci = a.coord[i];
+    const float4 me = ub[i], ml = lb4[i];
+    const long long base = off[i >> 5] + (i & 31);
+    const int W = (int)((off[(i >> 5) + 1] - off[i >> 5]) >> 5);  // slots of the slice
+    float S[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Cc[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, P[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int p = 0; p < W; ++p) {
+        const long long x = base + 32ll * p;
+        const int j = j_of[x];
+        if (j >= 0) {
             const int cj = a.coord[j];
             const int kx = (cj & 2047) - (ci & 2047), ky = ((cj >> 11) & 2047) - ((ci >> 11) & 2047),
                       kz = (cj >> 22) - (ci >> 22);
@@ -303,9 +356,9 @@ __global__ void __launch_bounds__(256) k_adj_bonds_f32(const AdjArgs a, const fl
             const float h = s * rL;
             const float s0 = 0.5f * (me.w + nj.w);
             const float cijV = a.kappa ? cV * 0.5f * (ml.w + lj.w) : cV;
-            const float dp = dprev[db + q], dc = dcur[db + q];
+            const float dp = dprev[db + x], dc = dcur[db + x];
             const bool active = dc > dp;
-            const float2 l0 = ld[db + q];
+            const float2 l0 = ld[db + x];
             const df lamd = df_add(df{l0.x, l0.y}, df{cijV * h * ydl, 0.f});
             float dDds = 0.f, dDds0 = 0.f;
             if (active) law_derivs_f(a, s, s0, dDds, dDds0);
@@ -314,26 +367,25 @@ __global__ void __launch_bounds__(256) k_adj_bonds_f32(const AdjArgs a, const fl
             const float dhk = rL * rL * (iL0 - s * rL);
             const float act = active ? lamdf * dDds * rL * iL0 : 0.f;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float lamy = -cijV * om * (ydl * dhk * y[c] + h * dl[c]) + act * y[c];
-                acc[c] -= lamy;
-            }
-            if (active) gs += 0.5f * lamdf * dDds0;
-            gk += 0.5f * cV * (-om * h * ydl);
-            ld[db + q] = active ? make_float2(0.f, 0.f) : make_float2(lamd.hi, lamd.lo);
+            for (int c = 0; c < 3; ++c) P[c] += cijV * om * (ydl * dhk * y[c] + h * dl[c]) - act * y[c];
+            if (active) P[3] += 0.5f * lamdf * dDds0;
+            P[4] += 0.5f * cV * (-om * h * ydl);
+            ld[db + x] = active ? make_float2(0.f, 0.f) : make_float2(lamd.hi, lamd.lo);
         }
-        df t[5] = {{acc[0], 0.f}, {acc[1], 0.f}, {acc[2], 0.f}, {gs, 0.f}, {gk, 0.f}};
+        if ((p & 7) == 7 || p + 1 == W) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) t[v] = warp_sum_df(t[v]);
-        if (lane == 0) {
-            double *lb = lun + (size_t)b * a.N * 3 + 3 * (size_t)i;
-            lb[0] += (double)t[0].hi + (double)t[0].lo;
-            lb[1] += (double)t[1].hi + (double)t[1].lo;
-            lb[2] += (double)t[2].hi + (double)t[2].lo;
-            g_s0[(size_t)b * a.N + i] += (double)t[3].hi + (double)t[3].lo;
-            if (g_k) g_k[(size_t)b * a.N + i] += (double)t[4].hi + (double)t[4].lo;
+            for (int v = 0; v < 5; ++v) {
+                fold(S[v], Cc[v], P[v]);
+                P[v] = 0.f;
+            }
         }
     }
+    double *lb = lun + (size_t)b * a.N * 3 + 3 * (size_t)i;
+    lb[0] += (double)S[0] + (double)Cc[0];
+    lb[1] += (double)S[1] + (double)Cc[1];
+    lb[2] += (double)S[2] + (double)Cc[2];
+    g_s0[(size_t)b * a.N + i] += (double)S[3] + (double)Cc[3];
+    if (g_k) g_k[(size_t)b * a.N + i] += (double)S[4] + (double)Cc[4];
 }
 
 // R_obs[b][o] = reaction[b][m] for the observations inside a segment.
@@ -447,7 +499,9 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
     DevBuf<float4> tr_u4, lF4;
     DevBuf<float> tr_d32;
     DevBuf<float2> ld2;
-    DevBuf<int32_t> slot;
+    DevBuf<int32_t> slot, q_of, j_of, dslot;
+    DevBuf<long long> sl_off;
+    long long SL = 0;  // sliced-ELL slots per sample
     const bool f32 = st->mat.precision == PD_PREC_MIXED;
     const long long BN = (long long)B * N;
     DevBuf<int32_t> obs;
@@ -460,13 +514,35 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
     PD_TRY(dalloc(&lF.p, U3));
     PD_TRY(dalloc(&rbuf.p, (size_t)B * k));
     if (f32) {
+        // sliced ELL of the CSR rows (slice widths on the host)
+        std::vector<int32_t> hrow(N + 1);
+        PD_CHECK_CUDA(cudaMemcpy(hrow.data(), st->row_ptr, (N + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        const long long nsl = (N + 31) / 32;
+        std::vector<long long> hoff(nsl + 1, 0);
+        for (long long sl = 0; sl < nsl; ++sl) {
+            int w = 0;
+            for (long long i = 32 * sl; i < std::min(N, 32 * sl + 32); ++i) w = std::max(w, hrow[i + 1] - hrow[i]);
+            hoff[sl + 1] = hoff[sl] + 32ll * w;
+        }
+        SL = std::max(hoff[nsl], 1ll);
+        PD_TRY(dalloc(&sl_off.p, nsl + 1));
+        PD_CHECK_CUDA(cudaMemcpy(sl_off.p, hoff.data(), (nsl + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+        PD_TRY(dalloc(&q_of.p, SL));
+        PD_TRY(dalloc(&j_of.p, SL));
+        PD_CHECK_CUDA(cudaMemsetAsync(q_of.p, 0xff, SL * sizeof(int32_t), s));
+        PD_CHECK_CUDA(cudaMemsetAsync(j_of.p, 0xff, SL * sizeof(int32_t), s));
+        k_sell_fill<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, st->row_ptr, st->col_csr, sl_off.p, q_of.p, j_of.p);
+        PD_CHECK_LAUNCH();
         PD_TRY(dalloc(&tr_u4.p, (size_t)k * BN));
-        PD_TRY(dalloc(&tr_d32.p, (size_t)(k + 1) * D1));
+        PD_TRY(dalloc(&tr_d32.p, (size_t)(k + 1) * B * SL));
         PD_TRY(dalloc(&lF4.p, BN));
-        PD_TRY(dalloc(&ld2.p, D1));
+        PD_TRY(dalloc(&ld2.p, (size_t)B * SL));
         if (st->stencil) {
             PD_TRY(dalloc(&slot.p, nb));
             PD_TRY(stencil_slot_table(st, slot.p, s));
+            PD_TRY(dalloc(&dslot.p, SL));
+            k_sell_slots<<<(unsigned)((SL + 255) / 256), 256, 0, s>>>(SL, q_of.p, slot.p, dslot.p);
+            PD_CHECK_LAUNCH();
         } else {
             PD_TRY(dalloc(&tr_d.p, D1));  // staging for the generic layout's FP64 store
         }
@@ -505,6 +581,8 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
     a.rho = st->mat.rho;
     a.a = 1.0 - 0.5 * st->mat.zeta * st->dt;
     a.b = 1.0 + 0.5 * st->mat.zeta * st->dt;
+    a.dt_rb = a.dt / (a.rho * a.b);
+    a.a_b = a.a / a.b;
     a.law = st->mat.law;
     a.s_ratio = st->mat.s_ratio;
     a.k = st->mat.k;
@@ -533,19 +611,17 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
     PD_CHECK_CUDA(cudaMemsetAsync(lu.p, 0, U3 * sizeof(double), s));
     PD_CHECK_CUDA(cudaMemsetAsync(lv.p, 0, U3 * sizeof(double), s));
     if (f32)
-        PD_CHECK_CUDA(cudaMemsetAsync(ld2.p, 0, D1 * sizeof(float2), s));
+        PD_CHECK_CUDA(cudaMemsetAsync(ld2.p, 0, (size_t)B * SL * sizeof(float2), s));
     else
         PD_CHECK_CUDA(cudaMemsetAsync(ld.p, 0, D1 * sizeof(double), s));
     PD_CHECK_CUDA(cudaMemsetAsync(grad_s0, 0, (size_t)B * N * sizeof(double), s));
     if (grad_kappa) PD_CHECK_CUDA(cudaMemsetAsync(grad_kappa, 0, (size_t)B * N * sizeof(double), s));
-    const unsigned nblk_dof = (unsigned)((U3 + 255) / 256);
     const unsigned nblk_bond = (unsigned)(((long long)B * N * 32 + 255) / 256);
-    // the mixed bond adjoint strides over the nodes with a few blocks per SM
-    int sms = 0, dev = 0;
-    PD_CHECK_CUDA(cudaGetDevice(&dev));
-    PD_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const unsigned nblk_bond32 = (unsigned)std::min<long long>(nblk_bond, 8ll * sms);
     const unsigned nblk_node = (unsigned)((BN + 255) / 256);
+    PD_REQUIRE(B <= 65535, "at most 65535 samples per state");
+    const dim3 grid_sl((unsigned)((SL + 255) / 256), (unsigned)B);
+    const dim3 grid_nodes((unsigned)((N + 255) / 256), (unsigned)B);
+    const dim3 grid_dof((unsigned)((3 * N + 255) / 256), (unsigned)B);
     // FP32 trajectory of the mixed path at the state's current step n: the
     // gather records of parity n and the damage in CSR order
     auto snap_f32 = [&](int n, float4 *u4, float *d32) -> int {
@@ -553,9 +629,12 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
             k_rec_to_u4<<<nblk_node, 256, 0, s>>>(BN, (const float4 *)st->rec[n & 1], u4);
             PD_CHECK_LAUNCH();
         }
-        if (st->stencil) return stencil_gather_damage_f32(st, slot.p, d32, s);
-        PD_TRY(pd_state_store(st, nullptr, nullptr, tr_d.p, stream));
-        k_to_float<<<(unsigned)((D1 + 255) / 256), 256, 0, s>>>(D1, tr_d.p, d32);
+        if (st->stencil) {
+            k_gather_dmg<<<grid_sl, 256, 0, s>>>(SL, st->st_len, dslot.p, (const float *)st->dmg, d32);
+        } else {
+            PD_TRY(pd_state_store(st, nullptr, nullptr, tr_d.p, stream));
+            k_gather_csr<<<grid_sl, 256, 0, s>>>(SL, nb, q_of.p, tr_d.p, d32);
+        }
         PD_CHECK_LAUNCH();
         return PD_OK;
     };
@@ -566,24 +645,25 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
                              n0 + start, stream));
         for (int m = 0; m < len; ++m) {
             if (f32)
-                PD_TRY(snap_f32(n0 + start + m, tr_u4.p + (size_t)m * BN, tr_d32.p + (size_t)m * D1));
+                PD_TRY(snap_f32(n0 + start + m, tr_u4.p + (size_t)m * BN, tr_d32.p + (size_t)m * B * SL));
             else
                 PD_TRY(pd_state_store(st, tr_u.p + (size_t)m * U3, nullptr, tr_d.p + (size_t)m * D1, stream));
             PD_TRY(pd_step(st, 1, nullptr, stream));
         }
         if (f32)
-            PD_TRY(snap_f32(n0 + start + len, nullptr, tr_d32.p + (size_t)len * D1));
+            PD_TRY(snap_f32(n0 + start + len, nullptr, tr_d32.p + (size_t)len * B * SL));
         else
             PD_TRY(pd_state_store(st, nullptr, nullptr, tr_d.p + (size_t)len * D1, stream));
         for (int m = len - 1; m >= 0; --m) {
-            k_adj_nodes<<<nblk_dof, 256, 0, s>>>(a, start + m, plu, lv.p, lF.p, plun);
+            k_adj_nodes<<<grid_dof, 256, 0, s>>>(a, start + m, plu, lv.p, lF.p, plun);
             PD_CHECK_LAUNCH();
             if (f32) {
                 k_lF_to_f4<<<nblk_node, 256, 0, s>>>(BN, lF.p, kappa, lF4.p);
                 PD_CHECK_LAUNCH();
-                k_adj_bonds_f32<<<nblk_bond32, 256, 0, s>>>(a, tr_u4.p + (size_t)m * BN, tr_d32.p + (size_t)m * D1,
-                                                            tr_d32.p + (size_t)(m + 1) * D1, lF4.p, ld2.p, plun,
-                                                            grad_s0, grad_kappa);
+                k_adj_bonds_f32<<<grid_nodes, 256, 0, s>>>(a, SL, sl_off.p, j_of.p, tr_u4.p + (size_t)m * BN,
+                                                           tr_d32.p + (size_t)m * B * SL,
+                                                           tr_d32.p + (size_t)(m + 1) * B * SL, lF4.p, ld2.p, plun,
+                                                           grad_s0, grad_kappa);
             } else {
                 k_adj_bonds<<<nblk_bond, 256, 0, s>>>(a, tr_u.p + (size_t)m * U3, tr_d.p + (size_t)m * D1,
                                                       tr_d.p + (size_t)(m + 1) * D1, lF.p, ld.p, plun, grad_s0,

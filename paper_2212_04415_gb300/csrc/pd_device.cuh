@@ -414,10 +414,9 @@ int stencil_build(pd_state *st, const int32_t *col);
 int stencil_launch(const pd_state *st, const StepArgs &a, bool force_only, cudaStream_t s);
 int stencil_reset_damage(pd_state *st, cudaStream_t s);
 int stencil_map_damage(const pd_state *st, double *csr, bool to_state, cudaStream_t s);
-// slot of every CSR bond in one sample's stencil damage array; the damage of
-// every sample gathered into CSR order in FP32 (the adjoint's trajectory)
+// slot of every CSR bond in one sample's stencil damage array (the adjoint
+// gathers its FP32 damage trajectory through it)
 int stencil_slot_table(const pd_state *st, int32_t *slot, cudaStream_t s);
-int stencil_gather_damage_f32(const pd_state *st, const int32_t *slot, float *out, cudaStream_t s);
 void stencil_fill_args(const pd_state *st, StepArgs &a);
 
 }  // namespace pdi

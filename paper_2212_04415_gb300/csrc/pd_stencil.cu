@@ -688,15 +688,6 @@ __global__ void k_stencil_slots(const int32_t *row_ptr, const int32_t *col, cons
     }
 }
 
-// Damage of every sample in CSR order, FP32: out[b][p] = dmg[b][slot[p]].
-__global__ void k_stencil_gather_f32(long long nb, long long len, const int32_t *slot, const float *dmg,
-                                     float *out) {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nb) return;
-    const int b = blockIdx.y;
-    out[(size_t)b * nb + p] = dmg[(size_t)b * len + slot[p]];
-}
-
 typedef void (*StencilKernel)(const StepArgs);
 
 template <int DIM, int NS, int Q>
@@ -863,14 +854,6 @@ int stencil_slot_table(const pd_state *st, int32_t *slot, cudaStream_t s) {
                                                      st->by, st->bz, st->nbx, st->nby, st->st_wpb,
                                                      st->st_dim == 3 ? Sten<3>::kRounds : Sten<2>::kRounds,
                                                      st->st_box, slot);
-    PD_CHECK_LAUNCH();
-    return PD_OK;
-}
-
-int stencil_gather_damage_f32(const pd_state *st, const int32_t *slot, float *out, cudaStream_t s) {
-    PD_REQUIRE(st->B <= 65535, "at most 65535 samples per state");
-    const dim3 grid((unsigned)((st->nb + 255) / 256), (unsigned)st->B);
-    k_stencil_gather_f32<<<grid, 256, 0, s>>>(st->nb, st->st_len, slot, (const float *)st->dmg, out);
     PD_CHECK_LAUNCH();
     return PD_OK;
 }
