@@ -763,10 +763,6 @@ int stencil_build(pd_state *st, const int32_t *col) {
     // (measured on GB300: Q = 2 for single samples of the 28k-node beam, 1 for batches)
     const long long warps1 = st->n_bricks * ((st->B + st->st_ns - 1) / st->st_ns) * st->st_wpb;
     st->st_q = warps1 >= 152ll * 24 ? 1 : 2;
-    if (const char *e = std::getenv("PD_STENCIL_Q")) {
-        const int v = std::atoi(e);
-        if (v == 1 || v == 2 || v == 4) st->st_q = v;
-    }
     if (st->q_req) st->st_q = st->q_req;
     if (st->st_dim == 2) st->st_q = 1;
     while (st->st_q > 1 && 32 * st->st_wpb * st->st_q > 512) st->st_q /= 2;

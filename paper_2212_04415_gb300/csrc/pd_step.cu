@@ -1020,7 +1020,7 @@ extern "C" int pd_state_create_sched(const pd_grid *g, const int32_t *row_ptr, c
     st->B = batch;
     st->N = (int64_t)g->nx * g->ny * g->nz;
     st->nb = n_bonds;
-    // brick rows (PD_BRICK=YxZ overrides, for tuning)
+    // brick rows (a schedule overrides them)
     {
         static const int cand_generic[][2] = {{8, 8}, {8, 4}, {4, 4}, {4, 2}, {2, 2}, {2, 1}, {1, 1}};
         const double m2 = g->m_ratio * g->m_ratio;
@@ -1051,13 +1051,6 @@ extern "C" int pd_state_create_sched(const pd_grid *g, const int32_t *row_ptr, c
                     st->bz = cb[1];
                     break;
                 }
-            }
-        }
-        if (const char *e = std::getenv("PD_BRICK")) {
-            int y = 0, z = 0;
-            if (sscanf(e, "%dx%d", &y, &z) == 2 && y >= 1 && y <= 16 && z >= 1 && z <= 16) {
-                st->by = y;
-                st->bz = z;
             }
         }
         if (sched && (sched->by > 0 || sched->bz > 0)) {
