@@ -43,23 +43,32 @@ L2_FLUSH_BYTES = 256 << 20
 
 # DRAM bytes (read + write) of one k_step_stencil launch on this workload, from
 # the ncu capture summarised in profiles/k_step_stencil_beam28k_b1.md (cold L2),
-# valid while the kernel's sources are the ones captured.
+# valid while the kernel's sources are the ones captured (compared as code:
+# comments and whitespace do not count).
 NCU_STEP_TRAFFIC = {
     "bytes": 16_766_208 + 512,
     "sources": {
-        "paper_2212_04415_gb300/csrc/pd_stencil.cu": "b66a2b4fa6023fd90a6be9da34b61e37f012d43387b9049e6c4201eee5b4fcca",
-        "paper_2212_04415_gb300/csrc/pd_device.cuh": "0d55c2893f705419ac4ecd7ea5c427e2c54b587cc3e0f791157c5b5f63149d62",
+        "paper_2212_04415_gb300/csrc/pd_stencil.cu": "481317c76f810458c193c59fcc42889c86ae6dffa938d7d4c28ca24e0c128c63",
+        "paper_2212_04415_gb300/csrc/pd_device.cuh": "8315c190d745fb6a8da118480fdc599b9f38a35f75fc3a1cf693f07b08097805",
     },
 }
 
 
+def code_digest(text: str) -> str:
+    """sha256 of C/C++/CUDA source with comments removed and whitespace collapsed."""
+    import hashlib
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return hashlib.sha256(" ".join(text.split()).encode()).hexdigest()
+
+
 def _captured_traffic():
     """The captured per-launch DRAM traffic, or None once the kernel has changed."""
-    import hashlib
     for rel, digest in NCU_STEP_TRAFFIC["sources"].items():
         try:
-            with open(os.path.join(ROOT, rel), "rb") as f:
-                if hashlib.sha256(f.read()).hexdigest() != digest:
+            with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+                if code_digest(f.read()) != digest:
                     return None
         except OSError:
             return None

@@ -6,18 +6,23 @@
 // whose neighbour does not exist (outside the body, or across the notch) is a
 // permanently broken bond (d = 1): its force (1 - d) c s is exactly zero, so
 // the node sums equal those over the neighbour list alone, and the bond loop
-// has no ids, no tables and no padding. Two sub-lanes share a node: sub-lane 0
+// has no ids and no neighbour list. Two sub-lanes share a node: sub-lane 0
 // takes the 61 offsets +k of the positive half-stencil, sub-lane 1 the mirrored
-// offsets -k, in the same code with a sign register, so the two directed
-// copies of a bond are computed by identical instruction sequences on exactly
-// negated operands (bitwise-symmetric stretch and damage).
+// offsets -k, in the same code with a sign table, so the two directed copies of
+// a bond are computed by identical instruction sequences on exactly negated
+// operands (bitwise-symmetric stretch and damage).
 //
 // Layout per sample: [brick][warp][64 rounds][32 lanes] damage words (the 61
 // offsets padded to 64); lane L = 16 t + 8 r + c serves node (x0 + c, brick
 // row 2 w + r) and sub-lane t. A block (one brick of 8 x BY x BZ nodes, one
-// sample) stages the brick's gather records and a 3-cell halo in shared memory
-// (cells outside the grid read as zero displacement), so all gathers are
-// shared-memory loads with compile-time offsets.
+// sample, or a pair of samples on the paired FP32 instructions) stages the
+// brick's gather records and a 3-cell halo in shared memory, row-blocked so
+// that gathers are free of bank conflicts (cells outside the grid read as zero
+// displacement); all gathers are shared-memory loads.
+//
+// A step's reaction is reduced in its own launch, or, for launches of a single
+// wave, by every block of the next launch before it steps (no serial tail at
+// the end of each step; the run bookkeeping is double-buffered by parity).
 //
 // A one-layer grid (nz = 1, the plane models) has only the 28 in-plane
 // offsets: the same kernel is compiled for that shape (14 offsets per sign,
