@@ -277,12 +277,20 @@ PD_API int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int32_t
  *              (kappa NULL: kappa = 1)
  *   grad_s0, grad_kappa: device double[B][N] out (grad_kappa may be NULL)
  *   R_obs:     device double[B][n_obs] out, the forward reactions, or NULL
- * Checkpoints (u, v, d) every ckpt_every steps and recomputes each segment;
- * device memory: ((n_steps / ckpt_every + 2) (6N + n_b) + ckpt_every (3N + n_b)
- * + 12 N + n_b) B doubles, allocated per call (PD_ERR_OOM when unavailable).
- * Arithmetic is FP64; the states come from the state's own forward path.
- * Host-synchronous. On return the state holds the forward run's final state
- * (step n0 + n_steps), as after pd_step(n_steps). */
+ * Checkpoints (u, v, d) every ckpt_every steps (k) and recomputes each
+ * segment. Device memory, allocated per call (PD_ERR_OOM when unavailable),
+ * per sample: checkpoints (n_steps / k + 2) (6N + n_b) doubles and adjoint
+ * state 12 N doubles; then for FP64-path states the segment's trajectory
+ * k 3N + (k + 1) n_b doubles and n_b doubles of damage adjoint, for
+ * mixed-path states 16 k N + 4 (k + 1) S bytes of FP32 trajectory (S the
+ * slots of a sliced-ELL copy of the rows, slices of 32 nodes padded to the
+ * longest row, about n_b) and 8 S bytes of double-float damage adjoint.
+ * Arithmetic: FP64 for FP64-path states; for mixed-path states the bond terms
+ * in FP32 on the FP32 trajectory (the forward path's own precision class),
+ * the damage adjoint in double-float, the node sums in FP64. The states come
+ * from the state's own forward path. Host-synchronous. On return the state
+ * holds the forward run's final state (step n0 + n_steps), as after
+ * pd_step(n_steps). */
 PD_API int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int32_t n_obs,
                       const int32_t *obs_steps, const double *dJ_dR, const float *s0,
                       const float *kappa, double *grad_s0, double *grad_kappa, double *R_obs,
