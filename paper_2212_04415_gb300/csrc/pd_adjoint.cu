@@ -217,10 +217,6 @@ __device__ __forceinline__ void law_derivs_f(const AdjArgs &a, float s, float s0
     dDds0 = (-(beta / s + (s0 / s) * dbeta * dtds0) - dsc * (s0 / s) * dbeta * dtdsc) / (1.0f + al);
 }
 
-__global__ void k_to_float(long long n, const double *x, float *y) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) y[t] = (float)x[t];
-}
 
 // Node records of the mixed path at one step: (u, s0) with u = u_hi + u_lo
 // rounded to FP32, from the state's double-float gather records.

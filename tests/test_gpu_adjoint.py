@@ -32,9 +32,15 @@ def _fields(w, B, seed=0):
     return np.ascontiguousarray(s0, np.float32), np.ascontiguousarray(kap, np.float32)
 
 
-@pytest.mark.parametrize("prec,T", [("fp64", 150), ("fp64", 300), ("mixed", 300)])
-def test_node_gradients_against_oracle(pd, prec, T):
+@pytest.mark.parametrize("prec,T,mr", [("fp64", 150, 3.01), ("fp64", 300, 3.01), ("mixed", 300, 3.01),
+                                        ("mixed", 300, 3.5)])
+def test_node_gradients_against_oracle(pd, prec, T, mr):
+    """m = 3.01 runs the compile-time stencil; m = 3.5 (178 offsets) the
+    generic neighbour-list step, whose mixed-path adjoint stores its damage
+    trajectory through the FP64 state store."""
     w = _case()
+    if mr != 3.01:
+        w = dataclasses.replace(w, grid=dataclasses.replace(w.grid, m_ratio=mr))
     g = w.grid
     B = 2
     s0, kap = _fields(w, B)
@@ -55,7 +61,7 @@ def test_node_gradients_against_oracle(pd, prec, T):
         es = np.abs(gs[b] - ogs).max() / max(np.abs(ogs).max(), 1e-300)
         ek = np.abs(gk[b] - ogk).max() / np.abs(ogk).max()
         er = np.abs(R[b] - rr[obs]).max() / np.abs(rr[obs]).max()
-        print(f"{prec} T={T} sample {b}: grad_s0 err {es:.2e} (max {np.abs(ogs).max():.3e}), "
+        print(f"{prec} m={mr} T={T} sample {b}: grad_s0 err {es:.2e} (max {np.abs(ogs).max():.3e}), "
               f"grad_kappa err {ek:.2e}, R err {er:.2e}")
         assert er <= (1e-10 if prec == "fp64" else 1e-5)
         assert ek <= tol
