@@ -12,6 +12,10 @@ Pins (tests under ``tests/test_oracle_*.py``):
   strain energy density matches the lattice closed form and, within the
   lattice error, the continuum value that defines the micromodulus;
 * run: R(2U) = 2R(U) in the linear regime; damage monotone in time;
+* reaction R_n: at static equilibrium it equals the axial force carried by
+  the bonds crossing any interior section of a bar in tension, and the sum of
+  the two (equal) support reactions of a beam in three-point bending, both
+  from independent pair forces (tests/test_oracle_reaction.py);
 * adjoint: central differences of the run with respect to node s0 and kappa
   (elastic and softening windows, both laws); s0 has no influence before a
   bond softens; linear in the observation weights.
