@@ -351,8 +351,15 @@ static void forces(const or_problem *p, const double *u, double *d, double *F,
     int64_t n = (int64_t)p->nx * p->ny * p->nz;
     or_grid g = {p->nx, p->ny, p->nz, p->dx, 0.0, 0, 0, 0};
     double V = p->vol > 0.0 ? p->vol : p->dx * p->dx * p->dx;
-    double sm = -INFINITY;
+    /* Nodes are independent (each sums its own row in CSR order and updates
+     * only its own bonds' damage), so the node loop may run on OpenMP threads
+     * without changing a single bit; the largest stretch is taken per node
+     * and reduced afterwards in node order. Inside or_run_batch's parallel
+     * region this loop runs on the calling thread alone. */
+    double *smn = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
+        double sm = -INFINITY;
         double xi_[3];
         node_xyz(&g, i, xi_);
         double Fi[3] = {0.0, 0.0, 0.0};
@@ -380,7 +387,12 @@ static void forces(const or_problem *p, const double *u, double *d, double *F,
             for (int c = 0; c < 3; ++c) Fi[c] += f * V * y[c] / L;
         }
         for (int c = 0; c < 3; ++c) F[3 * i + c] = Fi[c];
+        smn[i] = sm;
     }
+    double sm = -INFINITY;
+    for (int64_t i = 0; i < n; ++i)
+        if (smn[i] > sm) sm = smn[i];
+    free(smn);
     if (smax) *smax = sm;
 }
 
