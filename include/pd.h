@@ -170,10 +170,14 @@ PD_API int pd_build_neighbours(const pd_grid *g, int32_t *row_ptr, int32_t *col,
  * overflow flag) lives in a 256-byte static device array that every GPU
  * loading the library holds until exit; it is cleared on every call. The
  * first call on a device looks up the array's device address (with that
- * device current), so make that first call before any stream capture. Calls
- * that overlap on the GPU share the array and race. Sizes: at most 2^31 - 2
- * nodes and 2^31 - 1 bonds; larger grids return PD_ERR_ARG. Arguments,
- * outputs, synchronisation and errors are those of pd_build_neighbours. */
+ * device current) and keeps it for the life of the process, so make that
+ * first call before any stream capture, and do not use the library across a
+ * cudaDeviceReset of that device. The stream must belong to the current
+ * device (PD_ERR_ARG otherwise). Calls that overlap on the GPU share the
+ * array and race. Sizes: at most 2^31 - 2 nodes and 2^31 - 1 bonds; larger
+ * grids return PD_ERR_ARG (a count-only call detects the bond overflow).
+ * Arguments, outputs, synchronisation and errors are those of
+ * pd_build_neighbours. */
 PD_API int pd_build_neighbours_noalloc(const pd_grid *g, int32_t *row_ptr, int32_t *col, int64_t cap,
                                        int64_t *n_bonds, pd_stream stream);
 
@@ -230,6 +234,13 @@ PD_API int pd_state_info(const pd_state *st, double *dt, double *c, int64_t *n_n
  * per-node fields s0 (device float[B][N], required) and kappa (device
  * float[B][N], or NULL for kappa = 1). */
 PD_API int pd_state_reset(pd_state *st, const float *s0, const float *kappa, pd_stream stream);
+
+/* pd_state_reset with the elastic-limit field s0 in FP64 (device
+ * double[B][N], required): FP64-path states keep it in FP64 (so that the FP64
+ * path is FP64 from the field on, e.g. for finite differences with respect to
+ * the field), mixed-path states round it to FP32 as pd_state_reset does.
+ * kappa as in pd_state_reset. */
+PD_API int pd_state_reset_f64(pd_state *st, const double *s0, const float *kappa, pd_stream stream);
 
 /* Overwrite u, v (device double[B][N][3]) and damage d (device double[B][n_bonds]
  * in CSR order, or NULL to keep) and set the step index of every sample. */
@@ -298,12 +309,15 @@ PD_API int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int32_t
 
 /* pd_run_to_peak for several states at once (meshes of different sizes, such as
  * the fine and coarse members of an MLMC level): each 64-step chunk is one
- * captured graph whose branches are the states' step launches, so the small
- * meshes' launches overlap the large ones'; one host poll per chunk covers
- * every state. Per state i: max_steps[i] and device outputs peak[i],
- * peak_step[i], n_done[i] (the pointer arrays are host arrays; each may be
- * NULL). Results equal n_states calls of pd_run_to_peak bit for bit.
- * Host-synchronous; 1 <= n_states <= 16, no state twice. */
+ * captured graph. Two states with the same launch shape (one sample per
+ * block, brick rows and warp split alike, same law and stiffness-field mode)
+ * step together in one launch per step, whose blocks cover both meshes;
+ * other states run as graph branches, so the small meshes' launches overlap
+ * the large ones'. One host poll per chunk covers every state. Per state i:
+ * max_steps[i] and device outputs peak[i], peak_step[i], n_done[i] (the
+ * pointer arrays are host arrays; each may be NULL). Results equal n_states
+ * calls of pd_run_to_peak bit for bit. Host-synchronous; 1 <= n_states <= 16,
+ * no state twice. */
 PD_API int pd_run_to_peak_multi(pd_state *const *states, int32_t n_states, const int32_t *max_steps,
                                 double *const *peak, int32_t *const *peak_step, int32_t *const *n_done,
                                 pd_stream stream);
@@ -404,6 +418,19 @@ typedef struct pd_mlmc_result {
  * (in sample order) to exactly the totals of a single-process run. */
 PD_API int mlmc_estimate(const pd_mlmc_cfg *cfg, pd_mlmc_result *out, double *q_fine,
                   double *q_coarse, double *batch_sums, pd_stream stream);
+
+/* Level totals and the estimator from the per-batch FP64 sums (n, sum Y,
+ * sum Y^2) that mlmc_estimate returns (batch_sums), for one run or for
+ * several processes that each took whole batches of every level (Section 4.2:
+ * samples are independent, so a run shards by sample): batch_sums is host
+ * double[sum_l n_batches[l]][3], level-major, each level's batches in sample
+ * order. Each level's batch sums are added in the order given, from zero --
+ * the additions a single run makes -- so the totals equal a single run's bit
+ * for bit; then the mean, the sample variance (Eq. sample_variance, 1/n form,
+ * and the unbiased form), Q_hat^ML = sum_l Y_hat_l (Eq. MLMC_estimator) and
+ * var_ml = sum_l s_l^2 / n_l (Eq. MLMC_error). cost_s, steps and
+ * bond_updates are 0 in out. Host only. */
+PD_API int mlmc_merge(int32_t n_levels, const int64_t *n_batches, const double *batch_sums, pd_mlmc_result *out);
 
 /* Optimal allocation N_l = floor(eps_s^-2 (sum_k sqrt(V_k C_k)) sqrt(V_l/C_l))
  * (Eq. sample_allocation), host arrays of length n_levels. */

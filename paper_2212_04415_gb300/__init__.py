@@ -92,6 +92,7 @@ _SIGS = {
     "pd_state_info": (C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int64)]),
     "pd_state_reset": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "pd_state_reset_f64": (C.c_int, [_VP, _VP, _VP, _VP]),
     "pd_state_load": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int32, _VP]),
     "pd_state_store": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "pd_force": (C.c_int, [_VP, _VP, _VP]),
@@ -114,6 +115,7 @@ _SIGS = {
     "pd_adjoint": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "pd_field_adjoint": (C.c_int, [_VP, C.c_int32, _VP, C.c_int32, _VP, _VP, _VP]),
     "pd_mlmc_allocation": (C.c_int, [C.c_int32, _VP, _VP, C.c_double, _VP]),
+    "mlmc_merge": (C.c_int, [C.c_int32, _VP, _VP, C.POINTER(MlmcResult)]),
 }
 
 _lib = None
@@ -231,6 +233,10 @@ class State:
 
     def reset(self, s0, kappa=None, stream=None):
         _check(lib().pd_state_reset(self.h, _ptr(s0), _ptr(kappa), _stream(stream)))
+
+    def reset_f64(self, s0, kappa=None, stream=None):
+        """reset with the strength field s0 in FP64 (pd_state_reset_f64)."""
+        _check(lib().pd_state_reset_f64(self.h, _ptr(s0), _ptr(kappa), _stream(stream)))
 
     def load(self, u, v, d=None, step=0, stream=None):
         _check(lib().pd_state_load(self.h, _ptr(u), _ptr(v), _ptr(d), step, _stream(stream)))
@@ -494,6 +500,25 @@ def ml_cdf(levels, x, n_u=1000, stream=None):
     _check(lib().pd_ml_cdf(len(levels), C.cast(n, C.c_void_p), _ptr(qf), _ptr(qc), n_u, x.numel(), _ptr(x),
                            _ptr(F), _stream(stream)))
     return F
+
+
+def mlmc_merge(batch_sums_per_level):
+    """Level totals and the estimator from per-batch sums (mlmc_merge):
+    ``batch_sums_per_level[l]`` is an [n_batches, 3] array of (n, sum Y,
+    sum Y^2) in sample order."""
+    import numpy as np
+    L = len(batch_sums_per_level)
+    arrs = [np.asarray(b, np.float64).reshape(-1, 3) for b in batch_sums_per_level]
+    nb = (C.c_int64 * L)(*[a.shape[0] for a in arrs])
+    flat = np.ascontiguousarray(np.concatenate(arrs) if arrs else np.zeros((0, 3)))
+    res = MlmcResult()
+    _check(lib().mlmc_merge(L, nb, flat.ctypes.data_as(C.c_void_p) if flat.size else None, C.byref(res)))
+    levels = []
+    for l in range(L):
+        lv = res.level[l]
+        levels.append(dict(n=lv.n, sum_y=lv.sum_y, sum_y2=lv.sum_y2, mean=lv.mean, var=lv.var,
+                           var_unbiased=lv.var_unbiased))
+    return dict(levels=levels, q_ml=res.q_ml, var_ml=res.var_ml)
 
 
 def mlmc_allocation(V, Cst, eps_s):

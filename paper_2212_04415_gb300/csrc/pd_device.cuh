@@ -55,7 +55,7 @@ struct StepArgs {
     int32_t *status;
     double *peak;
     int32_t *peak_step;
-    double *partial;       // [2][B][nblk] block partials (double-float), by launch parity
+    double *partial;       // [2][B][nblk] block partials (FP64), by launch parity
     unsigned int *ticket;
     double *reaction;
     int n_react;
@@ -70,9 +70,9 @@ struct StepArgs {
     int max_steps;
     int use_stop;
     int st_wpb;      // stencil path: row pairs per brick
-    float4 half_tab[61];   // stencil path: xi of the positive half-stencil offsets (x, y, z) and |xi|
-    int half_off[3][61];   // stencil path: integer components of those offsets
     float dxf;       // dx in FP32
+    float4 *grec0, *grec1;  // stencil path: gather records (u / dx in FP32, s0 / 2) by step parity
+    df idx_df;              // stencil path: 1 / dx as double-float
     float L0q[10];   // sqrt(q) dx in FP32, q = |k|^2 (stencil path)
     double cV;  // micromodulus x node volume
     double V;
@@ -83,6 +83,13 @@ struct StepArgs {
     double gfA;   // > 0: s_crit = s0 + gfA / s0, else s_ratio s0
     float gfA_f;
     df cV_df, cVh_df;  // cV and cV / 2 as double-float (stencil path: applied to the node sums)
+};
+
+// The arguments of two states stepped in one launch (the first nblk0 blocks
+// step a[0]).
+struct StepPair {
+    StepArgs a[2];
+    int nblk0;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -182,16 +189,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Sum over a warp along a fixed xor tree in double-float. TwoSum is exact and
-// the low-part sum is commutative, so every lane ends with the same total.
-__device__ __forceinline__ df warp_sum_df(df v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const df w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
-        v = df_add(v, w);
-    }
-    return v;
-}
 
 // Prescribed displacement U(n+1) and the prescribed velocity
 // (U(n+1) - U(n)) / dt of step n as double-float, from m = min(n, n_ramp)
@@ -233,26 +230,23 @@ struct RunView {
 // not they are pending).
 __device__ __forceinline__ RunView run_view(const StepArgs &a, int b, int lane) {
     const int i = a.par * a.B + b;
-    const float2 *part = (const float2 *)a.partial + ((size_t)(1 - a.par) * a.B + b) * a.nblk;
+    const double *part = a.partial + ((size_t)(1 - a.par) * a.B + b) * a.nblk;
     RunView r;
     const int pe = a.pend[i];
     r.dn = a.done[i];
     r.n = a.step[i];
     r.Q = a.pk2[i];
     r.np = a.ps2[i];
-    const float2 p0 = lane < a.nblk ? __ldcg(part + lane) : make_float2(0.f, 0.f);
+    const double p0 = lane < a.nblk ? __ldcg(part + lane) : 0.0;
     r.Rp = 0.0;
     r.have = 0;
     if (r.dn || !pe) return r;
-    df acc = {p0.x, p0.y};
-    for (int q = lane + 32; q < a.nblk; q += 32) {
-        const float2 pv = __ldcg(part + q);
-        acc = df_add(acc, df{pv.x, pv.y});
-    }
-    acc = warp_sum_df(acc);
+    double acc = p0;
+    for (int q = lane + 32; q < a.nblk; q += 32) acc += __ldcg(part + q);
+    acc = warp_sum(acc);
     r.have = 1;
     if (lane != 0) return r;
-    const double R = a.V * ((double)acc.hi + (double)acc.lo);
+    const double R = a.V * acc;
     r.Rp = R;
     if (R > r.Q) {
         r.Q = R;
@@ -311,18 +305,17 @@ __device__ __forceinline__ void carry_done(const StepArgs &a, int b) {
 }
 
 // Deferred reaction: the block's partial (sum over its prescribed DOFs of
-// -F sign, double-float, warp then the block's warps in order) is stored for
-// the next launch. Called by every thread of a reaction block.
-__device__ __forceinline__ void reaction_defer(const StepArgs &a, df Rloc, int b, int blk, int warp, int lane,
-                                               int nwarps, float2 *red) {
-    if (__any_sync(0xffffffffu, Rloc.hi != 0.f || Rloc.lo != 0.f)) Rloc = warp_sum_df(Rloc);
-    if (lane == 0) red[warp] = make_float2(Rloc.hi, Rloc.lo);
+// -F sign, FP64, warp then the block's warps in order) is stored for the next
+// launch. Called by every thread of a reaction block.
+__device__ __forceinline__ void reaction_defer(const StepArgs &a, double Rloc, int b, int blk, int warp, int lane,
+                                               int nwarps, double *red) {
+    if (__any_sync(0xffffffffu, Rloc != 0.0)) Rloc = warp_sum(Rloc);
+    if (lane == 0) red[warp] = Rloc;
     __syncthreads();
     if (warp == 0) {
-        df v = {0.f, 0.f};
-        if (lane < nwarps) v = df{red[lane].x, red[lane].y};
-        if (__any_sync(0xffffffffu, v.hi != 0.f || v.lo != 0.f)) v = warp_sum_df(v);
-        if (lane == 0) ((float2 *)a.partial)[((size_t)a.par * a.B + b) * a.nblk + blk] = make_float2(v.hi, v.lo);
+        double v = lane < nwarps ? red[lane] : 0.0;
+        if (__any_sync(0xffffffffu, v != 0.0)) v = warp_sum(v);
+        if (lane == 0) a.partial[((size_t)a.par * a.B + b) * a.nblk + blk] = v;
     }
 }
 
@@ -334,29 +327,26 @@ __device__ __forceinline__ void reaction_defer(const StepArgs &a, df Rloc, int b
 // sample's last reaction block) -- which then updates the run bookkeeping
 // from the run view that every block of the launch holds (and publishes the
 // previous step's reaction if this launch reduced it).
-// FP64 appears only in the final conversion R = V (hi + lo) and the peak test.
-__device__ __forceinline__ void reaction_finish(const StepArgs &a, df Rloc, int b, int blk, int warp, int lane,
-                                                int nwarps, float2 *red, unsigned *s_cnt, const RunView &rv) {
-    if (__any_sync(0xffffffffu, Rloc.hi != 0.f || Rloc.lo != 0.f)) Rloc = warp_sum_df(Rloc);
+// The whole reduction is FP64.
+__device__ __forceinline__ void reaction_finish(const StepArgs &a, double Rloc, int b, int blk, int warp, int lane,
+                                                int nwarps, double *red, unsigned *s_cnt, const RunView &rv) {
+    if (__any_sync(0xffffffffu, Rloc != 0.0)) Rloc = warp_sum(Rloc);
     unsigned flag = 0u;
     if (lane == 0) {
-        red[warp] = make_float2(Rloc.hi, Rloc.lo);
+        red[warp] = Rloc;
         __threadfence_block();
         flag = (atomicAdd(s_cnt, 1u) == (unsigned)(nwarps - 1));
     }
     flag = __shfl_sync(0xffffffffu, flag, 0);
     if (!flag) return;
     __threadfence_block();
-    df v = {0.f, 0.f};
-    if (lane < nwarps) {
-        const volatile float2 *r = red + lane;
-        v = df{r->x, r->y};
-    }
+    double v = 0.0;
+    if (lane < nwarps) v = *(const volatile double *)(red + lane);
     // (shared-memory partials: one round trip)
-    if (__any_sync(0xffffffffu, v.hi != 0.f || v.lo != 0.f)) v = warp_sum_df(v);
-    float2 *part = (float2 *)a.partial + ((size_t)a.par * a.B + b) * a.nblk;
+    if (__any_sync(0xffffffffu, v != 0.0)) v = warp_sum(v);
+    double *part = a.partial + ((size_t)a.par * a.B + b) * a.nblk;
     if (lane == 0) {
-        part[blk] = make_float2(v.hi, v.lo);
+        part[blk] = v;
         __threadfence();
         flag = (atomicAdd(&a.ticket[b], 1u) == (unsigned)(a.nblk - 1));
     }
@@ -364,19 +354,21 @@ __device__ __forceinline__ void reaction_finish(const StepArgs &a, df Rloc, int 
     if (!flag) return;
     __threadfence();
     // the block partials are read with L2 loads issued eight at a time (a
-    // dependent chain of volatile loads would cost one L2 round trip each)
-    df acc = {0.f, 0.f};
+    // dependent chain of volatile loads would cost one L2 round trip each),
+    // in the order the deferred path adds them (lane, lane + 32, ...)
+    double acc = 0.0;
     for (int q0 = lane; q0 < a.nblk; q0 += 256) {
-        float2 pv[8];
+        double pv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int q = q0 + 32 * u;
-            pv[u] = q < a.nblk ? __ldcg(part + q) : make_float2(0.f, 0.f);
+            pv[u] = q < a.nblk ? __ldcg(part + q) : 0.0;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc = df_add(acc, df{pv[u].x, pv[u].y});
+        for (int u = 0; u < 8; ++u)
+            if (q0 + 32 * u < a.nblk) acc = (q0 + 32 * u == lane) ? pv[u] : acc + pv[u];
     }
-    acc = warp_sum_df(acc);
+    acc = warp_sum(acc);
     if (lane == 0) {
         const int n = rv.n;
         double Q = rv.have ? rv.Q : a.pk2[a.par * a.B + b];  // no view built: the buffer as read
@@ -385,7 +377,7 @@ __device__ __forceinline__ void reaction_finish(const StepArgs &a, df Rloc, int 
             if (!isfinite(rv.Rp)) a.status[b] |= 1;
             if (a.reaction && a.k_local >= 1) a.reaction[(size_t)b * a.n_react + a.k_local - 1] = rv.Rp;
         }
-        const double R = a.V * ((double)acc.hi + (double)acc.lo);
+        const double R = a.V * acc;
         if (!isfinite(R)) a.status[b] |= 1;
         if (a.reaction) a.reaction[(size_t)b * a.n_react + a.k_local] = R;
         if (R > Q) {
@@ -418,5 +410,13 @@ int stencil_map_damage(const pd_state *st, double *csr, bool to_state, cudaStrea
 // gathers its FP32 damage trajectory through it)
 int stencil_slot_table(const pd_state *st, int32_t *slot, cudaStream_t s);
 void stencil_fill_args(const pd_state *st, StepArgs &a);
+// the stencil kernel's gather records (u / dx, s0 / 2), both parities, from the state's records
+int stencil_refresh_grec(pd_state *st, cudaStream_t s);
+size_t stencil_smem(const pd_state *st, int ns, bool kappa);
+// two one-sample-per-block states with the same launch shape, law and kappa
+// mode: one launch steps both (the fine and coarse members of MLMC pairs)
+bool stencil_pairable(const pd_state *s0, const pd_state *s1);
+int stencil_launch_pair(const pd_state *s0, const StepArgs &a0, const pd_state *s1, const StepArgs &a1,
+                        cudaStream_t s);
 
 }  // namespace pdi

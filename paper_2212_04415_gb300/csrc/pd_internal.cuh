@@ -107,6 +107,7 @@ struct pd_state {
     int32_t reduce_req;     // requested reaction reduction (schedule): 0 built-in, 1 own launch, 2 deferred
     int64_t st_len;         // damage slots per sample
     float *st_tmpl;         // [st_len]: 0 for real bonds, 1 for absent (broken) slots
+    float4 *grec[2];        // gather records by step parity, [B][N]: (u / dx rounded to FP32, s0 / 2)
     int16_t *st_box;        // [7^3]: stencil code 2 m + t of an offset, -1 outside
     int32_t *col_csr;       // CSR copy for damage load/store
     // per-sample state

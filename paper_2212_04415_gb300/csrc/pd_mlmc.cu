@@ -83,6 +83,30 @@ struct Buffers {
     }
 };
 
+// Sample mean Y_hat = sum_y / n and variance s^2 = sum_y2 / n - Y_hat^2 (Eq.
+// sample_variance, the paper's 1/n form) with the unbiased n/(n-1) form.
+static void level_stats(pd_mlmc_level *lv) {
+    if (lv->n <= 0) {
+        lv->mean = lv->var = lv->var_unbiased = 0.0;
+        return;
+    }
+    lv->mean = lv->sum_y / (double)lv->n;
+    lv->var = lv->sum_y2 / (double)lv->n - lv->mean * lv->mean;
+    lv->var_unbiased = lv->n > 1 ? lv->var * (double)lv->n / (double)(lv->n - 1) : 0.0;
+}
+
+// Q_hat^ML = sum_l Y_hat_l (Eq. MLMC_estimator) and its sampling variance
+// sum_l s_l^2 / n_l (Eq. MLMC_error), over the levels that have samples.
+static void estimator(pd_mlmc_result *r) {
+    r->q_ml = r->var_ml = 0.0;
+    for (int l = 0; l < r->n_levels; ++l) {
+        if (r->level[l].n > 0) {
+            r->q_ml += r->level[l].mean;
+            r->var_ml += r->level[l].var / (double)r->level[l].n;
+        }
+    }
+}
+
 static int run_level(const pd_mlmc_cfg *cfg, pd_field *field, int l, pd_mlmc_level *lv, double *q_fine,
                      double *q_coarse, double *batch_sums, cudaStream_t s) {
     const int64_t n_total = cfg->n_samples[l];
@@ -123,20 +147,20 @@ static int run_level(const pd_mlmc_cfg *cfg, pd_field *field, int l, pd_mlmc_lev
             pd_state_destroy(sf);
             pd_state_destroy(sc);
             sf = sc = nullptr;
-            pd_schedule shf{0, 0, 0}, shc{0, 0, 0};
-            if (cfg->tune_steps > 0) {
-                if ((rc = pd_autotune(&cfg->grid[l], mf.row, mf.col, mf.nb, &cfg->mat, &cfg->bc[l], b,
-                                      cfg->tune_steps, &shf, nullptr)))
-                    break;
-                if (l > 0 && (rc = pd_autotune(&cfg->grid[l - 1], mc.row, mc.col, mc.nb, &cfg->mat, &cfg->bc[l - 1],
-                                               b, cfg->tune_steps, &shc, nullptr)))
-                    break;
-            }
+            pd_schedule shf{0, 0, 0};
+            if (cfg->tune_steps > 0 &&
+                (rc = pd_autotune(&cfg->grid[l], mf.row, mf.col, mf.nb, &cfg->mat, &cfg->bc[l], b, cfg->tune_steps,
+                                  &shf, nullptr)))
+                break;
             if ((rc = pd_state_create_sched(&cfg->grid[l], mf.row, mf.col, mf.nb, &cfg->mat, &cfg->bc[l], b,
                                             cfg->tune_steps > 0 ? &shf : nullptr, &sf)))
                 break;
+            // the coarse member takes the fine member's launch shape (a brick
+            // of the same rows, the same warp split, one sample per block), so
+            // that one launch per step covers the pair (pd_run_to_peak_multi)
+            pd_schedule shc{sf->by, sf->bz, sf->st_q, sf->st_ns, 0};
             if (l > 0 && (rc = pd_state_create_sched(&cfg->grid[l - 1], mc.row, mc.col, mc.nb, &cfg->mat,
-                                                     &cfg->bc[l - 1], b, cfg->tune_steps > 0 ? &shc : nullptr, &sc)))
+                                                     &cfg->bc[l - 1], b, sf->stencil ? &shc : nullptr, &sc)))
                 break;
             cur_b = b;
         }
@@ -198,9 +222,7 @@ static int run_level(const pd_mlmc_cfg *cfg, pd_field *field, int l, pd_mlmc_lev
     pd_state_destroy(sf);
     pd_state_destroy(sc);
     if (rc != PD_OK) return rc;
-    lv->mean = lv->sum_y / (double)lv->n;
-    lv->var = lv->sum_y2 / (double)lv->n - lv->mean * lv->mean;
-    lv->var_unbiased = lv->n > 1 ? lv->var * (double)lv->n / (double)(lv->n - 1) : 0.0;
+    level_stats(lv);
     return PD_OK;
 }
 
@@ -253,12 +275,37 @@ extern "C" int mlmc_estimate(const pd_mlmc_cfg *cfg, pd_mlmc_result *out, double
     }
     pd_field_destroy(field);
     if (rc != PD_OK) return rc;
-    for (int l = 0; l < cfg->n_levels; ++l) {
-        if (r.level[l].n > 0) {
-            r.q_ml += r.level[l].mean;
-            r.var_ml += r.level[l].var / (double)r.level[l].n;
-        }
+    estimator(&r);
+    *out = r;
+    return PD_OK;
+}
+
+extern "C" int mlmc_merge(int32_t n_levels, const int64_t *n_batches, const double *batch_sums, pd_mlmc_result *out) {
+    PD_REQUIRE(n_levels >= 1 && n_levels <= PD_MAX_LEVELS, "n_levels out of range");
+    PD_REQUIRE(n_batches && out, "n_batches and out are required");
+    int64_t tot = 0;
+    for (int l = 0; l < n_levels; ++l) {
+        PD_REQUIRE(n_batches[l] >= 0, "n_batches[%d] is negative", l);
+        tot += n_batches[l];
     }
+    PD_REQUIRE(tot == 0 || batch_sums, "batch_sums is required");
+    pd_mlmc_result r;
+    memset(&r, 0, sizeof(r));
+    r.n_levels = n_levels;
+    int64_t q = 0;
+    for (int l = 0; l < n_levels; ++l) {
+        pd_mlmc_level &lv = r.level[l];
+        for (int64_t k = 0; k < n_batches[l]; ++k, ++q) {
+            const double nb = batch_sums[3 * q];
+            PD_REQUIRE(nb >= 0.0 && nb == std::floor(nb), "batch %lld of level %d has a non-integer count",
+                       (long long)k, l);
+            lv.n += (int64_t)nb;
+            lv.sum_y += batch_sums[3 * q + 1];
+            lv.sum_y2 += batch_sums[3 * q + 2];
+        }
+        level_stats(&lv);
+    }
+    estimator(&r);
     *out = r;
     return PD_OK;
 }

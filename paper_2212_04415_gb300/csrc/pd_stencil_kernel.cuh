@@ -1,0 +1,873 @@
+// pd_stencil_kernel.cuh -- device code of the compile-time stencil step,
+// included by the translation units that instantiate its variants
+// (pd_stencil_d3q1.cu, pd_stencil_d3q2.cu, pd_stencil_d3q4.cu, pd_stencil_d2.cu)
+// and, for its layout constants, by pd_stencil.cu.
+//
+// The mixed-precision step for the 122-offset horizon
+// (|k|^2 <= 9 in cell units: m in [3, sqrt(10)), which covers m = 3.01, 3.14
+// and pi of the workloads), with the stencil fixed at compile time.
+//
+// Every node keeps one damage slot for each of the 122 stencil offsets. A slot
+// whose neighbour does not exist (outside the body, or across the notch) is a
+// permanently broken bond (d = 1): its force (1 - d) c s is exactly zero, so
+// the node sums equal those over the neighbour list alone, and the bond loop
+// has no ids and no neighbour list.
+//
+// Two sub-lanes share a node. Round m of the half-stencil has the offset k_m
+// (k_m in the positive half): sub-lane 0 of node i evaluates the bond
+// (i, i + k_m), sub-lane 1 of node j the bond (j - k_m, j), so every sub-lane
+// evaluates a bond of offset +k_m from its lower end to its upper end. The two
+// directed copies of a bond therefore run the same instructions on the same
+// operands (bitwise-equal stretch and damage), and the lane's force is +f for
+// sub-lane 0 and -f for sub-lane 1. Sub-lane 1 gathers from a point-reflected
+// copy of the staged box, in which node j - k sits at (j's position) + k, so
+// both sub-lanes address their neighbour as own + offset(k) with the same
+// compile-time offset: the rounds are unrolled, the offsets, |k| and |k|^2 are
+// immediates and no table is read per bond.
+//
+// Gather records are the displacements in cell units (u / dx) rounded to FP32,
+// with s0 / 2 (the bond's elastic limit is the plain sum of the two halves):
+// bond kinematics and forces are FP32 on FP32 positions (the stretch is
+// scale-free, and the force direction is a unit vector). The state itself
+// (u and v) stays double-float and is integrated per node.
+//
+// Layout per sample: [brick][warp][16 quads][32 lanes][4 rounds] damage words
+// (the 61 offsets padded to 64; one 128-bit load per lane covers four rounds);
+// lane L = 16 t + 8 r + c serves node (x0 + c, brick row 2 w + r) and sub-lane
+// t. A block (one brick of 8 x BY x BZ nodes, one sample, or a pair of samples
+// on the paired FP32 instructions) stages the brick's gather records and a
+// 3-cell halo in shared memory: the upper part (the brick's layers and the 3
+// above) as is for sub-lane 0, the lower part (the 3 below and the brick's
+// layers) point-reflected for sub-lane 1. Rows are blocked so that the 8
+// x-consecutive lanes of a gather read 128 contiguous bytes (no bank
+// conflicts); cells outside the grid read as zero displacement.
+//
+// A step's reaction is reduced in its own launch, or, for launches of a single
+// wave, by every block of the next launch before it steps (no serial tail at
+// the end of each step; the run bookkeeping is double-buffered by parity).
+//
+// A one-layer grid (nz = 1, the plane models) has only the 28 in-plane
+// offsets: the same kernel is compiled for that shape (14 offsets per sign,
+// padded to 16 rounds, no z-halo), so a plane node costs 14 rounds, not 61.
+#pragma once
+
+#include <utility>
+
+#include "pd_device.cuh"
+
+namespace pdi {
+
+namespace {
+
+constexpr int kHalo = 3;           // largest offset component (x and y)
+constexpr int kWx = kSlice + 2 * kHalo;
+constexpr int kRowC = kWx * 16;    // bytes of one 16-byte chunk across a staged row's cells
+constexpr int kRowK = kWx * 4;     // bytes of one staged row of kappa values (one sample)
+
+// Stencil shape by dimension: the positive half of the horizon (61 of the 122
+// offsets in 3D; 14 of the 28 offsets of a one-layer grid, where no bond
+// leaves the layer), padded to a multiple of 16 rounds in the damage layout,
+// and the z-halo staged in shared memory.
+template <int DIM>
+struct Sten;
+template <>
+struct Sten<3> {
+    static constexpr int kHalf = 61, kRounds = 64, kHaloZ = 3;
+};
+template <>
+struct Sten<2> {
+    static constexpr int kHalf = 14, kRounds = 16, kHaloZ = 0;
+};
+
+struct I3 {
+    int x, y, z;
+};
+
+__host__ __device__ constexpr bool positive_half(int x, int y, int z) {
+    return z > 0 || (z == 0 && (y > 0 || (y == 0 && x > 0)));
+}
+
+// m-th offset of the positive half-stencil, in ascending linear order (z, y, x);
+// the planar stencil is the z = 0 part of the same order.
+template <int DIM>
+__host__ __device__ constexpr I3 half_off(int m) {
+    int cnt = 0;
+    for (int z = 0; z <= (DIM == 3 ? 3 : 0); ++z)
+        for (int y = -3; y <= 3; ++y)
+            for (int x = -3; x <= 3; ++x)
+                if (positive_half(x, y, z) && x * x + y * y + z * z <= 9) {
+                    if (cnt == m) return I3{x, y, z};
+                    ++cnt;
+                }
+    return I3{0, 0, 0};
+}
+
+// |k| for |k|^2 = q (cell units; 7 is not a sum of three squares)
+__host__ __device__ constexpr float knorm(int q) {
+    return q == 1   ? 1.0f
+           : q == 2 ? 1.41421356237309505f
+           : q == 3 ? 1.73205080756887729f
+           : q == 4 ? 2.0f
+           : q == 5 ? 2.23606797749978970f
+           : q == 6 ? 2.44948974278317810f
+           : q == 8 ? 2.82842712474619010f
+                    : 3.0f;
+}
+
+// ---- lane arithmetic. A lane carries one sample (float) or a pair of samples
+// (float2, on the paired FP32 instructions, which issue once for both). Every
+// operation rounds once as written (no contraction), so the paired kernel
+// gives each sample of the pair the same bits as the one-sample kernel.
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <class V>
+__device__ __forceinline__ V splat(float x);
+template <>
+__device__ __forceinline__ float splat<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ float2 splat<float2>(float x) { return make_float2(x, x); }
+
+// a - b, rounded once (the fma -1 * b + a is exact before its rounding)
+template <class V>
+__device__ __forceinline__ V vsub(V a, V b) { return vfma(b, splat<V>(-1.0f), a); }
+
+__device__ __forceinline__ float neg(float a) { return -a; }
+__device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// PTX approximate reciprocal square root and reciprocal (the special-function
+// unit; relative error a few ulp, ample for a stretch of order 1e-4..1e-2)
+__device__ __forceinline__ float rsqrt_ap(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_ap(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float vrsqrt(float x) { return rsqrt_ap(x); }
+__device__ __forceinline__ float2 vrsqrt(float2 x) { return make_float2(rsqrt_ap(x.x), rsqrt_ap(x.y)); }
+__device__ __forceinline__ float vrcp(float x) { return rcp_ap(x); }
+__device__ __forceinline__ float2 vrcp(float2 x) { return make_float2(rcp_ap(x.x), rcp_ap(x.y)); }
+
+__device__ __forceinline__ float el(float v, int) { return v; }
+__device__ __forceinline__ float el(float2 v, int s) { return s ? v.y : v.x; }
+
+__device__ __forceinline__ float shfl16(float v) { return __shfl_xor_sync(0xffffffffu, v, 16); }
+__device__ __forceinline__ float2 shfl16(float2 v) { return make_float2(shfl16(v.x), shfl16(v.y)); }
+
+// s + x accumulated with the rounding error carried in c (Knuth's TwoSum)
+template <class V>
+__device__ __forceinline__ void two_sum_acc_v(V &s, V &c, V x) {
+    const V t = vadd(s, x);
+    const V z = vsub(t, s);
+    const V e = vadd(vsub(s, vsub(t, z)), vsub(x, z));
+    s = t;
+    c = vadd(c, e);
+}
+
+template <int NS>
+struct Lane;
+template <>
+struct Lane<1> {
+    using V = float;
+};
+template <>
+struct Lane<2> {
+    using V = float2;
+};
+
+// The staged box (dynamic shared memory of the step kernel).
+extern __shared__ float4 g_box[];
+
+// A staged gather record: u / dx (x, y, z) and s0 / 2. One sample: one float4
+// per cell. A pair: the two samples' values interleaved ({x0, x1, y0, y1},
+// {z0, z1, h0, h1}) in two chunks, kRowC bytes apart (row-blocked).
+template <class V>
+struct Rec {
+    V x, y, z, h;
+};
+
+template <int NS>
+__device__ __forceinline__ Rec<typename Lane<NS>::V> load_rec(int off) {
+    const char *p = (const char *)g_box + off;
+    if constexpr (NS == 1) {
+        const float4 v = *(const float4 *)p;
+        return {v.x, v.y, v.z, v.w};
+    } else {
+        const float4 A = *(const float4 *)p, B = *(const float4 *)(p + kRowC);
+        return {make_float2(A.x, A.y), make_float2(A.z, A.w), make_float2(B.x, B.y), make_float2(B.z, B.w)};
+    }
+}
+
+template <int NS>
+__device__ __forceinline__ typename Lane<NS>::V load_kap(int off) {
+    const char *p = (const char *)g_box + off;
+    if constexpr (NS == 1)
+        return *(const float *)p;
+    else
+        return *(const float2 *)p;
+}
+
+struct LawC {
+    float sr, kf, af, i1, i2, gfa;
+};
+
+// The law of a bond past its elastic limit, out of line: the bond loop is
+// unrolled over the whole half-stencil, and the law (divisions, an
+// exponential) inlined at every round would multiply the loop's code -- the
+// instruction cache then starves the warps -- for a path few bonds take.
+template <int LAW>
+__device__ __noinline__ float law_cold(float s, float s0, LawC lc) {
+    return law_damage<float>(LAW, s, s0, crit_stretch(s0, lc.sr, lc.gfa), lc.kf, lc.af, lc.i1, lc.i2);
+}
+
+// Per-lane context of the bond loop.
+template <int NS>
+struct BondCtx {
+    using V = typename Lane<NS>::V;
+    int rb[4];         // byte offset (in the staged box) of the lane's own record, + kz layers
+    int kb[4];         // the same for the staged kappa values
+    V sg;              // +1 (sub-lane 0) or -1 (sub-lane 1)
+    V cx, cy, cz;      // -sg x the lane's own displacement (cell units)
+    V h, kap;          // own s0 / 2 and kappa
+    float4 *dq0, *dq1; // damage quads of the lane's samples ([quad][32 lanes] float4)
+    bool w0, w1;       // damage writes enabled per sample
+    LawC lc;
+};
+
+// Damage words of one group of 8 rounds: two quads per sample.
+template <int NS>
+struct DQ {
+    float4 a0, a1, b0, b1;
+};
+
+template <int NS>
+__device__ __forceinline__ DQ<NS> load_dq(const BondCtx<NS> &cx, int g) {
+    DQ<NS> q;
+    q.a0 = cx.dq0[32 * (2 * g)];
+    q.a1 = cx.dq0[32 * (2 * g + 1)];
+    if constexpr (NS == 2) {
+        q.b0 = cx.dq1[32 * (2 * g)];
+        q.b1 = cx.dq1[32 * (2 * g + 1)];
+    }
+    return q;
+}
+
+template <int J>
+__device__ __forceinline__ float quad_el(const float4 &a0, const float4 &a1) {
+    const float4 &v = J < 4 ? a0 : a1;
+    constexpr int e = J % 4;
+    return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
+// Kinematics of one bond with offset k (cell units) from the staged record r
+// of its neighbour: the lower end's displacement is subtracted from the upper
+// end's (sg carries the sub-lane's role), eta = u_upper - u_lower, y = k +
+// eta, and the stretch s = (|y| - |k|)/|k| = eta.(2k + eta) / (|k| (|y| + |k|))
+// with |y|^2 = |k|^2 + eta.(2k + eta); zero components of k add nothing. The
+// unrolled loop (k known at compile time) and the fix-up of bonds past their
+// elastic limit (k from a table) run these same operations, so both see the
+// same bits.
+template <class V, class Ctx>
+__device__ __forceinline__ void bond_kin(const Ctx &cx, const Rec<V> &r, int kx, int ky, int kz, float KW, float KW2,
+                                         V &yx, V &yy, V &yz, V &rL, V &s) {
+    const V ex = vfma(cx.sg, r.x, cx.cx);
+    const V ey = vfma(cx.sg, r.y, cx.cy);
+    const V ez = vfma(cx.sg, r.z, cx.cz);
+    yx = kx ? vadd(ex, splat<V>((float)kx)) : ex;
+    yy = ky ? vadd(ey, splat<V>((float)ky)) : ey;
+    yz = kz ? vadd(ez, splat<V>((float)kz)) : ez;
+    const V wx = kx ? vadd(ex, splat<V>(2.0f * kx)) : ex;
+    const V wy = ky ? vadd(ey, splat<V>(2.0f * ky)) : ey;
+    const V wz = kz ? vadd(ez, splat<V>(2.0f * kz)) : ez;
+    const V num = vfma(ez, wz, vfma(ey, wy, vmul(ex, wx)));
+    const V y2 = vadd(num, splat<V>(KW2));
+    rL = vrsqrt(y2);
+    const V L = vmul(y2, rL);
+    s = vmul(num, vrcp(vfma(L, splat<V>(KW), splat<V>(KW2))));
+}
+
+// Force factor (1 - d) s / |y| of a bond (times kappa_i + kappa_j with a
+// stiffness field; micromodulus and volume are applied to the node sum).
+template <class V>
+__device__ __forceinline__ V bond_g(V d, V s, V rL) {
+    return vmul(vfma(neg(d), s, s), rL);
+}
+
+// Offsets of the rounds of the positive half-stencil, for the fix-up path.
+struct HalfTab {
+    signed char k[64][4];  // kx, ky, kz, |k|^2 (padding rounds: zero)
+};
+template <int DIM>
+__host__ __device__ constexpr HalfTab half_table() {
+    HalfTab t{};
+    for (int m = 0; m < Sten<DIM>::kHalf; ++m) {
+        const I3 k = half_off<DIM>(m);
+        t.k[m][0] = (signed char)k.x;
+        t.k[m][1] = (signed char)k.y;
+        t.k[m][2] = (signed char)k.z;
+        t.k[m][3] = (signed char)(k.x * k.x + k.y * k.y + k.z * k.z);
+    }
+    return t;
+}
+__constant__ HalfTab c_half[2] = {half_table<2>(), half_table<3>()};
+
+__device__ __forceinline__ float knorm_rt(int q) {
+    switch (q) {
+        case 1: return knorm(1);
+        case 2: return knorm(2);
+        case 3: return knorm(3);
+        case 4: return knorm(4);
+        case 5: return knorm(5);
+        case 6: return knorm(6);
+        case 8: return knorm(8);
+        default: return knorm(9);
+    }
+}
+
+// Bonds of rounds m0 + j (bit j of mask) whose stretch passed their elastic
+// limit this step, out of line: recompute the bond, apply the law, and where
+// the damage grew store it and correct the lane's force sums, which the
+// unrolled loop formed with the previous damage, by the difference of the
+// force factors (the two directed copies of a bond run the same correction).
+template <int DIM, int NS, int LAW, bool KAPPA>
+__device__ __forceinline__ void fix_bonds(unsigned mask, int m0, const BondCtx<NS> &cx, typename Lane<NS>::V &px,
+                                       typename Lane<NS>::V &py, typename Lane<NS>::V &pz) {
+    using V = typename Lane<NS>::V;
+    while (mask) {
+        const int j = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int m = m0 + j;
+        const signed char *k = c_half[DIM - 2].k[m];
+        const int kx = k[0], ky = k[1], kz = k[2], q = k[3];
+        const Rec<V> r = load_rec<NS>(cx.rb[kz] + 16 * kx + NS * kRowC * ky);
+        V yx, yy, yz, rL, s;
+        bond_kin<V>(cx, r, kx, ky, kz, knorm_rt(q), (float)q, yx, yy, yz, rL, s);
+        const V s0 = vadd(cx.h, r.h);
+        float *slot0 = (float *)(cx.dq0 + 32 * (m / 4)) + (m % 4);
+        V dold, dnew;
+        if constexpr (NS == 1) {
+            dold = dnew = *slot0;
+            if (s > s0) {
+                const float dl = law_cold<LAW>(s, s0, cx.lc);
+                if (dl > dold) {
+                    dnew = dl;
+                    *slot0 = dl;
+                }
+            }
+        } else {
+            float *slot1 = (float *)(cx.dq1 + 32 * (m / 4)) + (m % 4);
+            dold = make_float2(*slot0, *slot1);
+            dnew = dold;
+            if (s.x > s0.x) {
+                const float dl = law_cold<LAW>(s.x, s0.x, cx.lc);
+                if (dl > dold.x) {
+                    dnew.x = dl;
+                    if (cx.w0) *slot0 = dl;
+                }
+            }
+            if (s.y > s0.y) {
+                const float dl = law_cold<LAW>(s.y, s0.y, cx.lc);
+                if (dl > dold.y) {
+                    dnew.y = dl;
+                    if (cx.w1) *slot1 = dl;
+                }
+            }
+        }
+        V dg = vsub(bond_g(dnew, s, rL), bond_g(dold, s, rL));
+        if constexpr (KAPPA) dg = vmul(dg, vadd(cx.kap, load_kap<NS>(cx.kb[kz] + 4 * NS * kx + NS * kRowK * ky)));
+        px = vfma(dg, yx, px);
+        py = vfma(dg, yy, py);
+        pz = vfma(dg, yz, pz);
+    }
+}
+
+// One bond of the lane (round M, offset k = k_M) with the previous damage d,
+// for its one or two samples; a stretch past the elastic limit of a bond not
+// yet broken sets bit J of the group's mask (the law runs in fix_bonds).
+template <int DIM, int NS, bool KAPPA, int M, int J>
+__device__ __forceinline__ void stencil_bond(typename Lane<NS>::V d, const BondCtx<NS> &cx, typename Lane<NS>::V &px,
+                                             typename Lane<NS>::V &py, typename Lane<NS>::V &pz, unsigned &mask) {
+    using V = typename Lane<NS>::V;
+    constexpr I3 k = half_off<DIM>(M);
+    constexpr int q = k.x * k.x + k.y * k.y + k.z * k.z;
+    const Rec<V> r = load_rec<NS>(cx.rb[k.z] + 16 * k.x + NS * kRowC * k.y);
+    V yx, yy, yz, rL, s;
+    bond_kin<V>(cx, r, k.x, k.y, k.z, knorm(q), (float)q, yx, yy, yz, rL, s);
+    const V s0 = vadd(cx.h, r.h);
+    // a broken or absent bond (d = 1: cut by the notch, or a neighbour
+    // outside the body, whose staged record reads as zero) has nothing left
+    // to soften, whatever its stretch
+    bool past;
+    if constexpr (NS == 1)
+        past = s > s0 && d < 1.0f;
+    else
+        past = (s.x > s0.x && d.x < 1.0f) || (s.y > s0.y && d.y < 1.0f);
+    if (past) mask |= 1u << J;
+    V g = bond_g(d, s, rL);
+    if constexpr (KAPPA) g = vmul(g, vadd(cx.kap, load_kap<NS>(cx.kb[k.z] + 4 * NS * k.x + NS * kRowK * k.y)));
+    px = vfma(g, yx, px);
+    py = vfma(g, yy, py);
+    pz = vfma(g, yz, pz);
+}
+
+template <int DIM, int NS, bool KAPPA, int M, int J, int JG>
+__device__ __forceinline__ void bond_if(const BondCtx<NS> &cx, const DQ<NS> &dq, typename Lane<NS>::V &px,
+                                        typename Lane<NS>::V &py, typename Lane<NS>::V &pz, unsigned &mask) {
+    if constexpr (M < Sten<DIM>::kHalf) {
+        typename Lane<NS>::V d;
+        if constexpr (NS == 1)
+            d = quad_el<J>(dq.a0, dq.a1);
+        else
+            d = make_float2(quad_el<J>(dq.a0, dq.a1), quad_el<J>(dq.b0, dq.b1));
+        stencil_bond<DIM, NS, KAPPA, M, JG>(d, cx, px, py, pz, mask);
+    }
+}
+
+template <int DIM, int NS, bool KAPPA, int M0, int JG0, int... J>
+__device__ __forceinline__ void bond_group(const BondCtx<NS> &cx, const DQ<NS> &dq, typename Lane<NS>::V &px,
+                                           typename Lane<NS>::V &py, typename Lane<NS>::V &pz, unsigned &mask,
+                                           std::integer_sequence<int, J...>) {
+    (bond_if<DIM, NS, KAPPA, M0 + J, J, JG0 + J>(cx, dq, px, py, pz, mask), ...);
+}
+
+// Groups of 8 rounds are summed kSumGroups at a time: the FP32 sum of 8
+// kSumGroups bonds is added to the compensated (TwoSum) accumulator after the
+// bonds among them that passed their elastic limit have been fixed up.
+constexpr int kSumGroups = 2;
+
+// Groups [G, G1) of 8 rounds; the next group's damage words are requested
+// before the current group is computed.
+template <int DIM, int NS, int LAW, bool KAPPA, int G, int G1>
+__device__ __forceinline__ void bond_groups(const BondCtx<NS> &cx, const DQ<NS> &cur, typename Lane<NS>::V *acc,
+                                            typename Lane<NS>::V &px, typename Lane<NS>::V &py,
+                                            typename Lane<NS>::V &pz, unsigned &mask) {
+    using V = typename Lane<NS>::V;
+    if constexpr (G < G1) {
+        DQ<NS> nxt;
+        if constexpr (G + 1 < G1) nxt = load_dq<NS>(cx, G + 1);
+        constexpr int G0 = G - (G % kSumGroups);  // first group of the sum
+        bond_group<DIM, NS, KAPPA, 8 * G, 8 * (G - G0)>(cx, cur, px, py, pz, mask,
+                                                         std::make_integer_sequence<int, 8>{});
+        if (G % kSumGroups == kSumGroups - 1 || G + 1 == G1) {
+            if (__builtin_expect(mask != 0u, 0)) fix_bonds<DIM, NS, LAW, KAPPA>(mask, 8 * G0, cx, px, py, pz);
+            two_sum_acc_v(acc[0], acc[3], px);
+            two_sum_acc_v(acc[1], acc[4], py);
+            two_sum_acc_v(acc[2], acc[5], pz);
+            px = py = pz = splat<V>(0.f);
+            mask = 0u;
+        }
+        if constexpr (G + 1 < G1) bond_groups<DIM, NS, LAW, KAPPA, G + 1, G1>(cx, nxt, acc, px, py, pz, mask);
+    }
+}
+
+template <int DIM, int NS, int LAW, bool KAPPA, int G0, int G1>
+__device__ __forceinline__ void bond_span(const BondCtx<NS> &cx, typename Lane<NS>::V *acc) {
+    static_assert(G0 % kSumGroups == 0, "spans start at a sum boundary");
+    using V = typename Lane<NS>::V;
+    const DQ<NS> first = load_dq<NS>(cx, G0);
+    V px = splat<V>(0.f), py = px, pz = px;
+    unsigned mask = 0u;
+    bond_groups<DIM, NS, LAW, KAPPA, G0, G1>(cx, first, acc, px, py, pz, mask);
+}
+
+// Warps of a block: wpb row pairs x Q parts of the half-stencil, for NS
+// samples (one, or a pair on the paired FP32 instructions). Part 0's warp of
+// a row pair adds the other parts' sums (fixed order) and integrates.
+template <int DIM, int NS, int Q, int LAW, bool KAPPA, bool FORCE_ONLY>
+__device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
+    using V = typename Lane<NS>::V;
+    using S = Sten<DIM>;
+    constexpr int kRounds = S::kRounds, HZ = S::kHaloZ, NG = kRounds / 8;
+    constexpr int RB = NS * kRowC;  // bytes of a staged (y, z) row of records
+    constexpr int RK = NS * kRowK;  // bytes of a staged row of kappa values
+    __shared__ double red[NS][16];
+    __shared__ float s_pre[NS][4];  // U(n+1) and the prescribed velocity, double-float
+    __shared__ unsigned s_cnt[NS];
+    __shared__ RunView s_rv[NS];    // run bookkeeping per sample, with the pending reaction added
+    __shared__ int s_n[NS];         // step index per sample
+    __shared__ int s_ridx;          // the brick's index among the reaction bricks, or -1
+
+    const int nwarps = blockDim.x >> 5;
+    const int wpb = a.st_wpb;
+    const int ngrp = (a.B + NS - 1) / NS;
+    const int grp = blk % ngrp;
+    const int brick = blk / ngrp;
+    const auto sample_of = [&](int s) {
+        const int b = NS * grp + s;
+        return b < a.B ? b : NS * grp;  // the second member of the last pair of an odd batch is a copy
+    };
+    int ns[NS];
+    bool live[NS];
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const bool real = NS * grp + s < a.B;
+        const int b = sample_of(s);
+        ns[s] = a.step[a.par * a.B + b];
+        const bool dn = FORCE_ONLY ? false : (a.done[a.par * a.B + b] != 0);
+        live[s] = real && !dn;
+        if (!FORCE_ONLY && real && dn && brick == 0 && threadIdx.x == 0) carry_done(a, b);
+        any = any || live[s];
+    }
+    if (!any) return;  // block-uniform
+    if (threadIdx.x == 0) s_ridx = FORCE_ONLY ? -1 : a.brick_ridx[brick];
+    if (threadIdx.x < NS) s_n[threadIdx.x] = ns[threadIdx.x];
+    // the run view (with the previous launch's reaction, if it left it
+    // pending) is built by warp s for sample s while the staging copies fly
+    const auto build_views = [&]() {
+        if (FORCE_ONLY || !a.pendable) return;
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        for (int s = w; s < NS; s += nwarps) {
+            RunView rv;
+            if (live[s]) {
+                rv = run_view(a, sample_of(s), l);
+            } else {
+                rv.n = ns[s];
+                rv.dn = 1;
+                rv.Q = 0.0;
+                rv.np = 0;
+                rv.Rp = 0.0;
+                rv.have = 0;
+            }
+            if (l == 0) s_rv[s] = rv;
+        }
+    };
+    if (threadIdx.x < 16 * NS) (&red[0][0])[threadIdx.x] = 0.0;
+    if (threadIdx.x < NS) {
+        df U1, vp;
+        prescribed(a, ns[threadIdx.x], U1, vp);
+        s_pre[threadIdx.x][0] = U1.hi;
+        s_pre[threadIdx.x][1] = U1.lo;
+        s_pre[threadIdx.x][2] = vp.hi;
+        s_pre[threadIdx.x][3] = vp.lo;
+        s_cnt[threadIdx.x] = 0u;
+    }
+    const int bx = brick % a.nbx, by = (brick / a.nbx) % a.nby, bz = brick / (a.nbx * a.nby);
+    const int x0 = kSlice * bx, y0 = a.BY * by, z0 = a.BZ * bz;
+    const size_t BN = (size_t)a.B * a.N;
+    const int Wy = a.BY + 2 * kHalo;
+    const int Zp = a.BZ + HZ;    // layers of each copy: upper (sub-lane 0) and reflected lower (sub-lane 1)
+    const int LB = RB * Wy, LK = RK * Wy;
+    const int oP = 0, oM = LB * Zp;                  // record copies
+    const int okP = 2 * LB * Zp, okM = okP + LK * Zp;  // kappa copies (KAPPA)
+    const int oPart = KAPPA ? okM + LK * Zp : okP;
+    float *s_part = (float *)((char *)g_box + oPart);  // [Q-1][wpb][16][6 NS]
+
+    // stage the box (cells outside the grid read as zero): box layer lz holds
+    // z0 - HZ + lz; the upper copy takes lz >= HZ, the reflected lower copy
+    // lz < BZ + HZ at (Zp - 1 - lz, Wy - 1 - ly, kWx - 1 - lx)
+    {
+        const int nbox = kWx * Wy * (a.BZ + 2 * HZ);
+        const float4 *gin0 = ((ns[0] & 1) ? a.grec1 : a.grec0) + (size_t)sample_of(0) * a.N;
+        const float4 *gin1 = ((ns[NS - 1] & 1) ? a.grec1 : a.grec0) + (size_t)sample_of(NS - 1) * a.N;
+        const float *kin0 = KAPPA ? a.kappa + (size_t)sample_of(0) * a.N : nullptr;
+        const float *kin1 = KAPPA ? a.kappa + (size_t)sample_of(NS - 1) * a.N : nullptr;
+        // row / Wy as a multiply and shift: exact for rows below 2^20 / Wy
+        // (the error of the rounded-up reciprocal stays below 1 / Wy); the
+        // staged box has at most 38 x 22 rows
+        const unsigned inv_wy = ((1u << 20) + (unsigned)Wy - 1u) / (unsigned)Wy;
+        for (int qi = threadIdx.x; qi < nbox; qi += blockDim.x) {
+            const int row = qi / kWx, lx = qi - kWx * row;
+            const int lz = (int)(((unsigned)row * inv_wy) >> 20), ly = row - Wy * lz;
+            const int gx = x0 - kHalo + lx, gy = y0 - kHalo + ly, gz = z0 - HZ + lz;
+            const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz;
+            const int gi = in ? gx + a.nx * (gy + a.ny * gz) : 0;
+            const bool toP = lz >= HZ, toM = lz < a.BZ + HZ;
+            const int rP = LB * (lz - HZ) + RB * ly + 16 * lx;
+            const int rM = LB * (Zp - 1 - lz) + RB * (Wy - 1 - ly) + 16 * (kWx - 1 - lx);
+            if constexpr (NS == 1) {
+                if (toP) cp_async16((char *)g_box + oP + rP, gin0 + gi, in ? 16 : 0);
+                if (toM) cp_async16((char *)g_box + oM + rM, gin0 + gi, in ? 16 : 0);
+            } else {
+                float4 h0 = make_float4(0.f, 0.f, 0.f, 0.f), h1 = h0;
+                if (in) {
+                    h0 = gin0[gi];
+                    h1 = gin1[gi];
+                }
+                const float4 A = make_float4(h0.x, h1.x, h0.y, h1.y), C = make_float4(h0.z, h1.z, h0.w, h1.w);
+                if (toP) {
+                    *(float4 *)((char *)g_box + oP + rP) = A;
+                    *(float4 *)((char *)g_box + oP + rP + kRowC) = C;
+                }
+                if (toM) {
+                    *(float4 *)((char *)g_box + oM + rM) = A;
+                    *(float4 *)((char *)g_box + oM + rM + kRowC) = C;
+                }
+            }
+            if constexpr (KAPPA) {
+                const int kP = LK * (lz - HZ) + RK * ly + 4 * NS * lx;
+                const int kM = LK * (Zp - 1 - lz) + RK * (Wy - 1 - ly) + 4 * NS * (kWx - 1 - lx);
+                const float k0 = in ? kin0[gi] : 0.f;
+                if constexpr (NS == 1) {
+                    if (toP) *(float *)((char *)g_box + okP + kP) = k0;
+                    if (toM) *(float *)((char *)g_box + okM + kM) = k0;
+                } else {
+                    const float2 kk = make_float2(k0, in ? kin1[gi] : 0.f);
+                    if (toP) *(float2 *)((char *)g_box + okP + kP) = kk;
+                    if (toM) *(float2 *)((char *)g_box + okM + kM) = kk;
+                }
+            }
+        }
+        build_views();
+        cp_async_wait_all();
+    }
+    __syncthreads();
+    if (!FORCE_ONLY && a.pendable) {
+        // samples that the reduced reaction stops are not stepped (every
+        // block reaches the same decision); brick 0 records them
+        bool anyl = false;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const bool stop = live[s] && s_rv[s].dn;
+            if (stop && brick == 0 && threadIdx.x == 0) write_done(a, sample_of(s), s_rv[s]);
+            live[s] = live[s] && !stop;
+            anyl = anyl || live[s];
+        }
+        if (!anyl) return;  // block-uniform
+    }
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rp = warp % wpb, part = warp / wpb;
+    const int t = lane >> 4, r = (lane >> 3) & 1, c = lane & 7;
+    double Rloc[NS];  // this thread's share of each sample's reaction (FP64)
+#pragma unroll
+    for (int s = 0; s < NS; ++s) Rloc[s] = 0.0;
+    const int row = 2 * rp + r;
+    const int ly = row % a.BY, lz = row / a.BY;
+    const int gx = x0 + c, gy = y0 + ly, gz = z0 + lz;
+    const bool own = gx < a.nx && gy < a.ny && gz < a.nz;
+    const int ii = gx + a.nx * (gy + a.ny * gz);
+    V acc[6];  // sx, sy, sz, cx, cy, cz
+#pragma unroll
+    for (int q = 0; q < 6; ++q) acc[q] = splat<V>(0.f);
+    if (own) {
+        // own record: upper copy at (lz, kHalo + ly, kHalo + c) for sub-lane 0,
+        // reflected copy at (Zp - 1 - HZ - lz, Wy - 1 - kHalo - ly, kWx - 1 - kHalo - c) for sub-lane 1
+        const int rown = t == 0 ? oP + LB * lz + RB * (kHalo + ly) + 16 * (kHalo + c)
+                                : oM + LB * (Zp - 1 - HZ - lz) + RB * (Wy - 1 - kHalo - ly) + 16 * (kWx - 1 - kHalo - c);
+        const int kown = t == 0 ? okP + LK * lz + RK * (kHalo + ly) + 4 * NS * (kHalo + c)
+                                : okM + LK * (Zp - 1 - HZ - lz) + RK * (Wy - 1 - kHalo - ly) +
+                                      4 * NS * (kWx - 1 - kHalo - c);
+        const Rec<V> me = load_rec<NS>(rown);
+        BondCtx<NS> cx;
+#pragma unroll
+        for (int z = 0; z < 4; ++z) {
+            cx.rb[z] = rown + z * LB;
+            cx.kb[z] = kown + z * LK;
+        }
+        cx.sg = splat<V>(t == 0 ? 1.0f : -1.0f);
+        cx.cx = t == 0 ? neg(me.x) : me.x;
+        cx.cy = t == 0 ? neg(me.y) : me.y;
+        cx.cz = t == 0 ? neg(me.z) : me.z;
+        cx.h = me.h;
+        cx.kap = KAPPA ? load_kap<NS>(kown) : splat<V>(1.0f);
+        cx.dq0 = (float4 *)a.dmg + (size_t)sample_of(0) * (a.sell_len / 4) +
+                 ((size_t)brick * wpb + rp) * (kRounds / 4) * 32 + lane;
+        cx.dq1 = cx.dq0 + (size_t)(sample_of(NS - 1) - sample_of(0)) * (a.sell_len / 4);
+        cx.w0 = live[0];
+        cx.w1 = live[NS - 1];
+        cx.lc = LawC{a.s_ratio_f, a.k_f, a.alpha_f, a.inv_1mek_f, a.inv_1pa_f, a.gfA_f};
+        if constexpr (Q == 1) {
+            bond_span<DIM, NS, LAW, KAPPA, 0, NG>(cx, acc);
+        } else if constexpr (Q == 2) {
+            if (part == 0)
+                bond_span<DIM, NS, LAW, KAPPA, 0, NG / 2>(cx, acc);
+            else
+                bond_span<DIM, NS, LAW, KAPPA, NG / 2, NG>(cx, acc);
+        } else {
+            static_assert(Q == 4 && NG % 4 == 0, "four parts need a multiple of four groups");
+            if (part == 0)
+                bond_span<DIM, NS, LAW, KAPPA, 0, NG / 4>(cx, acc);
+            else if (part == 1)
+                bond_span<DIM, NS, LAW, KAPPA, NG / 4, NG / 2>(cx, acc);
+            else if (part == 2)
+                bond_span<DIM, NS, LAW, KAPPA, NG / 2, 3 * NG / 4>(cx, acc);
+            else
+                bond_span<DIM, NS, LAW, KAPPA, 3 * NG / 4, NG>(cx, acc);
+        }
+    }
+    // The node's force is sub-lane 0's sum minus sub-lane 1's: negate on
+    // sub-lane 1 (exact), then add the two partials in double-float (TwoSum is
+    // exact and symmetric, so both sub-lanes end with the same total).
+    if (t == 1) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) acc[q] = neg(acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const V p = shfl16(acc[q]);
+        const V pc = shfl16(acc[3 + q]);
+        V sq = acc[q], cq = splat<V>(0.f);
+        two_sum_acc_v(sq, cq, p);
+        acc[q] = sq;
+        acc[3 + q] = vadd(cq, vadd(acc[3 + q], pc));
+    }
+    if (Q > 1) {
+        if (part > 0 && t == 0) {
+            float *dst = s_part + (((size_t)(part - 1) * wpb + rp) * 16 + (lane & 15)) * (6 * NS);
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+#pragma unroll
+                for (int s = 0; s < NS; ++s) dst[NS * q + s] = el(acc[q], s);
+        }
+        __syncthreads();
+        if (part == 0) {
+            for (int pp = 1; pp < Q; ++pp) {
+                const float *src = s_part + (((size_t)(pp - 1) * wpb + rp) * 16 + (lane & 15)) * (6 * NS);
+                V w[6];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    if constexpr (NS == 1)
+                        w[q] = src[q];
+                    else
+                        w[q] = make_float2(src[2 * q], src[2 * q + 1]);
+                }
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    V sq = acc[q], cq = splat<V>(0.f);
+                    two_sum_acc_v(sq, cq, w[q]);
+                    acc[q] = sq;
+                    acc[3 + q] = vadd(cq, vadd(acc[3 + q], w[3 + q]));
+                }
+            }
+        }
+    }
+    if (own && part == 0) {
+        const df cVd = KAPPA ? a.cVh_df : a.cV_df;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            if (FORCE_ONLY ? (NS * grp + s >= a.B) : !live[s]) continue;
+            const size_t node = (size_t)sample_of(s) * a.N + ii;
+            const bool odd = s_n[s] & 1;
+            const float4 *rin = (const float4 *)(odd ? a.rec1 : a.rec0);
+            float4 *rout = (float4 *)(odd ? a.rec0 : a.rec1);
+            float4 *gout = odd ? a.grec0 : a.grec1;
+            for (int q = t; q < 3; q += 2) {
+                const float sq = el(q == 0 ? acc[0] : (q == 1 ? acc[1] : acc[2]), s);
+                const float cq = el(q == 0 ? acc[3] : (q == 1 ? acc[4] : acc[5]), s);
+                const df F = df_mul(two_sum(sq, cq), cVd);
+                if (FORCE_ONLY) {
+                    a.F_out[3 * node + q] = (double)F.hi + (double)F.lo;
+                    continue;
+                }
+                const uint8_t code = a.codes[3 * (size_t)ii + q];
+                df u = {((const float *)(rin + node))[q], ((const float *)(rin + BN + node))[q]};
+                float *vh = (float *)(a.vdf + node);
+                float *vl = (float *)(a.vdf + BN + node);
+                df v = {vh[q], vl[q]};
+                if (code == 0) {
+                    v = df_mul(df_add(df_mul(a.ca_df, v), df_mul(a.dtr_df, F)), a.icb_df);
+                    u = df_add(u, df_mul(a.dt_df, v));
+                } else if (code == 1) {
+                    u = {0.f, 0.f};
+                    v = {0.f, 0.f};
+                } else {
+                    const float sg = code == 2 ? 1.0f : -1.0f;
+                    Rloc[s] -= (double)sg * ((double)F.hi + (double)F.lo);
+                    v = df{sg * s_pre[s][2], sg * s_pre[s][3]};
+                    u = df{sg * s_pre[s][0], sg * s_pre[s][1]};
+                }
+                vh[q] = v.hi;
+                vl[q] = v.lo;
+                ((float *)(rout + node))[q] = u.hi;
+                ((float *)(rout + BN + node))[q] = u.lo;
+                ((float *)(gout + node))[q] = df_mul(u, a.idx_df).hi;
+            }
+        }
+    }
+    if (FORCE_ONLY) return;
+
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        if (!live[s]) continue;  // block-uniform
+        RunView rv;
+        if (a.pendable) {
+            rv = s_rv[s];
+        } else {  // nothing is ever pending: the finishing block reads the peak itself
+            rv.n = s_n[s];
+            rv.dn = 0;
+            rv.Q = 0.0;
+            rv.np = 0;
+            rv.Rp = 0.0;
+            rv.have = 0;
+        }
+        const int ridx = s_ridx;
+        if (a.defer) {
+            if (brick == 0 && threadIdx.x == 0) write_deferred(a, sample_of(s), rv);
+            if (ridx >= 0) reaction_defer(a, Rloc[s], sample_of(s), ridx, warp, lane, nwarps, red[s]);
+        } else if (ridx >= 0) {
+            reaction_finish(a, Rloc[s], sample_of(s), ridx, warp, lane, nwarps, red[s], &s_cnt[s], rv);
+        }
+    }
+}
+
+// One step of one state: blocks are (brick, sample group) pairs, sample fastest.
+template <int DIM, int NS, int Q, int LAW, bool KAPPA, bool FORCE_ONLY>
+__global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const StepArgs a) {
+    step_block<DIM, NS, Q, LAW, KAPPA, FORCE_ONLY>(a, blockIdx.x);
+}
+
+// One step of two states in one launch (the fine and the coarse member of the
+// coupled pairs of an MLMC level: meshes of different sizes with the same
+// brick shape and law): the first nblk0 blocks step state 0, the others state
+// 1, each exactly as its own launch would (same bits). The arguments stay in
+// parameter space (grid constant), so selecting a state by block copies
+// nothing.
+template <int DIM, int Q, int LAW, bool KAPPA>
+__global__ void __launch_bounds__(512, 2) k_step_stencil_pair(const __grid_constant__ StepPair g) {
+    const int i = (int)blockIdx.x >= g.nblk0 ? 1 : 0;
+    step_block<DIM, 1, Q, LAW, KAPPA, false>(g.a[i], (int)blockIdx.x - (i ? g.nblk0 : 0));
+}
+
+typedef void (*StencilKernel)(const StepArgs);
+typedef void (*StencilPairKernel)(const StepPair);
+
+template <int DIM, int Q>
+StencilPairKernel pick_pair_variant(int law, bool kappa) {
+    if (law == PD_LAW_BILINEAR) return kappa ? k_step_stencil_pair<DIM, Q, 0, true> : k_step_stencil_pair<DIM, Q, 0, false>;
+    return kappa ? k_step_stencil_pair<DIM, Q, 1, true> : k_step_stencil_pair<DIM, Q, 1, false>;
+}
+
+// The variant of one (dimension, parts) pair for samples per block, law,
+// stiffness field and force-only mode; force-only evaluations always take the
+// one-sample kernel (same bits).
+template <int DIM, int Q>
+StencilKernel pick_variant(int ns, int law, bool kappa, bool fo) {
+    if (fo) {
+        if (law == PD_LAW_BILINEAR)
+            return kappa ? k_step_stencil<DIM, 1, Q, 0, true, true> : k_step_stencil<DIM, 1, Q, 0, false, true>;
+        return kappa ? k_step_stencil<DIM, 1, Q, 1, true, true> : k_step_stencil<DIM, 1, Q, 1, false, true>;
+    }
+    if (ns == 2) {
+        if (law == PD_LAW_BILINEAR)
+            return kappa ? k_step_stencil<DIM, 2, Q, 0, true, false> : k_step_stencil<DIM, 2, Q, 0, false, false>;
+        return kappa ? k_step_stencil<DIM, 2, Q, 1, true, false> : k_step_stencil<DIM, 2, Q, 1, false, false>;
+    }
+    if (law == PD_LAW_BILINEAR)
+        return kappa ? k_step_stencil<DIM, 1, Q, 0, true, false> : k_step_stencil<DIM, 1, Q, 0, false, false>;
+    return kappa ? k_step_stencil<DIM, 1, Q, 1, true, false> : k_step_stencil<DIM, 1, Q, 1, false, false>;
+}
+
+}  // namespace
+
+// one per translation unit
+typedef void (*StencilKernelFn)(const StepArgs);
+typedef void (*StencilPairFn)(const StepPair);
+StencilKernelFn stencil_pick_d3q1(int ns, int law, bool kappa, bool fo);
+StencilKernelFn stencil_pick_d3q2(int ns, int law, bool kappa, bool fo);
+StencilKernelFn stencil_pick_d3q4(int ns, int law, bool kappa, bool fo);
+StencilKernelFn stencil_pick_d2(int ns, int law, bool kappa, bool fo);
+StencilPairFn stencil_pair_d3q1(int law, bool kappa);
+StencilPairFn stencil_pair_d3q2(int law, bool kappa);
+StencilPairFn stencil_pair_d3q4(int law, bool kappa);
+StencilPairFn stencil_pair_d2(int law, bool kappa);
+
+}  // namespace pdi

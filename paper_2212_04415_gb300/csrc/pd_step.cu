@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
     __shared__ float4 s_xi[kTab];
     __shared__ int s_off[kTab];
     __shared__ double4_32a s_xid[F64 ? kTab : 1];
-    __shared__ float2 red[kWarps];
+    __shared__ double red[kWarps];
     __shared__ double s_U[2];
     __shared__ float s_pre[4];
     __shared__ unsigned s_cnt;
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
         s_off[q] = a.off_tab[q];
         if (F64) s_xid[q] = a.xid_tab[q];
     }
-    if (threadIdx.x < kWarps) red[threadIdx.x] = make_float2(0.f, 0.f);
+    if (threadIdx.x < kWarps) red[threadIdx.x] = 0.0;
     if (threadIdx.x == 0) {
         if (F64) {
             s_U[0] = ramp(a, n);
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = lane % C, t = lane / C;
-    df Rloc = {0.f, 0.f};
+    double Rloc = 0.0;  // this thread's share of the reaction (FP64)
 
     if (!done) {
         for (int r = warp; r < a.BY * a.BZ; r += kWarps) {
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
                             vc = 0.0;
                         } else {
                             const double sg = code == 2 ? 1.0 : -1.0;
-                            Rloc = df_add(Rloc, df_split(-sg * F));
+                            Rloc -= sg * F;
                             vc = sg * (s_U[1] - s_U[0]) * a.idt;
                             uc = sg * s_U[1];
                         }
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
                             v = {0.f, 0.f};
                         } else {
                             const float sg = code == 2 ? 1.0f : -1.0f;
-                            Rloc = df_add(Rloc, df{-sg * F.hi, -sg * F.lo});
+                            Rloc -= (double)sg * ((double)F.hi + (double)F.lo);
                             v = df{sg * s_pre[2], sg * s_pre[3]};
                             u = df{sg * s_pre[0], sg * s_pre[1]};
                         }
@@ -411,17 +411,17 @@ __global__ void k_min(const double *x, long long n, double *out) {
 }
 
 template <bool F64>
-__global__ void k_reset(long long N, int B, const float *s0, const float *kappa, double *u64, double *v64,
-                        float4 *vdf, void *rec0, void *rec1) {
+__global__ void k_reset(long long N, int B, const float *s0, const double *s0d, const float *kappa, double *u64,
+                        double *v64, float4 *vdf, void *rec0, void *rec1) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N * B) return;
-    const float s = s0 ? s0[t] : 1e-4f;
+    const float s = s0d ? (float)s0d[t] : (s0 ? s0[t] : 1e-4f);
     if (F64) {
         for (int c = 0; c < 3; ++c) {
             u64[3 * t + c] = 0.0;
             v64[3 * t + c] = 0.0;
         }
-        const double4_32a r = make_double4_32a(0.0, 0.0, 0.0, (double)s);
+        const double4_32a r = make_double4_32a(0.0, 0.0, 0.0, s0d ? s0d[t] : (double)s);
         ((double4_32a *)rec0)[t] = r;
         ((double4_32a *)rec1)[t] = r;
     } else {
@@ -751,6 +751,8 @@ static void free_state(pd_state *st) {
     cudaFree(st->vdf);
     cudaFree(st->rec[0]);
     cudaFree(st->rec[1]);
+    cudaFree(st->grec[0]);
+    cudaFree(st->grec[1]);
     cudaFree(st->kappa);
     cudaFree(st->codes);
     cudaFree(st->coord);
@@ -1177,7 +1179,7 @@ extern "C" int pd_state_info(const pd_state *st, double *dt, double *c, int64_t 
     return PD_OK;
 }
 
-extern "C" int pd_state_reset(pd_state *st, const float *s0, const float *kappa, pd_stream stream) {
+static int state_reset(pd_state *st, const float *s0, const double *s0d, const float *kappa, pd_stream stream) {
     PD_REQUIRE(st != nullptr, "state is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     const long long NB = st->N * st->B;
@@ -1196,12 +1198,13 @@ extern "C" int pd_state_reset(pd_state *st, const float *s0, const float *kappa,
         st->has_kappa = false;
     }
     if (f64)
-        k_reset<true><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, s0, kappa, st->u64, st->v64, st->vdf, st->rec[0],
-                                                     st->rec[1]);
+        k_reset<true><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, s0, s0d, kappa, st->u64, st->v64, st->vdf,
+                                                     st->rec[0], st->rec[1]);
     else
-        k_reset<false><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, s0, kappa, st->u64, st->v64, st->vdf,
+        k_reset<false><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, s0, s0d, kappa, st->u64, st->v64, st->vdf,
                                                       st->rec[0], st->rec[1]);
     PD_CHECK_LAUNCH();
+    if (st->stencil) PD_TRY(stencil_refresh_grec(st, s));
     if (st->chunk_exec && had != st->has_kappa) {  // the captured chunk bakes the kernel choice
         cudaGraphExecDestroy(st->chunk_exec);
         st->chunk_exec = nullptr;
@@ -1211,6 +1214,15 @@ extern "C" int pd_state_reset(pd_state *st, const float *s0, const float *kappa,
                                                   st->ticket, 0);
     PD_CHECK_LAUNCH();
     return PD_OK;
+}
+
+extern "C" int pd_state_reset(pd_state *st, const float *s0, const float *kappa, pd_stream stream) {
+    return state_reset(st, s0, nullptr, kappa, stream);
+}
+
+extern "C" int pd_state_reset_f64(pd_state *st, const double *s0, const float *kappa, pd_stream stream) {
+    PD_REQUIRE(s0 != nullptr, "s0 is required");
+    return state_reset(st, nullptr, s0, kappa, stream);
 }
 
 extern "C" int pd_state_load(pd_state *st, const double *u, const double *v, const double *d, int32_t step,
@@ -1231,6 +1243,7 @@ extern "C" int pd_state_load(pd_state *st, const double *u, const double *v, con
         k_load_u<false><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, u, v, st->u64, st->v64, st->vdf, st->step + st->bk_par * st->B,
                                                        st->rec[0], st->rec[1]);
     PD_CHECK_LAUNCH();
+    if (st->stencil) PD_TRY(stencil_refresh_grec(st, s));
     if (d && st->stencil) {
         PD_TRY(stencil_map_damage(st, (double *)d, true, s));
     } else if (d) {
@@ -1408,10 +1421,28 @@ extern "C" int pd_run_to_peak_multi(pd_state *const *states, int32_t n_states, c
         set_error("stream or event creation failed");
         return PD_ERR_CUDA;
     }
-    // the chunk graph: state 0 on the capture stream, the others on forked branches
+    // the chunk graph: two states with the same launch shape (the members of an
+    // MLMC pair) step together, one launch per step; otherwise state 0 runs on
+    // the capture stream and the others on forked branches
+    const bool paired = n_states == 2 && stencil_pairable(states[0], states[1]);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && paired) {
+        int lrc = PD_OK;
+        StepArgs a0 = make_args(states[0]), a1 = make_args(states[1]);
+        a0.use_stop = a1.use_stop = 1;
+        a0.max_steps = max_steps[0];
+        a1.max_steps = max_steps[1];
+        for (int q = 0; q < chunk && lrc == PD_OK; ++q) {
+            a0.par = states[0]->bk_par ^ (q & 1);  // even chunk: ends on the parity it starts from
+            a1.par = states[1]->bk_par ^ (q & 1);
+            a0.defer = states[0]->st_defer && q + 1 < chunk;  // the last launch finishes
+            a1.defer = states[1]->st_defer && q + 1 < chunk;
+            lrc = stencil_launch_pair(states[0], a0, states[1], a1, cs);
+        }
+        e = cudaStreamEndCapture(cs, &graph);
+        if (lrc != PD_OK) rc = lrc;
+    } else if (e == cudaSuccess) {
         int lrc = PD_OK;
         if (n_states > 1) cudaEventRecord(fork, cs);
         for (int i = 0; i < n_states && lrc == PD_OK; ++i) {
