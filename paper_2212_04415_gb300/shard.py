@@ -44,31 +44,18 @@ def merge(batch_sums_by_rank):
 
     ``batch_sums_by_rank[r][l]`` is the [n_batches, 3] array that process r's
     ``mlmc_estimate`` returned for level l; processes are listed in rank order,
-    which is sample order under ``split``. Returns the per-level dicts and the
+    which is sample order under ``split``. The arrays are concatenated level
+    by level in that order and handed to the library's ``mlmc_merge``, which
+    adds them from zero (the additions of a single run) and forms the
     estimator Q_ML = sum_l Y_hat_l with its variance sum_l V_l / N_l (Eqs.
-    MLMC_estimator, MLMC_error), V_l being the sample variance of Eq.
-    sample_variance."""
+    MLMC_estimator, MLMC_error)."""
+    import numpy as np
+
+    from . import mlmc_merge
     n_levels = len(batch_sums_by_rank[0])
-    levels = []
-    q_ml = var_ml = 0.0
-    for l in range(n_levels):
-        n = 0
-        s1 = s2 = 0.0
-        for r in range(len(batch_sums_by_rank)):
-            for row in np.asarray(batch_sums_by_rank[r][l], np.float64).reshape(-1, 3):
-                n += int(row[0])
-                s1 += float(row[1])
-                s2 += float(row[2])
-        if n > 0:
-            mean = s1 / n
-            var = s2 / n - mean * mean
-            var_u = var * n / (n - 1) if n > 1 else 0.0
-            q_ml += mean
-            var_ml += var / n
-        else:
-            mean = var = var_u = 0.0
-        levels.append(dict(n=n, sum_y=s1, sum_y2=s2, mean=mean, var=var, var_unbiased=var_u))
-    return dict(levels=levels, q_ml=q_ml, var_ml=var_ml)
+    per_level = [np.concatenate([np.asarray(r[l], np.float64).reshape(-1, 3) for r in batch_sums_by_rank])
+                 for l in range(n_levels)]
+    return mlmc_merge(per_level)
 
 
 def allgather(obj, group=None):

@@ -13,6 +13,12 @@ from oracle import mlmc as omlmc
 from paper_2212_04415_gb300 import shard
 
 
+@pytest.fixture(autouse=True, scope="module")
+def _library(built_lib):
+    """shard.merge calls the library's host-only mlmc_merge (no GPU involved)."""
+    return built_lib
+
+
 def _batch_sums(Y, first, count, batch):
     """(n, sum Y, sum Y^2) per batch of ``batch`` consecutive samples, added in sample order."""
     rows = []
