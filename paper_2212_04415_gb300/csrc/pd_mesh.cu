@@ -270,9 +270,15 @@ extern "C" int pd_build_neighbours_noalloc(const pd_grid *g, int32_t *row_ptr, i
     PD_REQUIRE(row_ptr != nullptr && n_bonds != nullptr, "row_ptr and n_bonds are required");
     const long long n = (long long)g->nx * g->ny * g->nz;
     PD_REQUIRE(n + 1 <= 2147483647ll, "at most 2^31 - 2 nodes");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (s != nullptr) {  // the scratch address is the current device's: the stream must run there
+        int cur = 0, sdev = 0;
+        PD_CHECK_CUDA(cudaGetDevice(&cur));
+        PD_CHECK_CUDA(cudaStreamGetDevice(s, &sdev));
+        PD_REQUIRE(sdev == cur, "the stream belongs to device %d, not the current device %d", sdev, cur);
+    }
     int32_t *flag = nullptr;
     PD_TRY(noalloc_scratch(&flag));
-    cudaStream_t s = (cudaStream_t)stream;
     GridDev d = make_dev(g);
     PD_CHECK_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), s));  // the array keeps the previous call's value
     const int bs = 256;
