@@ -53,7 +53,7 @@ def test_node_gradients_against_oracle(pd, prec, T, mr):
     st.reset(s0d, kd)
     gs, gk, R = st.adjoint(T, obs, torch.tensor(wts, device="cuda"), s0d, kd, ckpt_every=64)
     gs, gk, R = gs.cpu().numpy(), gk.cpu().numpy(), R.cpu().numpy()
-    tol = 1e-8 if prec == "fp64" else 2e-3
+    tol = 1e-8 if prec == "fp64" else 1e-4
     for b in range(B):
         m = core.Model(w, s0=s0[b].astype(np.float64), kappa=kap[b].astype(np.float64), dt=st.dt)
         ogs, ogk = m.adjoint(T, obs, wts[b])
@@ -179,3 +179,120 @@ def test_coefficient_gradient_against_central_differences(pd):
     st.close()
     fs.close()
     fk.close()
+
+
+def test_strength_coefficient_gradient_against_central_differences_softening(pd):
+    """Softening window (bonds past their elastic limit), strength KL
+    coefficients, FP64 path: the adjoint (pd_adjoint + pd_field_adjoint)
+    against central differences of the GPU's own forward run, h = 1e-3 on xi,
+    1e-4 relative. The fields enter in FP64 (pd_state_reset_f64, from the FP64
+    KL map), so the differences see no FP32 rounding of s0. A coefficient
+    counts only where the +-h runs take every bond's damage branch (kept,
+    set by the law, broken) at every step exactly as the base run does:
+    across a branch change the response has a kink and central differences do
+    not estimate the derivative. Those coefficients are reported."""
+    w = _case()
+    T = 300
+    g = w.grid
+    row, col = pd.build_neighbours(g)
+    st = pd.State(g, row, col, w.mat, w.bc, batch=1, precision=pd.PREC_FP64)
+    K = w.field.n_modes
+    Phi, lam = field.kl_separable(g, w.field.length, K)
+    xs = field.draw_xi(w.seed, 0, [0], K)
+
+    def s0_of(x):
+        return field.lognormal(field.gaussian(Phi, lam, x), w.field.mean, w.field.cov)[0]
+
+    obs = [T - 1, T // 2, T - 40]
+    wts = np.array([1.0, 0.5, -0.3])
+
+    def run(x):
+        """J and the per-step branch signature of every bond."""
+        st.reset_f64(torch.tensor(s0_of(x)[None], device="cuda"))
+        d_prev = torch.zeros(st.nb, dtype=torch.float64, device="cuda")
+        sig, R = [], []
+        for n in range(T):
+            R.append(float(st.step(1)[0, 0]))
+            d = st.store()[2][0]
+            sig.append(torch.cat([d > d_prev, d >= 1.0]).cpu().numpy())
+            d_prev = d
+        return sum(wt * R[o] for o, wt in zip(obs, wts)), np.stack(sig)
+
+    J0, sig0 = run(xs)
+    assert sig0[:, :st.nb].any(), "the window must contain softening"
+    # adjoint: node gradient on the GPU, then the GPU's KL chain
+    s0d = torch.tensor(s0_of(xs)[None], device="cuda")
+    st.reset_f64(s0d)
+    gs, _, _ = st.adjoint(T, obs, torch.tensor(wts[None], device="cuda"), s0d.float(), grad_kappa=False)
+    fs = pd.Field(g, 1, w.field)
+    gxi = fs.adjoint(0, torch.tensor(xs, device="cuda"), gs).cpu().numpy()[0]
+    assert np.abs(gxi).max() > 0
+    h = 1e-3
+    noise = 1e-12 * abs(J0) / h
+    checked, skipped = 0, []
+    for k in range(K):
+        p, q = xs.copy(), xs.copy()
+        p[0, k] += h
+        q[0, k] -= h
+        Jp, sp = run(p)
+        Jm, sm = run(q)
+        fd = (Jp - Jm) / (2 * h)
+        same = np.array_equal(sp, sig0) and np.array_equal(sm, sig0)
+        print(f"xi_s[{k}]: adjoint {gxi[k]:.9e} fd {fd:.9e} {'' if same else '(branch change within +-h)'}")
+        if not same:
+            skipped.append(k)
+            continue
+        checked += 1
+        assert abs(gxi[k] - fd) <= 1e-4 * abs(fd) + noise, (k, gxi[k], fd)
+    print(f"{checked} of {K} coefficients checked; branch changes within +-h: {skipped}")
+    assert checked >= K // 2
+    st.close()
+    fs.close()
+
+
+def test_mixed_adjoint_midsize_through_the_peak(pd):
+    """The 5 mm notched beam (3,500 nodes, 322,444 bonds; the MLMC level-0
+    workload) through its peak load, mixed precision with strength and
+    stiffness fields: node gradients of a weighted sum of reactions before,
+    at and after the peak against the oracle's FP64 adjoint on the same
+    fields. Reactions within 1e-5; the kappa-gradient within 1e-4 of its
+    largest entry at every node; the s0-gradient within 1e-4 of its largest
+    entry at all but 0.1 % of the nodes and within 1e-3 at every node. Near the
+    peak hundreds of bonds cross their elastic limit every step, and a bond
+    whose stretch lies within the FP32 trajectory's rounding of its limit at
+    some step takes the other branch of d = max(d, D(s)) than in the FP64 run:
+    its contribution to the s0-gradient of its two nodes then differs by the
+    whole term (the derivative is discontinuous there), while every other
+    node agrees. The count of such nodes and both norms are printed."""
+    w = W.beam_levels()[0]
+    g = w.grid
+    T = w.n_steps
+    row, col = pd.build_neighbours(g)
+    Phi, lam = field.kl_separable(g, w.field.length, w.field.n_modes)
+    s0 = np.ascontiguousarray(field.sample_field(w, Phi, lam, w.seed, 0, [0]), np.float32)
+    kap = np.ascontiguousarray(np.exp(0.1 * np.random.default_rng(4).standard_normal((1, g.n_nodes))), np.float32)
+    m = core.Model(w, s0=s0[0].astype(np.float64), kappa=kap[0].astype(np.float64))
+    r = m.run(T)
+    pk = int(np.argmax(r["reaction"]))
+    assert 0 < pk < T - 20, "the window must pass the peak"
+    obs = [T // 2, pk, T - 1]
+    wts = np.array([0.5, 1.0, -0.7])
+    ogs, ogk = m.adjoint(T, obs, wts)
+    st = pd.State(g, row, col, w.mat, w.bc, batch=1, precision=pd.PREC_MIXED)
+    assert abs(st.dt - m.dt) <= 1e-13 * m.dt
+    s0d, kd = torch.tensor(s0, device="cuda"), torch.tensor(kap, device="cuda")
+    st.reset(s0d, kd)
+    gs, gk, R = st.adjoint(T, obs, torch.tensor(wts[None], device="cuda"), s0d, kd, ckpt_every=100)
+    gs, gk, R = gs.cpu().numpy()[0], gk.cpu().numpy()[0], R.cpu().numpy()[0]
+    es = np.abs(gs - ogs).max() / np.abs(ogs).max()
+    ek = np.abs(gk - ogk).max() / np.abs(ogk).max()
+    es2 = np.linalg.norm(gs - ogs) / np.linalg.norm(ogs)
+    ek2 = np.linalg.norm(gk - ogk) / np.linalg.norm(ogk)
+    n_off = int((np.abs(gs - ogs) > 1e-4 * np.abs(ogs).max()).sum())
+    er = np.abs(R - r["reaction"][obs]).max() / np.abs(r["reaction"][obs]).max()
+    print(f"peak at step {pk}; grad_s0 err 2-norm {es2:.2e} max {es:.2e} (max {np.abs(ogs).max():.3e}, "
+          f"{n_off} of {g.n_nodes} nodes above 1e-4), grad_kappa err 2-norm {ek2:.2e} max {ek:.2e}, R err {er:.2e}")
+    st.close()
+    assert er <= 1e-5
+    assert ek <= 1e-4
+    assert n_off <= g.n_nodes // 1000 and es <= 1e-3

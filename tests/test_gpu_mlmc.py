@@ -200,6 +200,53 @@ def test_multi_state_run_equals_separate_runs(pd):
     fld.close()
 
 
+@pytest.mark.parametrize("level", [1, 2])
+def test_paired_launch_of_a_level_equals_separate_runs(pd, level):
+    """The benchmark hierarchy's coupled pairs (level 1: 28,000 + 3,500 nodes;
+    level 2: 224,000 + 28,000 nodes), two samples, both members in the same
+    launch shape: one launch per step covering both meshes gives the peaks,
+    steps and final states of two separate runs, bit for bit."""
+    import time
+
+    import torch
+    levels = W.beam_levels()
+    fw, cw = levels[level], levels[level - 1]
+    rf, cf = pd.build_neighbours(fw.grid)
+    rc, cc = pd.build_neighbours(cw.grid)
+    fld = pd.Field(fw.grid, 2, fw.field)
+    xi = pd.draw_xi(fw.seed, 1, torch.arange(2, dtype=torch.int64, device="cuda"), fw.field.n_modes)
+    ff, fc = fld.sample(1, xi, coarse=True)
+    shape = (4, 4, 1, 1, 0)
+    sf = pd.State(fw.grid, rf, cf, fw.mat, fw.bc, batch=2, schedule=shape)
+    sc = pd.State(cw.grid, rc, cc, cw.mat, cw.bc, batch=2, schedule=shape)
+    sf.reset(ff)
+    sc.reset(fc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sep = [sf.run_to_peak(fw.n_steps), sc.run_to_peak(cw.n_steps)]
+    torch.cuda.synchronize()
+    t_sep = time.perf_counter() - t0
+    u_sep = [sf.store()[0], sc.store()[0]]
+    sf.reset(ff)
+    sc.reset(fc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    multi = pd.run_to_peak_multi([sf, sc], [fw.n_steps, cw.n_steps])
+    torch.cuda.synchronize()
+    t_multi = time.perf_counter() - t0
+    u_multi = [sf.store()[0], sc.store()[0]]
+    print(f"level {level}: separate {t_sep:.3f} s, one launch per step {t_multi:.3f} s "
+          f"(peaks {multi[0][0].tolist()}, {multi[1][0].tolist()})")
+    for a, b in zip(sep, multi):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+    for a, b in zip(u_sep, u_multi):
+        assert torch.equal(a, b)
+    sf.close()
+    sc.close()
+    fld.close()
+
+
 def test_plane_mlmc_against_oracle(pd):
     """A two-level plane-stress hierarchy (one-layer grids, the field restricted
     over 2 x 2 in-plane children): per-sample pairs and the estimator."""
