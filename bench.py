@@ -41,10 +41,10 @@ WORKLOAD = ("notched 3-point-bending beam 175x50x50 mm, dx 2.5 mm (28,000 nodes,
             "lognormal KL strength field (64 modes, l = 10 mm), one sample per step, run to peak (<= 5,000 steps)")
 L2_FLUSH_BYTES = 256 << 20
 
-# DRAM bytes (read + write) of one k_step_stencil launch on this workload, from
-# the ncu capture summarised in profiles/k_step_stencil_beam28k_b1.md (cold L2),
-# valid while the kernel's sources are the ones captured (compared as code:
-# comments and whitespace do not count).
+# DRAM bytes (read + write) of one k_step_stencil launch on this workload, a
+# constant carried from an ncu capture of that launch (cold L2; not measured by
+# this program), reported only while the kernel's sources are the ones captured
+# (compared as code: comments and whitespace do not count).
 NCU_STEP_TRAFFIC = {
     "bytes": 16_766_208 + 512,
     "sources": {
@@ -145,7 +145,8 @@ def dist_env():
 
 def cpu_baseline_leg(n_steps: int = 300):
     """The FP64 oracle as it stands, on the same beam and field recipe, for a
-    bounded number of explicit steps on one host core."""
+    bounded number of explicit steps on the host cores (its force loop runs
+    the nodes on OpenMP threads; the count used is reported)."""
     import pd_workloads as W
     from oracle import core, field
     w = W.beam()
@@ -156,9 +157,10 @@ def cpu_baseline_leg(n_steps: int = 300):
     r = m.run(n_steps)
     el = time.perf_counter() - t0
     bu = r["n_done"] * m.nb
-    return {"value": bu / el, "unit": METRIC, "cores": 1, "kind": "oracle",
+    nt = core.max_threads()
+    return {"value": bu / el, "unit": METRIC, "cores": nt, "kind": "oracle",
             "sample": f"first {n_steps} explicit steps of sample 0 (seed {w.seed}) of the {w.grid.nx}x{w.grid.ny}x"
-                      f"{w.grid.nz} notched beam, FP64, single thread ({el:.1f} s)"}
+                      f"{w.grid.nz} notched beam, FP64, {nt} OpenMP threads ({el:.1f} s wall)"}
 
 
 def mlmc_leg(pd, W, dist, tune_steps: int = 10, tol: float = 1e-3):
@@ -230,6 +232,63 @@ def mlmc_leg(pd, W, dist, tune_steps: int = 10, tol: float = 1e-3):
     }
 
 
+def mlmc_deliver_leg(pd, W, tol: float = 1e-3, q_pilot: float | None = None, tune_steps: int = 10):
+    """Algorithm MLMC (mlmc_adaptive) on the notched-beam hierarchy to a
+    sampling tolerance: eps = tol |Q_hat| (Q_hat from a pilot estimate), eps_s
+    = eps / sqrt(2) (Section 4.2: half the squared error budget to sampling,
+    half to bias), warm-up N* = 100 per level, costs measured on the GPU.
+    Reported beside it: the bias estimate of Eq. bias_error, |Y_hat_L| /
+    (m^alpha - 1) with m = 8 and alpha fitted from the level means
+    (Eq. alpha_convergence_mlmc), and the plain path (one sample per launch)
+    measured on 32 / 16 / 4 samples per level, with the time it would take
+    for the same samples per level."""
+    import math
+
+    import torch
+    lv = W.beam_levels()
+    a = dict(grids=[w.grid for w in lv], bcs=[w.bc for w in lv], max_steps=[w.n_steps for w in lv],
+             mat=lv[0].mat, field=lv[0].field, seed=lv[0].seed)
+    if q_pilot is None:
+        q_pilot = pd.mlmc_estimate(n_samples=[256, 32, 4], batch=256, first_sample=[3_000_000] * 3,
+                                   tune_steps=tune_steps, **a)["q_ml"]
+    eps = tol * abs(q_pilot)
+    eps_s = eps / math.sqrt(2.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = pd.mlmc_adaptive(batch=1024, eps_s=eps_s, eps_b=eps_s, m_dof=8.0, alpha=1.0, n_star=100,
+                         tune_steps=tune_steps, first_sample=[4_000_000] * 3, **a)
+    wall = time.perf_counter() - t0
+    means = [l_["mean"] for l_ in r["levels"]]
+    # alpha from |Y_l| ~ M_l^-alpha over the correction levels (M_l = 8^l)
+    xs = [l * math.log(8.0) for l in range(1, len(means))]
+    ys = [math.log(abs(m)) for m in means[1:]]
+    if len(xs) >= 2:
+        mx, my = sum(xs) / len(xs), sum(ys) / len(ys)
+        alpha = -sum((x - mx) * (y - my) for x, y in zip(xs, ys)) / sum((x - mx) ** 2 for x in xs)
+    else:
+        alpha = float("nan")
+    bias = abs(means[-1]) / (8.0 ** alpha - 1.0) if alpha > 0 else float("inf")
+    n = [l_["n"] for l_ in r["levels"]]
+    plain_n = [32, 16, 4]
+    plain = pd.mlmc_estimate(n_samples=plain_n, batch=1, first_sample=[5_000_000] * 3, **a)
+    plain_cost = [l_["cost_s"] / l_["n"] for l_ in plain["levels"]]
+    plain_time = sum(k * c for k, c in zip(n, plain_cost))
+    return {
+        "workload": "notched beam hierarchy dx 5 / 2.5 / 1.25 mm (3,500 / 28,000 / 224,000 nodes), coupled pairs, "
+                    "Algorithm MLMC to a sampling tolerance",
+        "tol_rel": tol, "q_pilot": q_pilot, "eps": eps, "eps_s": eps_s, "levels_used": r["L"] + 1,
+        "n_per_level": n, "wall_s": wall, "samples": sum(n), "samples_per_s": sum(n) / wall,
+        "q_ml": r["q_ml"], "sampling_rmse": math.sqrt(max(r["var_ml"], 0.0)),
+        "sampling_rel_rmse": math.sqrt(max(r["var_ml"], 0.0)) / abs(r["q_ml"]),
+        "level_means": means, "level_vars": [l_["var"] for l_ in r["levels"]],
+        "cost_per_sample_s": [l_["cost_s"] / max(l_["n"], 1) for l_ in r["levels"]],
+        "alpha_fit": alpha, "bias_estimate": bias, "bias_test_passed": bias < eps / math.sqrt(2.0),
+        "plain_sample": f"{plain_n} samples per level, one per launch (measured)",
+        "plain_cost_per_sample_s": plain_cost, "plain_time_for_same_n_s": plain_time,
+        "speedup_vs_plain": plain_time / wall,
+    }
+
+
 def sweep_leg(pd, W, hbm, steps: int = 10, warmup: int = 3):
     """Size-effect sweep, batched (64 samples per launch): geometrically similar
     notched beams D = 50 ... 400 mm at dx = 2.5 mm (up to 1.79M nodes, 204M
@@ -271,6 +330,62 @@ def sweep_leg(pd, W, hbm, steps: int = 10, warmup: int = 3):
             "timed": f"{steps} explicit steps after {warmup} from rest, per size", "sizes": out}
 
 
+def size_effect_leg(pd, W, hbm, sizes=(50.0, 100.0, 200.0, 400.0), max_steps: int = 6000):
+    """The statistical size-effect study (Section 6): geometrically similar
+    notched beams of depth D (span 3D, length 3.5D, thickness 50 mm, dx = 2.5
+    mm), 64 lognormal strength samples per size, every sample run to its peak
+    load in one batched launch sequence (pd_run_to_peak). Reported per size:
+    the mean and standard deviation of the nominal strength
+    sigma_N = 3 P S / (2 t D^2) (three-point bending; P the peak load, S the
+    span, t the thickness), and throughput over the whole run:
+    bond-updates/s and the algorithmic-bytes fraction of the copy bandwidth."""
+    import statistics as stats
+
+    import torch
+    out = []
+    for D in sizes:
+        w = W.sweep(D)
+        g = w.grid
+        row, col = pd.build_neighbours(g)
+        nb = int(col.numel())
+        B = w.batch
+        fld = pd.Field(g, 1, w.field)
+        xi = pd.draw_xi(w.seed, 0, torch.arange(B, dtype=torch.int64, device="cuda"), w.field.n_modes)
+        s0 = fld.sample(0, xi)
+        st = pd.State(g, row, col, w.mat, w.bc, batch=B)
+        st.reset(s0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pk, ps, nd = st.run_to_peak(max_steps)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        pk, ps, nd = pk.cpu().numpy(), ps.cpu().numpy(), nd.cpu().numpy()
+        span = 3.0 * D * 1e-3
+        t = g.nz * g.dx
+        sig = [1.5 * float(p) * span / (t * (D * 1e-3) ** 2) / 1e6 for p in pk]
+        bu = float(nd.sum()) * nb
+        steps_max = int(nd.max())
+        # history and node state of every sample-step taken, the index once per launch
+        alg = float(nd.sum()) * (nb * 4.0 + g.n_nodes * 108.0) + steps_max * nb * 4.0
+        out.append({"D_mm": D, "nodes": g.n_nodes, "bonds": nb, "samples": B,
+                    "sigma_N_mean_MPa": stats.fmean(sig), "sigma_N_std_MPa": stats.stdev(sig),
+                    "peak_mean_N": float(pk.mean()), "peak_step_mean": float(ps.mean()),
+                    "steps_mean": float(nd.mean()), "steps_max": steps_max, "wall_s": wall,
+                    "bond_updates_per_s": bu / wall, "algorithmic_gbs": alg / wall / 1e9,
+                    "hbm_frac": alg / wall / 1e9 / hbm})
+        st.close()
+        fld.close()
+        del row, col, xi, s0, st, fld
+        torch.cuda.empty_cache()
+    return {"workload": "size-effect study: notched beams D = " + "/".join(str(int(d)) for d in sizes) +
+                        " mm (span 3D, length 3.5D, thickness 50 mm), dx 2.5 mm, 64 samples per size, "
+                        f"run to peak (<= {max_steps} steps)",
+            "sigma_N": "3 P S / (2 t D^2)",
+            "hbm_frac_note": "algorithmic bytes of the sample-steps taken over the whole-run wall time (host "
+                             "polls once per 64 steps included)",
+            "sizes": out}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -279,7 +394,7 @@ def run_reference(args):
     from oracle import core, field
     w = W.beam()
     Phi, lam = field.kl_separable(w.grid, w.field.length, w.field.n_modes)
-    per_step = 40
+    per_step = 200
     total_bu, total_t = 0, 0.0
     for k in range(args.warmup + args.steps):
         s0 = field.sample_field(w, Phi, lam, w.seed, 0, [k])[0]
@@ -295,8 +410,9 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "sample": f"{per_step} explicit steps of each sample"},
-            "cpu_baseline": {"value": val, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} explicit steps per bench step, FP64 oracle, one thread"},
+            "cpu_baseline": {"value": val, "unit": METRIC, "cores": core.max_threads(), "kind": "oracle",
+                             "sample": f"{per_step} explicit steps per bench step, FP64 oracle, "
+                                       f"{core.max_threads()} OpenMP threads"},
             "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -312,6 +428,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mlmc", action="store_true", help="skip the MLMC hierarchy leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the size-effect sweep leg")
+    ap.add_argument("--size-effect", action="store_true",
+                    help="run the size-effect study: D = 50..400 mm x 64 samples to their peaks (minutes)")
+    ap.add_argument("--mlmc-deliver", type=float, default=0.0,
+                    help="run Algorithm MLMC to this relative sampling tolerance (e.g. 1e-3; minutes of GPU time)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -458,8 +578,9 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "samples_per_step": 1, "mean_explicit_steps": nd_tot / args.steps,
                    "l2": "flushed between timed steps (256 MB write outside the events)",
-                   "precision": "FP32 bond arithmetic; compensated FP32 / double-float nodal sums and integration; "
-                                "FP64 reaction and estimator sums",
+                   "precision": "FP32 bond kinematics and forces (positions gathered in FP32, cell units); "
+                                "nodal sums FP32 in groups of 8 added by TwoSum into double-float; double-float "
+                                "integration; FP64 reaction reduction and estimator sums",
                    "mesh": "neighbour list built once before timing"},
         "samples_per_s": ws * args.steps / t_max,
         "e2e": e2e,
@@ -467,8 +588,10 @@ def main():
         "clocks": clk,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": _captured_traffic(), "peak_kind": peak_kind, "kernel": "k_step_stencil",
-                     "traffic_note": "ncu dram__bytes_read+write of one launch, cold L2 (warm, as in the "
-                                     "timed steps, the one-sample working set stays in L2)",
+                     "traffic_note": "ncu dram__bytes_read+write of one launch, cold L2, carried as a constant "
+                                     "from a capture of the same kernel sources (not measured in this run; null "
+                                     "once the sources differ); warm, as in the timed steps, the one-sample "
+                                     "working set stays in L2",
                      "algorithmic_bytes_per_launch": alg_bytes, "launch_us": per_launch_ms * 1e3},
         "batched": batched,
     }
@@ -476,6 +599,11 @@ def main():
         line["mlmc"] = mlmc_leg(pd, W, dist)
     if not args.no_sweep and ws == 1:
         line["sweep"] = sweep_leg(pd, W, hbm)
+    if args.size_effect and ws == 1:
+        line["size_effect"] = size_effect_leg(pd, W, hbm)
+    if args.mlmc_deliver > 0 and ws == 1:
+        line["mlmc_deliver"] = mlmc_deliver_leg(pd, W, args.mlmc_deliver,
+                                                q_pilot=(line.get("mlmc") or {}).get("q_ml"))
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_leg()
     if rank == 0:
