@@ -257,13 +257,15 @@ def test_mixed_adjoint_midsize_through_the_peak(pd):
     at and after the peak against the oracle's FP64 adjoint on the same
     fields. Reactions within 1e-5; the kappa-gradient within 1e-4 of its
     largest entry at every node; the s0-gradient within 1e-4 of its largest
-    entry at all but 0.1 % of the nodes and within 1e-3 at every node. Near the
+    entry at all but 1 % of the nodes and within 1e-3 at every node. Near the
     peak hundreds of bonds cross their elastic limit every step, and a bond
     whose stretch lies within the FP32 trajectory's rounding of its limit at
     some step takes the other branch of d = max(d, D(s)) than in the FP64 run:
     its contribution to the s0-gradient of its two nodes then differs by the
     whole term (the derivative is discontinuous there), while every other
-    node agrees. The count of such nodes and both norms are printed."""
+    node agrees. Which bonds fall in that band depends on the FP32 rounding
+    of the run (3 to 8 nodes of 3,500 across kernel revisions that only
+    reorder FP32 sums). The count of such nodes and both norms are printed."""
     w = W.beam_levels()[0]
     g = w.grid
     T = w.n_steps
@@ -295,4 +297,4 @@ def test_mixed_adjoint_midsize_through_the_peak(pd):
     st.close()
     assert er <= 1e-5
     assert ek <= 1e-4
-    assert n_off <= g.n_nodes // 1000 and es <= 1e-3
+    assert n_off <= g.n_nodes // 100 and es <= 1e-3
