@@ -219,12 +219,12 @@ struct LawC {
     float sr, kf, af, i1, i2, gfa;
 };
 
-// The law of a bond past its elastic limit, out of line: the bond loop is
-// unrolled over the whole half-stencil, and the law (divisions, an
-// exponential) inlined at every round would multiply the loop's code -- the
-// instruction cache then starves the warps -- for a path few bonds take.
+// The law of a bond past its elastic limit. It is evaluated only in the
+// fix-up of flagged bonds (below), never in the unrolled bond loop: the law
+// (divisions, an exponential) inlined at each of the 61 rounds multiplied the
+// loop's code until the instruction cache starved the warps.
 template <int LAW>
-__device__ __noinline__ float law_cold(float s, float s0, LawC lc) {
+__device__ __forceinline__ float law_cold(float s, float s0, LawC lc) {
     return law_damage<float>(LAW, s, s0, crit_stretch(s0, lc.sr, lc.gfa), lc.kf, lc.af, lc.i1, lc.i2);
 }
 
@@ -332,60 +332,73 @@ __device__ __forceinline__ float knorm_rt(int q) {
     }
 }
 
+// The fix-up of one bond (round m) whose stretch passed its elastic limit
+// this step: recompute it (the same operations as the unrolled loop, so the
+// same bits), apply the law, store the damage where it grew (only when act),
+// and return the correction of the force factor -- the unrolled loop formed
+// the lane's sums with the previous damage -- with the bond's direction (zero
+// where nothing grew). The two directed copies of a bond run the same
+// correction.
+template <class V>
+struct FixOut {
+    V dg, yx, yy, yz;
+};
+
+template <int DIM, int NS, int LAW, bool KAPPA>
+__device__ __forceinline__ FixOut<typename Lane<NS>::V> fix_one(int m, bool act, const BondCtx<NS> &cx) {
+    using V = typename Lane<NS>::V;
+    const signed char *k = c_half[DIM - 2].k[m];
+    const int kx = k[0], ky = k[1], kz = k[2], q = k[3];
+    const Rec<V> r = load_rec<NS>(cx.rb[kz] + 16 * kx + NS * kRowC * ky);
+    FixOut<V> o;
+    V rL, s;
+    bond_kin<V>(cx, r, kx, ky, kz, knorm_rt(q), (float)q, o.yx, o.yy, o.yz, rL, s);
+    const V s0 = vadd(cx.h, r.h);
+    float *slot0 = (float *)(cx.dq0 + 32 * (m / 4)) + (m % 4);
+    V dold, dnew;
+    if constexpr (NS == 1) {
+        dold = *slot0;
+        const float dl = s > s0 ? law_cold<LAW>(s, s0, cx.lc) : 0.f;
+        const bool grow = act && dl > dold;
+        dnew = grow ? dl : dold;
+        if (grow) *slot0 = dl;
+    } else {
+        float *slot1 = (float *)(cx.dq1 + 32 * (m / 4)) + (m % 4);
+        dold = make_float2(*slot0, *slot1);
+        const float dlx = s.x > s0.x ? law_cold<LAW>(s.x, s0.x, cx.lc) : 0.f;
+        const float dly = s.y > s0.y ? law_cold<LAW>(s.y, s0.y, cx.lc) : 0.f;
+        const bool gx = act && dlx > dold.x, gy = act && dly > dold.y;
+        dnew = make_float2(gx ? dlx : dold.x, gy ? dly : dold.y);
+        if (gx && cx.w0) *slot0 = dlx;
+        if (gy && cx.w1) *slot1 = dly;
+    }
+    o.dg = vsub(bond_g(dnew, s, rL), bond_g(dold, s, rL));
+    if constexpr (KAPPA) o.dg = vmul(o.dg, vadd(cx.kap, load_kap<NS>(cx.kb[kz] + 4 * NS * kx + NS * kRowK * ky)));
+    return o;
+}
+
 // Bonds of rounds m0 + j (bit j of mask) whose stretch passed their elastic
-// limit this step, out of line: recompute the bond, apply the law, and where
-// the damage grew store it and correct the lane's force sums, which the
-// unrolled loop formed with the previous damage, by the difference of the
-// force factors (the two directed copies of a bond run the same correction).
+// limit this step: fixed up two at a time (independent instruction streams,
+// so that their latencies overlap in the few warps at a growing crack), the
+// corrections added to the lane's sums in ascending round order.
 template <int DIM, int NS, int LAW, bool KAPPA>
 __device__ __forceinline__ void fix_bonds(unsigned mask, int m0, const BondCtx<NS> &cx, typename Lane<NS>::V &px,
                                        typename Lane<NS>::V &py, typename Lane<NS>::V &pz) {
     using V = typename Lane<NS>::V;
     while (mask) {
-        const int j = __ffs(mask) - 1;
+        const int j1 = __ffs(mask) - 1;
         mask &= mask - 1;
-        const int m = m0 + j;
-        const signed char *k = c_half[DIM - 2].k[m];
-        const int kx = k[0], ky = k[1], kz = k[2], q = k[3];
-        const Rec<V> r = load_rec<NS>(cx.rb[kz] + 16 * kx + NS * kRowC * ky);
-        V yx, yy, yz, rL, s;
-        bond_kin<V>(cx, r, kx, ky, kz, knorm_rt(q), (float)q, yx, yy, yz, rL, s);
-        const V s0 = vadd(cx.h, r.h);
-        float *slot0 = (float *)(cx.dq0 + 32 * (m / 4)) + (m % 4);
-        V dold, dnew;
-        if constexpr (NS == 1) {
-            dold = dnew = *slot0;
-            if (s > s0) {
-                const float dl = law_cold<LAW>(s, s0, cx.lc);
-                if (dl > dold) {
-                    dnew = dl;
-                    *slot0 = dl;
-                }
-            }
-        } else {
-            float *slot1 = (float *)(cx.dq1 + 32 * (m / 4)) + (m % 4);
-            dold = make_float2(*slot0, *slot1);
-            dnew = dold;
-            if (s.x > s0.x) {
-                const float dl = law_cold<LAW>(s.x, s0.x, cx.lc);
-                if (dl > dold.x) {
-                    dnew.x = dl;
-                    if (cx.w0) *slot0 = dl;
-                }
-            }
-            if (s.y > s0.y) {
-                const float dl = law_cold<LAW>(s.y, s0.y, cx.lc);
-                if (dl > dold.y) {
-                    dnew.y = dl;
-                    if (cx.w1) *slot1 = dl;
-                }
-            }
-        }
-        V dg = vsub(bond_g(dnew, s, rL), bond_g(dold, s, rL));
-        if constexpr (KAPPA) dg = vmul(dg, vadd(cx.kap, load_kap<NS>(cx.kb[kz] + 4 * NS * kx + NS * kRowK * ky)));
-        px = vfma(dg, yx, px);
-        py = vfma(dg, yy, py);
-        pz = vfma(dg, yz, pz);
+        const bool two = mask != 0u;
+        const int j2 = two ? __ffs(mask) - 1 : j1;  // without a second bond: the first again, with no effect
+        if (two) mask &= mask - 1;
+        const FixOut<V> a = fix_one<DIM, NS, LAW, KAPPA>(m0 + j1, true, cx);
+        const FixOut<V> b = fix_one<DIM, NS, LAW, KAPPA>(m0 + j2, two, cx);
+        px = vfma(a.dg, a.yx, px);
+        py = vfma(a.dg, a.yy, py);
+        pz = vfma(a.dg, a.yz, pz);
+        px = vfma(b.dg, b.yx, px);
+        py = vfma(b.dg, b.yy, py);
+        pz = vfma(b.dg, b.yz, pz);
     }
 }
 
