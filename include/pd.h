@@ -168,12 +168,10 @@ PD_API int pd_build_neighbours(const pd_grid *g, int32_t *row_ptr, int32_t *col,
  * call cudaMalloc, e.g. code running under an external memory manager that
  * owns all device memory). The one word of device scratch (the scan's
  * overflow flag) lives in a 256-byte static device array that every GPU
- * loading the library holds until exit; it is cleared on every call. The
- * first call on a device looks up the array's device address (with that
- * device current) and keeps it for the life of the process, so make that
- * first call before any stream capture, and do not use the library across a
- * cudaDeviceReset of that device. The stream must belong to the current
- * device (PD_ERR_ARG otherwise). Calls that overlap on the GPU share the
+ * loading the library holds until exit; it is cleared on every call. Every
+ * call looks up the array's address on the current device, so no address
+ * outlives a cudaDeviceReset. The stream must belong to the current device
+ * (PD_ERR_ARG otherwise). Calls that overlap on the GPU share the
  * array and race. Sizes: at most 2^31 - 2 nodes and 2^31 - 1 bonds; larger
  * grids return PD_ERR_ARG (a count-only call detects the bond overflow).
  * Arguments, outputs, synchronisation and errors are those of

@@ -9,7 +9,6 @@
 #include <string.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "pd_internal.cuh"
 
@@ -239,28 +238,19 @@ extern "C" int pd_bc_codes(const pd_grid *g, const pd_bc *bc, uint8_t *codes, pd
 // The build needs one word of device scratch beyond its inputs and outputs:
 // the overflow flag of the row-pointer scan. pd_build_neighbours takes it from
 // cudaMalloc on every call; this variant keeps it in a file-scope device array
-// instead, for callers that cannot allocate device memory. Device addresses of
-// the array are looked up once per device (cudaGetSymbolAddress, with that
-// device current) on the first call made on that device.
+// instead, for callers that cannot allocate device memory. Its address is
+// looked up on every call with the current device (cudaGetSymbolAddress), so a
+// context torn down by cudaDeviceReset leaves no stale pointer behind.
 static __device__ __align__(256) int32_t g_noalloc_scratch[64];  // 256 bytes; word 0 = scan overflow flag
 
 static int noalloc_scratch(int32_t **out) {
-    static std::mutex mu;
-    static int32_t *addr[64] = {nullptr};
-    int dev = 0;
-    PD_CHECK_CUDA(cudaGetDevice(&dev));
-    PD_REQUIRE(dev >= 0 && dev < 64, "device index %d out of range for the static scratch table", dev);
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) {
-            set_error("cudaGetSymbolAddress of the neighbour-build scratch failed: %s", cudaGetErrorString(e));
-            return PD_ERR_CUDA;
-        }
-        addr[dev] = (int32_t *)p;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        set_error("cudaGetSymbolAddress of the neighbour-build scratch failed: %s", cudaGetErrorString(e));
+        return PD_ERR_CUDA;
     }
-    *out = addr[dev];
+    *out = (int32_t *)p;
     return PD_OK;
 }
 
