@@ -20,6 +20,28 @@ struct df {
     float hi, lo;
 };
 
+// Division of 0 <= n < 2^31 by a launch constant d as a multiply and a shift:
+// with c = ceil(log2 d), s = 31 + c and m = ceil(2^s / d) < 2^32,
+// n m / 2^s = n / d + n (m d - 2^s) / (d 2^s), and the second term is below
+// 2^-c <= 1/d, so it never carries the quotient past the next integer.
+struct FastDiv {
+    uint32_t m;
+    int s;
+    int d;
+};
+
+inline FastDiv fastdiv_make(int d) {
+    int c = 0;
+    while ((1ll << c) < (long long)d) ++c;
+    const int s = 31 + c;
+    const unsigned long long m = ((1ull << s) + (unsigned long long)d - 1ull) / (unsigned long long)d;
+    return FastDiv{(uint32_t)m, s, d};
+}
+
+__device__ __forceinline__ int fdiv(int n, const FastDiv &f) {
+    return (int)(((unsigned long long)(uint32_t)n * f.m) >> f.s);
+}
+
 struct StepArgs {
     long long N;
     long long n_slices;
@@ -72,6 +94,9 @@ struct StepArgs {
     int st_wpb;      // stencil path: row pairs per brick
     float dxf;       // dx in FP32
     float4 *grec0, *grec1;  // stencil path: gather records (u / dx in FP32, s0 / 2) by step parity
+    float4 *grecR0, *grecR1;  // the same point-reflected (node i of a sample at N - 1 - i)
+    FastDiv fd_grp1, fd_grp2;   // stencil path: sample groups per brick with 1 and 2 samples per block
+    FastDiv fd_nbx, fd_nby, fd_by;  // bricks along x, along y, brick rows along y
     df idx_df;              // stencil path: 1 / dx as double-float
     float L0q[10];   // sqrt(q) dx in FP32, q = |k|^2 (stencil path)
     double cV;  // micromodulus x node volume
@@ -90,6 +115,7 @@ struct StepArgs {
 struct StepPair {
     StepArgs a[2];
     int nblk0;
+    StencilMaps t[2];
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -321,13 +347,12 @@ __device__ __forceinline__ void reaction_defer(const StepArgs &a, double Rloc, i
 
 // End of a step kernel in a reaction brick (one holding prescribed DOFs, or
 // brick 0), called by every warp of the block with all lanes active: the
-// reaction sum (sum over prescribed DOFs of -F sign, double-float) is reduced
+// reaction sum (sum over prescribed DOFs of -F sign, FP64) is reduced in FP64
 // along fixed trees -- warp, the block's warps in order (by the block's last
 // warp to finish), the reaction bricks of the sample in order (by the
 // sample's last reaction block) -- which then updates the run bookkeeping
 // from the run view that every block of the launch holds (and publishes the
 // previous step's reaction if this launch reduced it).
-// The whole reduction is FP64.
 __device__ __forceinline__ void reaction_finish(const StepArgs &a, double Rloc, int b, int blk, int warp, int lane,
                                                 int nwarps, double *red, unsigned *s_cnt, const RunView &rv) {
     if (__any_sync(0xffffffffu, Rloc != 0.0)) Rloc = warp_sum(Rloc);

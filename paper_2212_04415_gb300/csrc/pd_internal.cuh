@@ -2,6 +2,7 @@
 // (error plumbing, small device helpers, the state layout).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -68,6 +69,14 @@ __host__ __device__ __forceinline__ int32_t pack_coord(int ix, int iy, int iz) {
 }  // namespace pdi
 
 // Opaque handles (definitions shared between translation units).
+// Tensor maps (TMA) of the stencil step's staged box, by step parity: the
+// gather records [B][nz][ny][nx] x 4 floats and their point-reflected copy,
+// in boxes of 4 x 14 x (by + 6) x (bz + z-halo) floats.
+struct StencilMaps {
+    CUtensorMap rec[2];
+    CUtensorMap ref[2];
+};
+
 struct pd_state {
     pd_grid g;
     pd_material mat;
@@ -108,6 +117,8 @@ struct pd_state {
     int64_t st_len;         // damage slots per sample
     float *st_tmpl;         // [st_len]: 0 for real bonds, 1 for absent (broken) slots
     float4 *grec[2];        // gather records by step parity, [B][N]: (u / dx rounded to FP32, s0 / 2)
+    float4 *grecR[2];       // the same point-reflected: node i of a sample at N - 1 - i
+    StencilMaps st_maps;    // TMA maps of the staged box over grec and grecR
     int16_t *st_box;        // [7^3]: stencil code 2 m + t of an offset, -1 outside
     int32_t *col_csr;       // CSR copy for damage load/store
     // per-sample state

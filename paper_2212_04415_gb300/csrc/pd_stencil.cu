@@ -29,16 +29,20 @@ __device__ __forceinline__ long long slot_of(int i, int code, int nx, int ny, in
 }
 
 // Gather records of both parities from the state's double-float records:
-// (u / dx rounded to FP32, s0 / 2).
-__global__ void k_stencil_grec(long long NB, const float4 *rec0, const float4 *rec1, df idx, float4 *g0, float4 *g1) {
+// (u / dx rounded to FP32, s0 / 2), and the same point-reflected (node i of a
+// sample at N - 1 - i).
+__global__ void k_stencil_grec(long long N, long long NB, const float4 *rec0, const float4 *rec1, df idx, float4 *g0,
+                               float4 *g1, float4 *r0, float4 *r1) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= NB) return;
+    const long long b = t / N, i = t - b * N;
     for (int p = 0; p < 2; ++p) {
         const float4 *rc = p ? rec1 : rec0;
         const float4 h = rc[t], l = rc[NB + t];
         const float4 o = make_float4(df_mul(df{h.x, l.x}, idx).hi, df_mul(df{h.y, l.y}, idx).hi,
                                      df_mul(df{h.z, l.z}, idx).hi, 0.5f * h.w);
         (p ? g1 : g0)[t] = o;
+        (p ? r1 : r0)[b * N + (N - 1 - i)] = o;
     }
 }
 
@@ -133,12 +137,50 @@ unsigned blocks_of(long long n) { return (unsigned)((n + 255) / 256); }
 // Dynamic shared memory of a launch: the upper and the reflected lower copy
 // of the staged records (BZ + halo layers each), the same for kappa when a
 // stiffness field is set, and the partial sums of Q > 1 parts.
+// Dynamic shared memory of a launch: the two record copies, each rounded up to
+// 128 bytes (TMA destinations), the kappa copies, the parts' partial sums,
+// and 128 bytes to align the box.
 size_t stencil_smem(const pd_state *st, int ns, bool kappa) {
     const int hz = st->st_dim == 3 ? Sten<3>::kHaloZ : Sten<2>::kHaloZ;
     const size_t rows = (size_t)(st->by + 2 * kHalo) * (st->bz + hz);
-    size_t b = 2 * rows * ns * kRowC;
+    size_t b = 2 * ((rows * ns * kRowC + 127) & ~(size_t)127) + 128;
     if (kappa) b += 2 * rows * ns * kRowK;
     return b + (size_t)(st->st_q - 1) * st->st_wpb * 16 * 6 * ns * sizeof(float);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn tiled_encoder() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// Map of a [B][nz][ny][nx] array of 4-float records, read in boxes of 14 cells
+// x Wy rows x Zp layers of one sample; cells outside the grid read as zero.
+static int encode_box_map(CUtensorMap *tm, float4 *base, const pd_state *st, int Wy, int Zp) {
+    EncodeTiledFn enc = tiled_encoder();
+    PD_REQUIRE(enc != nullptr, "cuTensorMapEncodeTiled is unavailable");
+    const cuuint64_t nx = (cuuint64_t)st->g.nx, ny = (cuuint64_t)st->g.ny, nz = (cuuint64_t)st->g.nz;
+    const cuuint64_t dims[5] = {4, nx, ny, nz, (cuuint64_t)st->B};
+    const cuuint64_t strides[4] = {16, 16 * nx, 16 * nx * ny, 16 * nx * ny * nz};
+    const cuuint32_t box[5] = {4, (cuuint32_t)kWx, (cuuint32_t)Wy, (cuuint32_t)Zp, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, base, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    PD_REQUIRE(r == CUDA_SUCCESS, "cuTensorMapEncodeTiled failed for the stencil box (%d)", (int)r);
+    return PD_OK;
 }
 
 bool stencil_applicable(const pd_state *st) {
@@ -221,6 +263,16 @@ int stencil_build(pd_state *st, const int32_t *col) {
     PD_TRY(dalloc(&st->st_tmpl, st->st_len));
     PD_TRY(dalloc(&st->grec[0], (size_t)st->B * N));
     PD_TRY(dalloc(&st->grec[1], (size_t)st->B * N));
+    PD_TRY(dalloc(&st->grecR[0], (size_t)st->B * N));
+    PD_TRY(dalloc(&st->grecR[1], (size_t)st->B * N));
+    {
+        const int Wy = st->by + 2 * kHalo;
+        const int Zp = st->bz + (st->st_dim == 3 ? Sten<3>::kHaloZ : Sten<2>::kHaloZ);
+        for (int p = 0; p < 2; ++p) {
+            PD_TRY(encode_box_map(&st->st_maps.rec[p], st->grec[p], st, Wy, Zp));
+            PD_TRY(encode_box_map(&st->st_maps.ref[p], st->grecR[p], st, Wy, Zp));
+        }
+    }
     // every slot starts as an absent (broken) bond; the slots of real bonds are cleared
     k_fill_float<<<blocks_of(st->st_len), 256>>>(st->st_tmpl, st->st_len, 1.0f);
     PD_CHECK_LAUNCH();
@@ -239,8 +291,9 @@ int stencil_build(pd_state *st, const int32_t *col) {
 
 int stencil_refresh_grec(pd_state *st, cudaStream_t s) {
     const long long NB = st->N * st->B;
-    k_stencil_grec<<<blocks_of(NB), 256, 0, s>>>(NB, (const float4 *)st->rec[0], (const float4 *)st->rec[1],
-                                                 df_split(1.0 / st->g.dx), st->grec[0], st->grec[1]);
+    k_stencil_grec<<<blocks_of(NB), 256, 0, s>>>(st->N, NB, (const float4 *)st->rec[0], (const float4 *)st->rec[1],
+                                                 df_split(1.0 / st->g.dx), st->grec[0], st->grec[1], st->grecR[0],
+                                                 st->grecR[1]);
     PD_CHECK_LAUNCH();
     return PD_OK;
 }
@@ -248,7 +301,14 @@ int stencil_refresh_grec(pd_state *st, cudaStream_t s) {
 void stencil_fill_args(const pd_state *st, StepArgs &a) {
     a.grec0 = st->grec[0];
     a.grec1 = st->grec[1];
+    a.grecR0 = st->grecR[0];
+    a.grecR1 = st->grecR[1];
     a.idx_df = df_split(1.0 / st->g.dx);
+    a.fd_grp1 = fastdiv_make(st->B);
+    a.fd_grp2 = fastdiv_make((st->B + 1) / 2);
+    a.fd_nbx = fastdiv_make(st->nbx);
+    a.fd_nby = fastdiv_make(st->nby);
+    a.fd_by = fastdiv_make(st->by);
 }
 
 int stencil_reset_damage(pd_state *st, cudaStream_t s) {
@@ -295,6 +355,8 @@ int stencil_launch_pair(const pd_state *s0, const StepArgs &a0, const pd_state *
     g.a[0] = a0;
     g.a[1] = a1;
     g.nblk0 = (int)s0->n_bricks * s0->B;
+    g.t[0] = s0->st_maps;
+    g.t[1] = s1->st_maps;
     const unsigned grid = (unsigned)g.nblk0 + (unsigned)s1->n_bricks * (unsigned)s1->B;
     const size_t smem = std::max(stencil_smem(s0, 1, s0->has_kappa), stencil_smem(s1, 1, s1->has_kappa));
     pick_pair(s0->st_dim, s0->st_q, s0->mat.law, s0->has_kappa)<<<grid, 32 * s0->st_wpb * s0->st_q, smem, s>>>(g);
@@ -306,7 +368,7 @@ int stencil_launch(const pd_state *st, const StepArgs &a, bool force_only, cudaS
     const int ns = force_only ? 1 : st->st_ns;
     StencilKernel k = pick_stencil(st->st_dim, ns, st->st_q, st->mat.law, st->has_kappa, force_only);
     const unsigned grid = (unsigned)st->n_bricks * (unsigned)((st->B + ns - 1) / ns);
-    k<<<grid, 32 * st->st_wpb * st->st_q, stencil_smem(st, ns, st->has_kappa), s>>>(a);
+    k<<<grid, 32 * st->st_wpb * st->st_q, stencil_smem(st, ns, st->has_kappa), s>>>(a, st->st_maps);
     PD_CHECK_LAUNCH();
     return PD_OK;
 }

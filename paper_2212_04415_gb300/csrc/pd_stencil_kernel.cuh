@@ -186,6 +186,48 @@ struct Lane<2> {
 // The staged box (dynamic shared memory of the step kernel).
 extern __shared__ float4 g_box[];
 
+// ---- TMA staging of the box (one-sample blocks). One thread arms an
+// mbarrier with the bytes of both record copies and issues two tiled copies
+// of a 5D box (4 floats x 14 cells x rows x layers x 1 sample); cells outside
+// the grid arrive as zeros. Waits are bounded: after kStageSpin polls the
+// caller flags the sample and gives up.
+constexpr uint32_t kStageSpin = 1u << 22;
+
+__device__ __forceinline__ uint32_t sm_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void stage_bar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void stage_bar_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sm_addr(bar)), "r"(bytes) : "memory");
+}
+
+// true once phase 0 of the barrier has completed; false after kStageSpin polls
+__device__ __forceinline__ bool stage_bar_wait(uint64_t *bar) {
+    const uint32_t b = sm_addr(bar);
+    for (uint32_t it = 0; it < kStageSpin; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(b)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// box of the records map at cell (x, y, z) of sample b, into shared memory at dst
+__device__ __forceinline__ void stage_box(void *dst, const CUtensorMap *tm, int x, int y, int z, int b, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], "
+        "[%7];" ::"r"(sm_addr(dst)),
+        "l"((uint64_t)tm), "r"(0), "r"(x), "r"(y), "r"(z), "r"(b), "r"(sm_addr(bar))
+        : "memory");
+}
+
 // A staged gather record: u / dx (x, y, z) and s0 / 2. One sample: one float4
 // per cell. A pair: the two samples' values interleaved ({x0, x1, y0, y1},
 // {z0, z1, h0, h1}) in two chunks, kRowC bytes apart (row-blocked).
@@ -232,8 +274,8 @@ __device__ __forceinline__ float law_cold(float s, float s0, LawC lc) {
 template <int NS>
 struct BondCtx {
     using V = typename Lane<NS>::V;
-    int rb[4];         // byte offset (in the staged box) of the lane's own record, + kz layers
-    int kb[4];         // the same for the staged kappa values
+    int rb, lb;        // byte offset (in the staged box) of the lane's own record; bytes per layer
+    int kb, lk;        // the same for the staged kappa values
     V sg;              // +1 (sub-lane 0) or -1 (sub-lane 1)
     V cx, cy, cz;      // -sg x the lane's own displacement (cell units)
     V h, kap;          // own s0 / 2 and kappa
@@ -349,7 +391,7 @@ __device__ __forceinline__ FixOut<typename Lane<NS>::V> fix_one(int m, bool act,
     using V = typename Lane<NS>::V;
     const signed char *k = c_half[DIM - 2].k[m];
     const int kx = k[0], ky = k[1], kz = k[2], q = k[3];
-    const Rec<V> r = load_rec<NS>(cx.rb[kz] + 16 * kx + NS * kRowC * ky);
+    const Rec<V> r = load_rec<NS>(cx.rb + cx.lb * kz + 16 * kx + NS * kRowC * ky);
     FixOut<V> o;
     V rL, s;
     bond_kin<V>(cx, r, kx, ky, kz, knorm_rt(q), (float)q, o.yx, o.yy, o.yz, rL, s);
@@ -373,7 +415,9 @@ __device__ __forceinline__ FixOut<typename Lane<NS>::V> fix_one(int m, bool act,
         if (gy && cx.w1) *slot1 = dly;
     }
     o.dg = vsub(bond_g(dnew, s, rL), bond_g(dold, s, rL));
-    if constexpr (KAPPA) o.dg = vmul(o.dg, vadd(cx.kap, load_kap<NS>(cx.kb[kz] + 4 * NS * kx + NS * kRowK * ky)));
+    if constexpr (KAPPA) {
+        o.dg = vmul(o.dg, vadd(cx.kap, load_kap<NS>(cx.kb + cx.lk * kz + 4 * NS * kx + NS * kRowK * ky)));
+    }
     return o;
 }
 
@@ -411,7 +455,7 @@ __device__ __forceinline__ void stencil_bond(typename Lane<NS>::V d, const BondC
     using V = typename Lane<NS>::V;
     constexpr I3 k = half_off<DIM>(M);
     constexpr int q = k.x * k.x + k.y * k.y + k.z * k.z;
-    const Rec<V> r = load_rec<NS>(cx.rb[k.z] + 16 * k.x + NS * kRowC * k.y);
+    const Rec<V> r = load_rec<NS>(cx.rb + cx.lb * k.z + 16 * k.x + NS * kRowC * k.y);
     V yx, yy, yz, rL, s;
     bond_kin<V>(cx, r, k.x, k.y, k.z, knorm(q), (float)q, yx, yy, yz, rL, s);
     const V s0 = vadd(cx.h, r.h);
@@ -425,7 +469,7 @@ __device__ __forceinline__ void stencil_bond(typename Lane<NS>::V d, const BondC
         past = (s.x > s0.x && d.x < 1.0f) || (s.y > s0.y && d.y < 1.0f);
     if (past) mask |= 1u << J;
     V g = bond_g(d, s, rL);
-    if constexpr (KAPPA) g = vmul(g, vadd(cx.kap, load_kap<NS>(cx.kb[k.z] + 4 * NS * k.x + NS * kRowK * k.y)));
+    if constexpr (KAPPA) g = vmul(g, vadd(cx.kap, load_kap<NS>(cx.kb + cx.lk * k.z + 4 * NS * k.x + NS * kRowK * k.y)));
     px = vfma(g, yx, px);
     py = vfma(g, yy, py);
     pz = vfma(g, yz, pz);
@@ -495,7 +539,7 @@ __device__ __forceinline__ void bond_span(const BondCtx<NS> &cx, typename Lane<N
 // samples (one, or a pair on the paired FP32 instructions). Part 0's warp of
 // a row pair adds the other parts' sums (fixed order) and integrates.
 template <int DIM, int NS, int Q, int LAW, bool KAPPA, bool FORCE_ONLY>
-__device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
+__device__ __forceinline__ void step_block(const StepArgs &a, const int blk, const StencilMaps *maps) {
     using V = typename Lane<NS>::V;
     using S = Sten<DIM>;
     constexpr int kRounds = S::kRounds, HZ = S::kHaloZ, NG = kRounds / 8;
@@ -507,12 +551,14 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
     __shared__ RunView s_rv[NS];    // run bookkeeping per sample, with the pending reaction added
     __shared__ int s_n[NS];         // step index per sample
     __shared__ int s_ridx;          // the brick's index among the reaction bricks, or -1
+    __shared__ uint64_t s_bar;      // completion of the box's TMA copies (one-sample blocks)
+    __shared__ int s_staged;
 
     const int nwarps = blockDim.x >> 5;
     const int wpb = a.st_wpb;
-    const int ngrp = (a.B + NS - 1) / NS;
-    const int grp = blk % ngrp;
-    const int brick = blk / ngrp;
+    const FastDiv fg = NS == 1 ? a.fd_grp1 : a.fd_grp2;  // (B + NS - 1) / NS sample groups
+    const int brick = fdiv(blk, fg);
+    const int grp = blk - fg.d * brick;
     const auto sample_of = [&](int s) {
         const int b = NS * grp + s;
         return b < a.B ? b : NS * grp;  // the second member of the last pair of an odd batch is a copy
@@ -532,7 +578,8 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
     }
     if (!any) return;  // block-uniform
     if (threadIdx.x == 0) s_ridx = FORCE_ONLY ? -1 : a.brick_ridx[brick];
-    if (threadIdx.x < NS) s_n[threadIdx.x] = ns[threadIdx.x];
+    const int n_mine = (NS == 2 && threadIdx.x == 1) ? ns[NS - 1] : ns[0];  // the step of sample threadIdx.x
+    if (threadIdx.x < NS) s_n[threadIdx.x] = n_mine;
     // the run view (with the previous launch's reaction, if it left it
     // pending) is built by warp s for sample s while the staging copies fly
     const auto build_views = [&]() {
@@ -556,83 +603,112 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
     if (threadIdx.x < 16 * NS) (&red[0][0])[threadIdx.x] = 0.0;
     if (threadIdx.x < NS) {
         df U1, vp;
-        prescribed(a, ns[threadIdx.x], U1, vp);
+        prescribed(a, n_mine, U1, vp);
         s_pre[threadIdx.x][0] = U1.hi;
         s_pre[threadIdx.x][1] = U1.lo;
         s_pre[threadIdx.x][2] = vp.hi;
         s_pre[threadIdx.x][3] = vp.lo;
         s_cnt[threadIdx.x] = 0u;
     }
-    const int bx = brick % a.nbx, by = (brick / a.nbx) % a.nby, bz = brick / (a.nbx * a.nby);
+    const int bxy = fdiv(brick, a.fd_nbx), bz = fdiv(bxy, a.fd_nby);
+    const int bx = brick - a.nbx * bxy, by = bxy - a.nby * bz;
     const int x0 = kSlice * bx, y0 = a.BY * by, z0 = a.BZ * bz;
     const size_t BN = (size_t)a.B * a.N;
     const int Wy = a.BY + 2 * kHalo;
     const int Zp = a.BZ + HZ;    // layers of each copy: upper (sub-lane 0) and reflected lower (sub-lane 1)
     const int LB = RB * Wy, LK = RK * Wy;
-    const int oP = 0, oM = LB * Zp;                  // record copies
-    const int okP = 2 * LB * Zp, okM = okP + LK * Zp;  // kappa copies (KAPPA)
+    // record copies on 128-byte boundaries (TMA destinations), then the kappa
+    // copies (KAPPA) and the parts' partial sums (Q > 1)
+    const int CP = (LB * Zp + 127) & ~127;
+    const int pad = (int)((0u - sm_addr(g_box)) & 127u);
+    const int oP = pad, oM = pad + CP;
+    const int okP = pad + 2 * CP, okM = okP + LK * Zp;
     const int oPart = KAPPA ? okM + LK * Zp : okP;
     float *s_part = (float *)((char *)g_box + oPart);  // [Q-1][wpb][16][6 NS]
 
     // stage the box (cells outside the grid read as zero): box layer lz holds
     // z0 - HZ + lz; the upper copy takes lz >= HZ, the reflected lower copy
-    // lz < BZ + HZ at (Zp - 1 - lz, Wy - 1 - ly, kWx - 1 - lx)
+    // lz < BZ + HZ at (Zp - 1 - lz, Wy - 1 - ly, kWx - 1 - lx). One sample:
+    // both copies by TMA, the lower one from the point-reflected records (the
+    // cell at (x, y, z) of the reflected grid is (nx-1-x, ny-1-y, nz-1-z)).
     {
-        const int nbox = kWx * Wy * (a.BZ + 2 * HZ);
-        const float4 *gin0 = ((ns[0] & 1) ? a.grec1 : a.grec0) + (size_t)sample_of(0) * a.N;
-        const float4 *gin1 = ((ns[NS - 1] & 1) ? a.grec1 : a.grec0) + (size_t)sample_of(NS - 1) * a.N;
-        const float *kin0 = KAPPA ? a.kappa + (size_t)sample_of(0) * a.N : nullptr;
-        const float *kin1 = KAPPA ? a.kappa + (size_t)sample_of(NS - 1) * a.N : nullptr;
-        // row / Wy as a multiply and shift: exact for rows below 2^20 / Wy
-        // (the error of the rounded-up reciprocal stays below 1 / Wy); the
-        // staged box has at most 38 x 22 rows
-        const unsigned inv_wy = ((1u << 20) + (unsigned)Wy - 1u) / (unsigned)Wy;
-        for (int qi = threadIdx.x; qi < nbox; qi += blockDim.x) {
-            const int row = qi / kWx, lx = qi - kWx * row;
-            const int lz = (int)(((unsigned)row * inv_wy) >> 20), ly = row - Wy * lz;
-            const int gx = x0 - kHalo + lx, gy = y0 - kHalo + ly, gz = z0 - HZ + lz;
-            const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz;
-            const int gi = in ? gx + a.nx * (gy + a.ny * gz) : 0;
-            const bool toP = lz >= HZ, toM = lz < a.BZ + HZ;
-            const int rP = LB * (lz - HZ) + RB * ly + 16 * lx;
-            const int rM = LB * (Zp - 1 - lz) + RB * (Wy - 1 - ly) + 16 * (kWx - 1 - lx);
-            if constexpr (NS == 1) {
-                if (toP) cp_async16((char *)g_box + oP + rP, gin0 + gi, in ? 16 : 0);
-                if (toM) cp_async16((char *)g_box + oM + rM, gin0 + gi, in ? 16 : 0);
-            } else {
-                float4 h0 = make_float4(0.f, 0.f, 0.f, 0.f), h1 = h0;
-                if (in) {
-                    h0 = gin0[gi];
-                    h1 = gin1[gi];
-                }
-                const float4 A = make_float4(h0.x, h1.x, h0.y, h1.y), C = make_float4(h0.z, h1.z, h0.w, h1.w);
-                if (toP) {
-                    *(float4 *)((char *)g_box + oP + rP) = A;
-                    *(float4 *)((char *)g_box + oP + rP + kRowC) = C;
-                }
-                if (toM) {
-                    *(float4 *)((char *)g_box + oM + rM) = A;
-                    *(float4 *)((char *)g_box + oM + rM + kRowC) = C;
-                }
+        const int par0 = ns[0] & 1;
+        if constexpr (NS == 1) {
+            if (threadIdx.x == 0) {
+                stage_bar_init(&s_bar);
+                stage_bar_expect(&s_bar, 2u * (uint32_t)(LB * Zp));
+                const int b0 = sample_of(0);
+                stage_box((char *)g_box + oP, &maps->rec[par0], x0 - kHalo, y0 - kHalo, z0, b0, &s_bar);
+                stage_box((char *)g_box + oM, &maps->ref[par0], a.nx - kSlice - kHalo - x0,
+                          a.ny - a.BY - kHalo - y0, a.nz - a.BZ - z0, b0, &s_bar);
             }
-            if constexpr (KAPPA) {
-                const int kP = LK * (lz - HZ) + RK * ly + 4 * NS * lx;
-                const int kM = LK * (Zp - 1 - lz) + RK * (Wy - 1 - ly) + 4 * NS * (kWx - 1 - lx);
-                const float k0 = in ? kin0[gi] : 0.f;
-                if constexpr (NS == 1) {
-                    if (toP) *(float *)((char *)g_box + okP + kP) = k0;
-                    if (toM) *(float *)((char *)g_box + okM + kM) = k0;
-                } else {
-                    const float2 kk = make_float2(k0, in ? kin1[gi] : 0.f);
-                    if (toP) *(float2 *)((char *)g_box + okP + kP) = kk;
-                    if (toM) *(float2 *)((char *)g_box + okM + kM) = kk;
+        }
+        if constexpr (NS == 2 || KAPPA) {
+            const int nbox = kWx * Wy * (a.BZ + 2 * HZ);
+            const float4 *gin0 = (par0 ? a.grec1 : a.grec0) + (size_t)sample_of(0) * a.N;
+            const float4 *gin1 = ((ns[NS - 1] & 1) ? a.grec1 : a.grec0) + (size_t)sample_of(NS - 1) * a.N;
+            const float *kin0 = KAPPA ? a.kappa + (size_t)sample_of(0) * a.N : nullptr;
+            const float *kin1 = KAPPA ? a.kappa + (size_t)sample_of(NS - 1) * a.N : nullptr;
+            // row / Wy as a multiply and shift: exact for rows below 2^20 / Wy
+            // (the error of the rounded-up reciprocal stays below 1 / Wy); the
+            // staged box has at most 38 x 22 rows
+            const unsigned inv_wy = ((1u << 20) + (unsigned)Wy - 1u) / (unsigned)Wy;
+            for (int qi = threadIdx.x; qi < nbox; qi += blockDim.x) {
+                const int row = qi / kWx, lx = qi - kWx * row;
+                const int lz = (int)(((unsigned)row * inv_wy) >> 20), ly = row - Wy * lz;
+                const int gx = x0 - kHalo + lx, gy = y0 - kHalo + ly, gz = z0 - HZ + lz;
+                const bool in = gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz;
+                const int gi = in ? gx + a.nx * (gy + a.ny * gz) : 0;
+                const bool toP = lz >= HZ, toM = lz < a.BZ + HZ;
+                if constexpr (NS == 2) {
+                    const int rP = LB * (lz - HZ) + RB * ly + 16 * lx;
+                    const int rM = LB * (Zp - 1 - lz) + RB * (Wy - 1 - ly) + 16 * (kWx - 1 - lx);
+                    float4 h0 = make_float4(0.f, 0.f, 0.f, 0.f), h1 = h0;
+                    if (in) {
+                        h0 = gin0[gi];
+                        h1 = gin1[gi];
+                    }
+                    const float4 A = make_float4(h0.x, h1.x, h0.y, h1.y), C = make_float4(h0.z, h1.z, h0.w, h1.w);
+                    if (toP) {
+                        *(float4 *)((char *)g_box + oP + rP) = A;
+                        *(float4 *)((char *)g_box + oP + rP + kRowC) = C;
+                    }
+                    if (toM) {
+                        *(float4 *)((char *)g_box + oM + rM) = A;
+                        *(float4 *)((char *)g_box + oM + rM + kRowC) = C;
+                    }
+                }
+                if constexpr (KAPPA) {
+                    const int kP = LK * (lz - HZ) + RK * ly + 4 * NS * lx;
+                    const int kM = LK * (Zp - 1 - lz) + RK * (Wy - 1 - ly) + 4 * NS * (kWx - 1 - lx);
+                    const float k0 = in ? kin0[gi] : 0.f;
+                    if constexpr (NS == 1) {
+                        if (toP) *(float *)((char *)g_box + okP + kP) = k0;
+                        if (toM) *(float *)((char *)g_box + okM + kM) = k0;
+                    } else {
+                        const float2 kk = make_float2(k0, in ? kin1[gi] : 0.f);
+                        if (toP) *(float2 *)((char *)g_box + okP + kP) = kk;
+                        if (toM) *(float2 *)((char *)g_box + okM + kM) = kk;
+                    }
                 }
             }
         }
         build_views();
-        cp_async_wait_all();
+        if constexpr (NS == 1) {
+            if (threadIdx.x == 0) s_staged = stage_bar_wait(&s_bar) ? 1 : 0;
+        }
     }
     __syncthreads();
+    if constexpr (NS == 1) {
+        if (!s_staged) {  // block-uniform: the copies did not arrive within the limit
+            if (threadIdx.x == 0) {
+                atomicOr(&a.status[sample_of(0)], 2);
+                stage_bar_wait(&s_bar);  // still in flight: wait once more (bounded) before leaving
+            }
+            return;
+        }
+        stage_bar_wait(&s_bar);  // completed: returns at once, and orders the box before this thread's reads
+    }
     if (!FORCE_ONLY && a.pendable) {
         // samples that the reduced reaction stops are not stepped (every
         // block reaches the same decision); brick 0 records them
@@ -654,7 +730,7 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
 #pragma unroll
     for (int s = 0; s < NS; ++s) Rloc[s] = 0.0;
     const int row = 2 * rp + r;
-    const int ly = row % a.BY, lz = row / a.BY;
+    const int lz = fdiv(row, a.fd_by), ly = row - a.BY * lz;
     const int gx = x0 + c, gy = y0 + ly, gz = z0 + lz;
     const bool own = gx < a.nx && gy < a.ny && gz < a.nz;
     const int ii = gx + a.nx * (gy + a.ny * gz);
@@ -671,11 +747,10 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
                                       4 * NS * (kWx - 1 - kHalo - c);
         const Rec<V> me = load_rec<NS>(rown);
         BondCtx<NS> cx;
-#pragma unroll
-        for (int z = 0; z < 4; ++z) {
-            cx.rb[z] = rown + z * LB;
-            cx.kb[z] = kown + z * LK;
-        }
+        cx.rb = rown;
+        cx.lb = LB;
+        cx.kb = kown;
+        cx.lk = LK;
         cx.sg = splat<V>(t == 0 ? 1.0f : -1.0f);
         cx.cx = t == 0 ? neg(me.x) : me.x;
         cx.cy = t == 0 ? neg(me.y) : me.y;
@@ -763,9 +838,15 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
             const float4 *rin = (const float4 *)(odd ? a.rec1 : a.rec0);
             float4 *rout = (float4 *)(odd ? a.rec0 : a.rec1);
             float4 *gout = odd ? a.grec0 : a.grec1;
-            for (int q = t; q < 3; q += 2) {
-                const float sq = el(q == 0 ? acc[0] : (q == 1 ? acc[1] : acc[2]), s);
-                const float cq = el(q == 0 ? acc[3] : (q == 1 ? acc[4] : acc[5]), s);
+            float4 *goutR = odd ? a.grecR0 : a.grecR1;
+            const size_t nodeR = (size_t)sample_of(s) * a.N + (a.N - 1 - ii);  // its reflected cell
+            // sub-lane 0 integrates components 0 and 2, sub-lane 1 component 1
+#pragma unroll
+            for (int it = 0; it < 2; ++it) {
+                const int q = t + 2 * it;
+                if (q > 2) break;
+                const float sq = el(it ? acc[2] : (t ? acc[1] : acc[0]), s);
+                const float cq = el(it ? acc[5] : (t ? acc[4] : acc[3]), s);
                 const df F = df_mul(two_sum(sq, cq), cVd);
                 if (FORCE_ONLY) {
                     a.F_out[3 * node + q] = (double)F.hi + (double)F.lo;
@@ -792,7 +873,9 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
                 vl[q] = v.lo;
                 ((float *)(rout + node))[q] = u.hi;
                 ((float *)(rout + BN + node))[q] = u.lo;
-                ((float *)(gout + node))[q] = df_mul(u, a.idx_df).hi;
+                const float gq = df_mul(u, a.idx_df).hi;
+                ((float *)(gout + node))[q] = gq;
+                ((float *)(goutR + nodeR))[q] = gq;
             }
         }
     }
@@ -824,8 +907,9 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk) {
 
 // One step of one state: blocks are (brick, sample group) pairs, sample fastest.
 template <int DIM, int NS, int Q, int LAW, bool KAPPA, bool FORCE_ONLY>
-__global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const StepArgs a) {
-    step_block<DIM, NS, Q, LAW, KAPPA, FORCE_ONLY>(a, blockIdx.x);
+__global__ void __launch_bounds__(512, NS == 1 ? 2 : 1)
+    k_step_stencil(const StepArgs a, const __grid_constant__ StencilMaps t) {
+    step_block<DIM, NS, Q, LAW, KAPPA, FORCE_ONLY>(a, blockIdx.x, &t);
 }
 
 // One step of two states in one launch (the fine and the coarse member of the
@@ -837,10 +921,10 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1) k_step_stencil(const Ste
 template <int DIM, int Q, int LAW, bool KAPPA>
 __global__ void __launch_bounds__(512, 2) k_step_stencil_pair(const __grid_constant__ StepPair g) {
     const int i = (int)blockIdx.x >= g.nblk0 ? 1 : 0;
-    step_block<DIM, 1, Q, LAW, KAPPA, false>(g.a[i], (int)blockIdx.x - (i ? g.nblk0 : 0));
+    step_block<DIM, 1, Q, LAW, KAPPA, false>(g.a[i], (int)blockIdx.x - (i ? g.nblk0 : 0), &g.t[i]);
 }
 
-typedef void (*StencilKernel)(const StepArgs);
+typedef void (*StencilKernel)(const StepArgs, const StencilMaps);
 typedef void (*StencilPairKernel)(const StepPair);
 
 template <int DIM, int Q>
@@ -872,7 +956,7 @@ StencilKernel pick_variant(int ns, int law, bool kappa, bool fo) {
 }  // namespace
 
 // one per translation unit
-typedef void (*StencilKernelFn)(const StepArgs);
+typedef void (*StencilKernelFn)(const StepArgs, const StencilMaps);
 typedef void (*StencilPairFn)(const StepPair);
 StencilKernelFn stencil_pick_d3q1(int ns, int law, bool kappa, bool fo);
 StencilKernelFn stencil_pick_d3q2(int ns, int law, bool kappa, bool fo);

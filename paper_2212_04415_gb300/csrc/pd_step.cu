@@ -753,6 +753,8 @@ static void free_state(pd_state *st) {
     cudaFree(st->rec[1]);
     cudaFree(st->grec[0]);
     cudaFree(st->grec[1]);
+    cudaFree(st->grecR[0]);
+    cudaFree(st->grecR[1]);
     cudaFree(st->kappa);
     cudaFree(st->codes);
     cudaFree(st->coord);
@@ -1375,7 +1377,10 @@ extern "C" int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int
     PD_CHECK_CUDA(cudaMemcpyAsync(status.data(), st->status, st->B * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PD_CHECK_CUDA(cudaStreamSynchronize(s));
     for (int b = 0; b < st->B; ++b)
-        if (status[b] & 1) {
+        if (status[b] & 2) {
+            set_error("the staged box of a stencil step of sample %d did not arrive (bounded wait expired)", b);
+            return PD_ERR_CUDA;
+        } else if (status[b] & 1) {
             set_error("non-finite reaction in sample %d", b);
             return PD_ERR_NAN;
         }
@@ -1529,7 +1534,11 @@ extern "C" int pd_run_to_peak_multi(pd_state *const *states, int32_t n_states, c
     PD_CHECK_CUDA(se);
     for (int i = 0; i < n_states; ++i)
         for (int b = 0; b < states[i]->B; ++b)
-            if (status[i][b] & 1) {
+            if (status[i][b] & 2) {
+                set_error("the staged box of a stencil step of sample %d of state %d did not arrive (bounded wait "
+                          "expired)", b, i);
+                return PD_ERR_CUDA;
+            } else if (status[i][b] & 1) {
                 set_error("non-finite reaction in sample %d of state %d", b, i);
                 return PD_ERR_NAN;
             }
