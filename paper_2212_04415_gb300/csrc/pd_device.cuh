@@ -108,6 +108,9 @@ struct StepArgs {
     double gfA;   // > 0: s_crit = s0 + gfA / s0, else s_ratio s0
     float gfA_f;
     df cV_df, cVh_df;  // cV and cV / 2 as double-float (stencil path: applied to the node sums)
+    // stencil path: v(n+1) = va v(n) + vf S for a free DOF with bond sum S,
+    // va = ca icb and vf = dtr icb cV (vfh: cV / 2, with a stiffness field)
+    df va_df, vf_df, vfh_df;
 };
 
 // The arguments of two states stepped in one launch (the first nblk0 blocks

@@ -112,6 +112,7 @@ struct pd_state {
     int32_t st_dim;         // 3, or 2 for a one-layer grid (planar 28-offset stencil)
     int32_t st_ns;          // samples per block (1, or 2 on the paired FP32 instructions)
     int32_t st_defer;       // launches may leave their reaction to the next launch (few blocks per SM)
+    int32_t st_one_wave;    // a launch is a single wave of at most 4 blocks per SM
     int32_t ns_req;         // requested st_ns (schedule), 0 = built-in choice
     int32_t reduce_req;     // requested reaction reduction (schedule): 0 built-in, 1 own launch, 2 deferred
     int64_t st_len;         // damage slots per sample

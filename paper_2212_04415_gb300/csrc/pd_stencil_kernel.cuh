@@ -563,6 +563,11 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
         const int b = NS * grp + s;
         return b < a.B ? b : NS * grp;  // the second member of the last pair of an odd batch is a copy
     };
+    // Launched as a programmatic dependent of the previous step: let the next
+    // step's blocks be scheduled now, and wait here until the previous step
+    // has completed and its writes are visible (both are no-ops otherwise).
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     int ns[NS];
     bool live[NS];
     bool any = false;
@@ -847,8 +852,9 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
                 if (q > 2) break;
                 const float sq = el(it ? acc[2] : (t ? acc[1] : acc[0]), s);
                 const float cq = el(it ? acc[5] : (t ? acc[4] : acc[3]), s);
-                const df F = df_mul(two_sum(sq, cq), cVd);
+                const df S = two_sum(sq, cq);  // the node's bond sum (F = cV S, or cV S / 2 with kappa)
                 if (FORCE_ONLY) {
+                    const df F = df_mul(S, cVd);
                     a.F_out[3 * node + q] = (double)F.hi + (double)F.lo;
                     continue;
                 }
@@ -858,12 +864,14 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
                 float *vl = (float *)(a.vdf + BN + node);
                 df v = {vh[q], vl[q]};
                 if (code == 0) {
-                    v = df_mul(df_add(df_mul(a.ca_df, v), df_mul(a.dtr_df, F)), a.icb_df);
+                    // v(n+1) = (ca v(n) + dtr F) icb with the constants folded on the host
+                    v = df_add(df_mul(a.va_df, v), df_mul(KAPPA ? a.vfh_df : a.vf_df, S));
                     u = df_add(u, df_mul(a.dt_df, v));
                 } else if (code == 1) {
                     u = {0.f, 0.f};
                     v = {0.f, 0.f};
                 } else {
+                    const df F = df_mul(S, cVd);
                     const float sg = code == 2 ? 1.0f : -1.0f;
                     Rloc[s] -= (double)sg * ((double)F.hi + (double)F.lo);
                     v = df{sg * s_pre[s][2], sg * s_pre[s][3]};

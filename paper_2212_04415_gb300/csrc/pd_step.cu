@@ -689,6 +689,9 @@ static StepArgs make_args(const pd_state *st) {
     a.cVf = (float)a.cV;
     a.cV_df = df_split(a.cV);
     a.cVh_df = df_split(0.5 * a.cV);
+    a.va_df = df_split(a.ca * a.icb);
+    a.vf_df = df_split(a.dtr * a.icb * a.cV);
+    a.vfh_df = df_split(a.dtr * a.icb * (0.5 * a.cV));
     a.s_ratio_f = (float)a.s_ratio;
     a.k_f = (float)a.k;
     a.alpha_f = (float)a.alpha;
