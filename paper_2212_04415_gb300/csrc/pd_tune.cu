@@ -48,8 +48,9 @@ static std::vector<pd_schedule> candidates(const pd_grid *g, const pd_material *
     const bool stencil = mat->precision == PD_PREC_MIXED && m2 >= 9.0 && m2 < 10.0;
     std::vector<std::pair<double, std::pair<int, int>>> bricks;
     if (stencil) {
-        static const int list[][2] = {{2, 2}, {4, 2}, {2, 4}, {4, 4}, {8, 2}, {2, 8}, {8, 4}, {4, 8},
-                                      {6, 2}, {2, 6}, {6, 4}, {4, 6}, {8, 1}, {4, 1}, {2, 1}, {6, 1}};
+        static const int list[][2] = {{2, 2},  {4, 2}, {2, 4},  {4, 4}, {8, 2},  {2, 8}, {8, 4},  {4, 8},
+                                      {6, 2},  {2, 6}, {6, 4},  {4, 6}, {10, 2}, {2, 10}, {12, 2}, {2, 12},
+                                      {16, 2}, {2, 16}, {8, 1}, {4, 1}, {2, 1},  {6, 1}};
         for (const auto &b : list) {
             if ((size_t)14 * (b[0] + 6) * (b[1] + 6) * 32 > 160 * 1024) continue;
             bricks.push_back({slot_ratio(g, b[0], b[1]), {b[0], b[1]}});
