@@ -95,6 +95,8 @@ struct StepArgs {
     float dxf;       // dx in FP32
     float4 *grec0, *grec1;  // stencil path: gather records (u / dx in FP32, s0 / 2) by step parity
     float4 *grecR0, *grecR1;  // the same point-reflected (node i of a sample at N - 1 - i)
+    const float *tmpl;        // stencil path: initial damage of every slot (0 real bond, 1 absent), shared by samples
+    uint8_t *dirty;           // stencil path: per sample, lane and part, bit g = round group g differs from tmpl
     FastDiv fd_grp1, fd_grp2;   // stencil path: sample groups per brick with 1 and 2 samples per block
     FastDiv fd_nbx, fd_nby, fd_by;  // bricks along x, along y, brick rows along y
     df idx_df;              // stencil path: 1 / dx as double-float

@@ -117,6 +117,7 @@ struct pd_state {
     int32_t reduce_req;     // requested reaction reduction (schedule): 0 built-in, 1 own launch, 2 deferred
     int64_t st_len;         // damage slots per sample
     float *st_tmpl;         // [st_len]: 0 for real bonds, 1 for absent (broken) slots
+    uint8_t *st_dirty;      // [B][bricks][wpb][32 lanes][4 parts]: 8-round groups whose damage differs from st_tmpl
     float4 *grec[2];        // gather records by step parity, [B][N]: (u / dx rounded to FP32, s0 / 2)
     float4 *grecR[2];       // the same point-reflected: node i of a sample at N - 1 - i
     StencilMaps st_maps;    // TMA maps of the staged box over grec and grecR

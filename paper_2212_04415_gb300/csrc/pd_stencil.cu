@@ -233,7 +233,8 @@ int stencil_build(pd_state *st, const int32_t *col) {
     st->st_q = warps1 >= 152ll * 24 ? 1 : 2;
     if (st->q_req) st->st_q = st->q_req;
     if (st->st_dim == 2) st->st_q = 1;
-    while (st->st_q > 1 && 32 * st->st_wpb * st->st_q > 512) st->st_q /= 2;
+    // threads a block: at most 512, or 256 for one sample at Q = 2 (its register budget)
+    while (st->st_q > 1 && 32 * st->st_wpb * st->st_q > (st->st_q == 2 && st->st_ns == 1 ? 256 : 512)) st->st_q /= 2;
     // Deferring the reaction to the next launch pays when a launch is a
     // single wave of a few blocks per SM, whose reduction tail would
     // otherwise stand alone at the end (measured on GB300: 28k-node beam,
@@ -262,6 +263,8 @@ int stencil_build(pd_state *st, const int32_t *col) {
     PD_TRY(dalloc(&st->st_box, box.size()));
     PD_CHECK_CUDA(cudaMemcpy(st->st_box, box.data(), box.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
     PD_TRY(dalloc(&st->st_tmpl, st->st_len));
+    PD_TRY(dalloc(&st->st_dirty, (size_t)st->B * (st->st_len / rounds) * 4));
+    PD_CHECK_CUDA(cudaMemset(st->st_dirty, 0, (size_t)st->B * (st->st_len / rounds) * 4));
     PD_TRY(dalloc(&st->grec[0], (size_t)st->B * N));
     PD_TRY(dalloc(&st->grec[1], (size_t)st->B * N));
     PD_TRY(dalloc(&st->grecR[0], (size_t)st->B * N));
@@ -305,6 +308,8 @@ void stencil_fill_args(const pd_state *st, StepArgs &a) {
     a.grecR0 = st->grecR[0];
     a.grecR1 = st->grecR[1];
     a.idx_df = df_split(1.0 / st->g.dx);
+    a.tmpl = st->st_tmpl;
+    a.dirty = st->st_dirty;
     a.fd_grp1 = fastdiv_make(st->B);
     a.fd_grp2 = fastdiv_make((st->B + 1) / 2);
     a.fd_nbx = fastdiv_make(st->nbx);
@@ -315,11 +320,18 @@ void stencil_fill_args(const pd_state *st, StepArgs &a) {
 int stencil_reset_damage(pd_state *st, cudaStream_t s) {
     k_stencil_reset<<<blocks_of(st->st_len * st->B), 256, 0, s>>>(st->st_len, st->B, st->st_tmpl, (float *)st->dmg);
     PD_CHECK_LAUNCH();
+    // every group equals the template again
+    const int rounds = st->st_dim == 3 ? Sten<3>::kRounds : Sten<2>::kRounds;
+    PD_CHECK_CUDA(cudaMemsetAsync(st->st_dirty, 0, (size_t)st->B * (st->st_len / rounds) * 4, s));
     return PD_OK;
 }
 
 int stencil_map_damage(const pd_state *st, double *csr, bool to_state, cudaStream_t s) {
     const long long NB = st->N * st->B;
+    if (to_state) {  // loaded damage: every group is read from the samples' own words
+        const int rounds = st->st_dim == 3 ? Sten<3>::kRounds : Sten<2>::kRounds;
+        PD_CHECK_CUDA(cudaMemsetAsync(st->st_dirty, 0xFF, (size_t)st->B * (st->st_len / rounds) * 4, s));
+    }
     if (to_state)
         k_stencil_map<true><<<blocks_of(NB), 256, 0, s>>>(st->row_ptr, st->col_csr, st->coord, st->N, st->B, st->nb,
                                                           st->g.nx, st->g.ny, st->by, st->bz, st->nbx, st->nby,

@@ -42,6 +42,17 @@
 // x-consecutive lanes of a gather read 128 contiguous bytes (no bank
 // conflicts); cells outside the grid read as zero displacement.
 //
+// Most damage words never change: an intact bond stays at 0 until its
+// stretch passes the elastic limit, an absent one stays at 1. Every lane
+// keeps one bit per group of 8 rounds (per part of the half-stencil, so that
+// parts never write the same byte), set when a fix-up first grows a damage
+// word of the group. A group whose bit is clear still equals the template
+// (the initial damage of every slot, shared by all samples of the state), so
+// it is read from the template, which stays in L2, instead of from the
+// sample's own words: the values are the same, and the DRAM stream of a
+// launch shrinks to the groups that are softening or broken. Reset clears the
+// bits; a state loaded with damage marks every group.
+//
 // A step's reaction is reduced in its own launch, or, for launches of a single
 // wave, by every block of the next launch before it steps (no serial tail at
 // the end of each step; the run bookkeeping is double-buffered by parity).
@@ -280,24 +291,44 @@ struct BondCtx {
     V cx, cy, cz;      // -sg x the lane's own displacement (cell units)
     V h, kap;          // own s0 / 2 and kappa
     float4 *dq0, *dq1; // damage quads of the lane's samples ([quad][32 lanes] float4)
+    const float4 *tq;  // the same quads of the template (initial damage, shared by all samples)
+    unsigned dw;       // groups of 8 rounds read from dq0 (bits 0-7) and dq1 (bits 8-15), else from tq
     bool w0, w1;       // damage writes enabled per sample
     LawC lc;
 };
 
-// Damage words of one group of 8 rounds: two quads per sample.
+// Damage words of one prefetched group of rounds: two quads (8 rounds) of
+// the one sample, or one quad (4 rounds) of each sample of a pair (half the
+// words in flight, so that the pair kernel fits fewer registers).
 template <int NS>
-struct DQ {
-    float4 a0, a1, b0, b1;
+struct DQ;
+template <>
+struct DQ<1> {
+    float4 a0, a1;
 };
+template <>
+struct DQ<2> {
+    float4 a0, b0;
+};
+template <int NS>
+constexpr int kGroupRounds = NS == 1 ? 8 : 4;
 
+// A group whose damage no bond has changed since the reset equals the
+// template, which all samples of the launch share (it stays in L2): its words
+// are read from there, and only groups that some fix-up has written come
+// from the sample's own words (the same values either way).
 template <int NS>
 __device__ __forceinline__ DQ<NS> load_dq(const BondCtx<NS> &cx, int g) {
     DQ<NS> q;
-    q.a0 = cx.dq0[32 * (2 * g)];
-    q.a1 = cx.dq0[32 * (2 * g + 1)];
-    if constexpr (NS == 2) {
-        q.b0 = cx.dq1[32 * (2 * g)];
-        q.b1 = cx.dq1[32 * (2 * g + 1)];
+    if constexpr (NS == 1) {
+        const float4 *p = (cx.dw >> g) & 1u ? cx.dq0 : cx.tq;
+        q.a0 = p[32 * (2 * g)];
+        q.a1 = p[32 * (2 * g + 1)];
+    } else {
+        const float4 *p0 = (cx.dw >> (g / 2)) & 1u ? cx.dq0 : cx.tq;
+        const float4 *p1 = (cx.dw >> (8 + g / 2)) & 1u ? cx.dq1 : cx.tq;
+        q.a0 = p0[32 * g];
+        q.b0 = p1[32 * g];
     }
     return q;
 }
@@ -307,6 +338,15 @@ __device__ __forceinline__ float quad_el(const float4 &a0, const float4 &a1) {
     const float4 &v = J < 4 ? a0 : a1;
     constexpr int e = J % 4;
     return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+
+// Damage of round J of the group, per sample of the lane.
+template <int NS, int J>
+__device__ __forceinline__ typename Lane<NS>::V dmg_el(const DQ<NS> &q) {
+    if constexpr (NS == 1)
+        return quad_el<J>(q.a0, q.a1);
+    else
+        return make_float2(quad_el<J>(q.a0, q.a0), quad_el<J>(q.b0, q.b0));
 }
 
 // Kinematics of one bond with offset k (cell units) from the staged record r
@@ -387,7 +427,7 @@ struct FixOut {
 };
 
 template <int DIM, int NS, int LAW, bool KAPPA>
-__device__ __forceinline__ FixOut<typename Lane<NS>::V> fix_one(int m, bool act, const BondCtx<NS> &cx) {
+__device__ __forceinline__ FixOut<typename Lane<NS>::V> fix_one(int m, bool act, const BondCtx<NS> &cx, unsigned &dwn) {
     using V = typename Lane<NS>::V;
     const signed char *k = c_half[DIM - 2].k[m];
     const int kx = k[0], ky = k[1], kz = k[2], q = k[3];
@@ -403,7 +443,10 @@ __device__ __forceinline__ FixOut<typename Lane<NS>::V> fix_one(int m, bool act,
         const float dl = s > s0 ? law_cold<LAW>(s, s0, cx.lc) : 0.f;
         const bool grow = act && dl > dold;
         dnew = grow ? dl : dold;
-        if (grow) *slot0 = dl;
+        if (grow) {
+            *slot0 = dl;
+            dwn |= 1u << (16 + m / 8);
+        }
     } else {
         float *slot1 = (float *)(cx.dq1 + 32 * (m / 4)) + (m % 4);
         dold = make_float2(*slot0, *slot1);
@@ -411,8 +454,14 @@ __device__ __forceinline__ FixOut<typename Lane<NS>::V> fix_one(int m, bool act,
         const float dly = s.y > s0.y ? law_cold<LAW>(s.y, s0.y, cx.lc) : 0.f;
         const bool gx = act && dlx > dold.x, gy = act && dly > dold.y;
         dnew = make_float2(gx ? dlx : dold.x, gy ? dly : dold.y);
-        if (gx && cx.w0) *slot0 = dlx;
-        if (gy && cx.w1) *slot1 = dly;
+        if (gx && cx.w0) {
+            *slot0 = dlx;
+            dwn |= 1u << (16 + m / 8);
+        }
+        if (gy && cx.w1) {
+            *slot1 = dly;
+            dwn |= 1u << (24 + m / 8);
+        }
     }
     o.dg = vsub(bond_g(dnew, s, rL), bond_g(dold, s, rL));
     if constexpr (KAPPA) {
@@ -426,7 +475,8 @@ __device__ __forceinline__ FixOut<typename Lane<NS>::V> fix_one(int m, bool act,
 // so that their latencies overlap in the few warps at a growing crack), the
 // corrections added to the lane's sums in ascending round order.
 template <int DIM, int NS, int LAW, bool KAPPA>
-__device__ __forceinline__ void fix_bonds(unsigned mask, int m0, const BondCtx<NS> &cx, typename Lane<NS>::V &px,
+__device__ __forceinline__ void fix_bonds(unsigned mask, int m0, const BondCtx<NS> &cx, unsigned &dwn,
+                                          typename Lane<NS>::V &px,
                                        typename Lane<NS>::V &py, typename Lane<NS>::V &pz) {
     using V = typename Lane<NS>::V;
     while (mask) {
@@ -435,8 +485,8 @@ __device__ __forceinline__ void fix_bonds(unsigned mask, int m0, const BondCtx<N
         const bool two = mask != 0u;
         const int j2 = two ? __ffs(mask) - 1 : j1;  // without a second bond: the first again, with no effect
         if (two) mask &= mask - 1;
-        const FixOut<V> a = fix_one<DIM, NS, LAW, KAPPA>(m0 + j1, true, cx);
-        const FixOut<V> b = fix_one<DIM, NS, LAW, KAPPA>(m0 + j2, two, cx);
+        const FixOut<V> a = fix_one<DIM, NS, LAW, KAPPA>(m0 + j1, true, cx, dwn);
+        const FixOut<V> b = fix_one<DIM, NS, LAW, KAPPA>(m0 + j2, two, cx, dwn);
         px = vfma(a.dg, a.yx, px);
         py = vfma(a.dg, a.yy, py);
         pz = vfma(a.dg, a.yz, pz);
@@ -479,12 +529,7 @@ template <int DIM, int NS, bool KAPPA, int M, int J, int JG>
 __device__ __forceinline__ void bond_if(const BondCtx<NS> &cx, const DQ<NS> &dq, typename Lane<NS>::V &px,
                                         typename Lane<NS>::V &py, typename Lane<NS>::V &pz, unsigned &mask) {
     if constexpr (M < Sten<DIM>::kHalf) {
-        typename Lane<NS>::V d;
-        if constexpr (NS == 1)
-            d = quad_el<J>(dq.a0, dq.a1);
-        else
-            d = make_float2(quad_el<J>(dq.a0, dq.a1), quad_el<J>(dq.b0, dq.b1));
-        stencil_bond<DIM, NS, KAPPA, M, JG>(d, cx, px, py, pz, mask);
+        stencil_bond<DIM, NS, KAPPA, M, JG>(dmg_el<NS, J>(dq), cx, px, py, pz, mask);
     }
 }
 
@@ -495,44 +540,49 @@ __device__ __forceinline__ void bond_group(const BondCtx<NS> &cx, const DQ<NS> &
     (bond_if<DIM, NS, KAPPA, M0 + J, J, JG0 + J>(cx, dq, px, py, pz, mask), ...);
 }
 
-// Groups of 8 rounds are summed kSumGroups at a time: the FP32 sum of 8
-// kSumGroups bonds is added to the compensated (TwoSum) accumulator after the
-// bonds among them that passed their elastic limit have been fixed up.
-constexpr int kSumGroups = 2;
+// The rounds are summed 16 at a time: the FP32 sum of 16 bonds is added to
+// the compensated (TwoSum) accumulator after the bonds among them that passed
+// their elastic limit have been fixed up. The sums do not depend on the
+// prefetch group (8 or 4 rounds), so one-sample and paired lanes agree bit
+// for bit.
+constexpr int kSumRounds = 16;
 
-// Groups [G, G1) of 8 rounds; the next group's damage words are requested
-// before the current group is computed.
+// Groups [G, G1) of kGroupRounds rounds; the next group's damage words are
+// requested before the current group is computed.
 template <int DIM, int NS, int LAW, bool KAPPA, int G, int G1>
 __device__ __forceinline__ void bond_groups(const BondCtx<NS> &cx, const DQ<NS> &cur, typename Lane<NS>::V *acc,
                                             typename Lane<NS>::V &px, typename Lane<NS>::V &py,
-                                            typename Lane<NS>::V &pz, unsigned &mask) {
+                                            typename Lane<NS>::V &pz, unsigned &mask, unsigned &dwn) {
     using V = typename Lane<NS>::V;
+    constexpr int GR = kGroupRounds<NS>, GS = kSumRounds / GR;
     if constexpr (G < G1) {
         DQ<NS> nxt;
         if constexpr (G + 1 < G1) nxt = load_dq<NS>(cx, G + 1);
-        constexpr int G0 = G - (G % kSumGroups);  // first group of the sum
-        bond_group<DIM, NS, KAPPA, 8 * G, 8 * (G - G0)>(cx, cur, px, py, pz, mask,
-                                                         std::make_integer_sequence<int, 8>{});
-        if (G % kSumGroups == kSumGroups - 1 || G + 1 == G1) {
-            if (__builtin_expect(mask != 0u, 0)) fix_bonds<DIM, NS, LAW, KAPPA>(mask, 8 * G0, cx, px, py, pz);
+        constexpr int G0 = G - (G % GS);  // first group of the sum
+        bond_group<DIM, NS, KAPPA, GR * G, GR * (G - G0)>(cx, cur, px, py, pz, mask,
+                                                           std::make_integer_sequence<int, GR>{});
+        if (G % GS == GS - 1 || G + 1 == G1) {
+            if (__builtin_expect(mask != 0u, 0)) fix_bonds<DIM, NS, LAW, KAPPA>(mask, GR * G0, cx, dwn, px, py, pz);
             two_sum_acc_v(acc[0], acc[3], px);
             two_sum_acc_v(acc[1], acc[4], py);
             two_sum_acc_v(acc[2], acc[5], pz);
             px = py = pz = splat<V>(0.f);
             mask = 0u;
         }
-        if constexpr (G + 1 < G1) bond_groups<DIM, NS, LAW, KAPPA, G + 1, G1>(cx, nxt, acc, px, py, pz, mask);
+        if constexpr (G + 1 < G1) bond_groups<DIM, NS, LAW, KAPPA, G + 1, G1>(cx, nxt, acc, px, py, pz, mask, dwn);
     }
 }
 
-template <int DIM, int NS, int LAW, bool KAPPA, int G0, int G1>
-__device__ __forceinline__ void bond_span(const BondCtx<NS> &cx, typename Lane<NS>::V *acc) {
-    static_assert(G0 % kSumGroups == 0, "spans start at a sum boundary");
+// Rounds [R0, R1) of the half-stencil.
+template <int DIM, int NS, int LAW, bool KAPPA, int R0, int R1>
+__device__ __forceinline__ void bond_span(const BondCtx<NS> &cx, typename Lane<NS>::V *acc, unsigned &dwn) {
+    static_assert(R0 % kSumRounds == 0, "spans start at a sum boundary");
     using V = typename Lane<NS>::V;
-    const DQ<NS> first = load_dq<NS>(cx, G0);
+    constexpr int GR = kGroupRounds<NS>;
+    const DQ<NS> first = load_dq<NS>(cx, R0 / GR);
     V px = splat<V>(0.f), py = px, pz = px;
     unsigned mask = 0u;
-    bond_groups<DIM, NS, LAW, KAPPA, G0, G1>(cx, first, acc, px, py, pz, mask);
+    bond_groups<DIM, NS, LAW, KAPPA, R0 / GR, R1 / GR>(cx, first, acc, px, py, pz, mask, dwn);
 }
 
 // Warps of a block: wpb row pairs x Q parts of the half-stencil, for NS
@@ -542,7 +592,7 @@ template <int DIM, int NS, int Q, int LAW, bool KAPPA, bool FORCE_ONLY>
 __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, const StencilMaps *maps) {
     using V = typename Lane<NS>::V;
     using S = Sten<DIM>;
-    constexpr int kRounds = S::kRounds, HZ = S::kHaloZ, NG = kRounds / 8;
+    constexpr int kRounds = S::kRounds, HZ = S::kHaloZ;
     constexpr int RB = NS * kRowC;  // bytes of a staged (y, z) row of records
     constexpr int RK = NS * kRowK;  // bytes of a staged row of kappa values
     __shared__ double red[NS][16];
@@ -630,6 +680,17 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
     const int okP = pad + 2 * CP, okM = okP + LK * Zp;
     const int oPart = KAPPA ? okM + LK * Zp : okP;
     float *s_part = (float *)((char *)g_box + oPart);  // [Q-1][wpb][16][6 NS]
+
+    // The dirty bits of this thread's lane and part (byte `part` of the lane's
+    // word holds the part's groups of 8 rounds from bit 0), read before the
+    // staging wait so that their latency overlaps it.
+    constexpr int kGroups = kRounds / 8;
+    const auto dirty_byte = [&](int s) {
+        const size_t lane_slot = ((size_t)brick * wpb + (threadIdx.x >> 5) % wpb) * 32 + (threadIdx.x & 31);
+        return a.dirty + ((size_t)sample_of(s) * (size_t)(a.sell_len / kRounds) + lane_slot) * 4 +
+               (threadIdx.x >> 5) / wpb;
+    };
+    const unsigned dw0 = *dirty_byte(0), dw1 = NS == 2 ? (unsigned)*dirty_byte(NS - 1) : 0u;
 
     // stage the box (cells outside the grid read as zero): box layer lz holds
     // z0 - HZ + lz; the upper copy takes lz >= HZ, the reflected lower copy
@@ -765,26 +826,42 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
         cx.dq0 = (float4 *)a.dmg + (size_t)sample_of(0) * (a.sell_len / 4) +
                  ((size_t)brick * wpb + rp) * (kRounds / 4) * 32 + lane;
         cx.dq1 = cx.dq0 + (size_t)(sample_of(NS - 1) - sample_of(0)) * (a.sell_len / 4);
+        cx.tq = (const float4 *)a.tmpl + ((size_t)brick * wpb + rp) * (kRounds / 4) * 32 + lane;
+        const unsigned dbase = part * (kGroups / Q);  // the part's first group
+        cx.dw = (dw0 << dbase) | (dw1 << (8 + dbase));
         cx.w0 = live[0];
         cx.w1 = live[NS - 1];
         cx.lc = LawC{a.s_ratio_f, a.k_f, a.alpha_f, a.inv_1mek_f, a.inv_1pa_f, a.gfA_f};
+        constexpr int R = kRounds;
+        unsigned dwn = 0u;  // groups whose damage a fix-up changed: bits 16-23 (sample 0), 24-31 (sample 1)
         if constexpr (Q == 1) {
-            bond_span<DIM, NS, LAW, KAPPA, 0, NG>(cx, acc);
+            bond_span<DIM, NS, LAW, KAPPA, 0, R>(cx, acc, dwn);
         } else if constexpr (Q == 2) {
             if (part == 0)
-                bond_span<DIM, NS, LAW, KAPPA, 0, NG / 2>(cx, acc);
+                bond_span<DIM, NS, LAW, KAPPA, 0, R / 2>(cx, acc, dwn);
             else
-                bond_span<DIM, NS, LAW, KAPPA, NG / 2, NG>(cx, acc);
+                bond_span<DIM, NS, LAW, KAPPA, R / 2, R>(cx, acc, dwn);
         } else {
-            static_assert(Q == 4 && NG % 4 == 0, "four parts need a multiple of four groups");
+            static_assert(Q == 4 && R % (4 * kSumRounds) == 0, "four parts need a multiple of 64 rounds");
             if (part == 0)
-                bond_span<DIM, NS, LAW, KAPPA, 0, NG / 4>(cx, acc);
+                bond_span<DIM, NS, LAW, KAPPA, 0, R / 4>(cx, acc, dwn);
             else if (part == 1)
-                bond_span<DIM, NS, LAW, KAPPA, NG / 4, NG / 2>(cx, acc);
+                bond_span<DIM, NS, LAW, KAPPA, R / 4, R / 2>(cx, acc, dwn);
             else if (part == 2)
-                bond_span<DIM, NS, LAW, KAPPA, NG / 2, 3 * NG / 4>(cx, acc);
+                bond_span<DIM, NS, LAW, KAPPA, R / 2, 3 * R / 4>(cx, acc, dwn);
             else
-                bond_span<DIM, NS, LAW, KAPPA, 3 * NG / 4, NG>(cx, acc);
+                bond_span<DIM, NS, LAW, KAPPA, 3 * R / 4, R>(cx, acc, dwn);
+        }
+        if (__builtin_expect(dwn != 0u, 0)) {  // their words now differ from the template
+            const unsigned db = part * (kGroups / Q), n0 = (dwn >> 16) & 0xFFu, n1 = dwn >> 24;
+            if (n0) {
+                uint8_t *p = dirty_byte(0);
+                *p = (uint8_t)(*p | (n0 >> db));
+            }
+            if (NS == 2 && n1) {
+                uint8_t *p = dirty_byte(NS - 1);
+                *p = (uint8_t)(*p | (n1 >> db));
+            }
         }
     }
     // The node's force is sub-lane 0's sum minus sub-lane 1's: negate on
@@ -859,10 +936,10 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
                     continue;
                 }
                 const uint8_t code = a.codes[3 * (size_t)ii + q];
-                df u = {((const float *)(rin + node))[q], ((const float *)(rin + BN + node))[q]};
+                df u = {__ldcs((const float *)(rin + node) + q), __ldcs((const float *)(rin + BN + node) + q)};
                 float *vh = (float *)(a.vdf + node);
                 float *vl = (float *)(a.vdf + BN + node);
-                df v = {vh[q], vl[q]};
+                df v = {__ldcs(vh + q), __ldcs(vl + q)};
                 if (code == 0) {
                     // v(n+1) = (ca v(n) + dtr F) icb with the constants folded on the host
                     v = df_add(df_mul(a.va_df, v), df_mul(KAPPA ? a.vfh_df : a.vf_df, S));
@@ -877,10 +954,10 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
                     v = df{sg * s_pre[s][2], sg * s_pre[s][3]};
                     u = df{sg * s_pre[s][0], sg * s_pre[s][1]};
                 }
-                vh[q] = v.hi;
-                vl[q] = v.lo;
-                ((float *)(rout + node))[q] = u.hi;
-                ((float *)(rout + BN + node))[q] = u.lo;
+                __stcs(vh + q, v.hi);
+                __stcs(vl + q, v.lo);
+                __stcs((float *)(rout + node) + q, u.hi);
+                __stcs((float *)(rout + BN + node) + q, u.lo);
                 const float gq = df_mul(u, a.idx_df).hi;
                 ((float *)(gout + node))[q] = gq;
                 ((float *)(goutR + nodeR))[q] = gq;
@@ -915,7 +992,11 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
 
 // One step of one state: blocks are (brick, sample group) pairs, sample fastest.
 template <int DIM, int NS, int Q, int LAW, bool KAPPA, bool FORCE_ONLY>
-__global__ void __launch_bounds__(512, NS == 1 ? 2 : 1)
+// Register budgets: 64 registers at up to 512 threads (two blocks an SM),
+// except the half-stencil split in two (Q = 2, the few-block launches of
+// single samples): 80 registers at up to 256 threads, where 3 blocks an SM
+// hold the whole grid; sample pairs take 128.
+__global__ void __launch_bounds__(Q == 2 && NS == 1 ? 256 : 512, NS == 2 ? 1 : (Q == 2 ? 3 : 2))
     k_step_stencil(const StepArgs a, const __grid_constant__ StencilMaps t) {
     step_block<DIM, NS, Q, LAW, KAPPA, FORCE_ONLY>(a, blockIdx.x, &t);
 }
@@ -927,7 +1008,7 @@ __global__ void __launch_bounds__(512, NS == 1 ? 2 : 1)
 // parameter space (grid constant), so selecting a state by block copies
 // nothing.
 template <int DIM, int Q, int LAW, bool KAPPA>
-__global__ void __launch_bounds__(512, 2) k_step_stencil_pair(const __grid_constant__ StepPair g) {
+__global__ void __launch_bounds__(Q == 2 ? 256 : 512, Q == 2 ? 3 : 2) k_step_stencil_pair(const __grid_constant__ StepPair g) {
     const int i = (int)blockIdx.x >= g.nblk0 ? 1 : 0;
     step_block<DIM, 1, Q, LAW, KAPPA, false>(g.a[i], (int)blockIdx.x - (i ? g.nblk0 : 0), &g.t[i]);
 }

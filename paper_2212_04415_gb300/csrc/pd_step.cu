@@ -743,6 +743,7 @@ static void free_state(pd_state *st) {
     cudaFree(st->slice_nv);
     cudaFree(st->ids);
     cudaFree(st->st_tmpl);
+    cudaFree(st->st_dirty);
     cudaFree(st->st_box);
     cudaFree(st->col_csr);
     cudaFree(st->xi_tab);

@@ -77,7 +77,7 @@ static std::vector<pd_schedule> candidates(const pd_grid *g, const pd_material *
         for (int ns = batch >= 2 ? 2 : 1; ns >= 1; --ns) {
             if ((size_t)14 * (by + 6) * (bz + zhalo) * 32 * ns > 200 * 1024) continue;
             for (int q = 1; q <= (g->nz == 1 ? 1 : 4); q *= 2)  // the planar stencil runs at q = 1
-                if (32 * wpb * q <= 512) out.push_back(pd_schedule{by, bz, q, ns, 0});
+                if (32 * wpb * q <= (q == 2 && ns == 1 ? 256 : 512)) out.push_back(pd_schedule{by, bz, q, ns, 0});
         }
     }
     return out;
