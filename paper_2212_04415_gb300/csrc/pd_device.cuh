@@ -71,6 +71,7 @@ struct StepArgs {
     double *pk2;           // [2][B]: peak reaction so far, double-buffered the same way
     int32_t *ps2;          // [2][B]: its step
     int par;               // this launch reads buffer par and writes buffer 1 - par
+    int rec_off;           // step parity of the live samples = par ^ rec_off (set by the last reset or load)
     int defer;             // stencil path: leave this step's reaction to the next launch
     int pendable;          // stencil path: some launch of this state may defer (blocks build run views)
     const int32_t *brick_ridx;  // [n_bricks]: index among the reaction bricks, or -1

@@ -142,6 +142,8 @@ struct pd_state {
     int32_t *ps2;       // [2][B]: its step
     int32_t bk_par;     // buffer holding the current step/done
     int32_t chunk_par;  // parity the captured chunk starts from
+    int32_t rec_off;    // step parity of the live samples = bk_par ^ rec_off (reset: 0 at bk_par; load: step & 1)
+    int32_t chunk_rec_off;  // rec_off the captured chunk was made with
     int32_t *brick_ridx;  // [n_bricks]: index among reaction bricks, or -1
     int32_t nrb;          // reaction bricks (bricks with prescribed DOFs, and brick 0)
     int32_t *status;    // [B] bit 0: non-finite reaction

@@ -618,6 +618,40 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
     // has completed and its writes are visible (both are no-ops otherwise).
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int bxy = fdiv(brick, a.fd_nbx), bz = fdiv(bxy, a.fd_nby);
+    const int bx = brick - a.nbx * bxy, by = bxy - a.nby * bz;
+    const int x0 = kSlice * bx, y0 = a.BY * by, z0 = a.BZ * bz;
+    const size_t BN = (size_t)a.B * a.N;
+    const int Wy = a.BY + 2 * kHalo;
+    const int Zp = a.BZ + HZ;    // layers of each copy: upper (sub-lane 0) and reflected lower (sub-lane 1)
+    const int LB = RB * Wy, LK = RK * Wy;
+    // record copies on 128-byte boundaries (TMA destinations), then the kappa
+    // copies (KAPPA) and the parts' partial sums (Q > 1)
+    const int CP = (LB * Zp + 127) & ~127;
+    const int pad = (int)((0u - sm_addr(g_box)) & 127u);
+    const int oP = pad, oM = pad + CP;
+    const int okP = pad + 2 * CP, okM = okP + LK * Zp;
+    const int oPart = KAPPA ? okM + LK * Zp : okP;
+    float *s_part = (float *)((char *)g_box + oPart);  // [Q-1][wpb][16][6 NS]
+    // One-sample steps: every live sample of the state is at the step parity
+    // a.par ^ a.rec_off (the launch parity and the offset set by the last
+    // reset or load), which selects the record buffer to stage; the box's TMA
+    // copies go out at once, before the per-sample bookkeeping is read (whose
+    // step index is checked against it below). Force-only evaluations, which
+    // include samples stopped at other steps, stage after reading it.
+    constexpr bool kEarly = NS == 1 && !FORCE_ONLY;
+    const int rpar = (a.par ^ a.rec_off) & 1;
+    const auto issue_box = [&](int par0) {
+        stage_bar_init(&s_bar);
+        stage_bar_expect(&s_bar, 2u * (uint32_t)(LB * Zp));
+        const int b0 = sample_of(0);
+        stage_box((char *)g_box + oP, &maps->rec[par0], x0 - kHalo, y0 - kHalo, z0, b0, &s_bar);
+        stage_box((char *)g_box + oM, &maps->ref[par0], a.nx - kSlice - kHalo - x0, a.ny - a.BY - kHalo - y0,
+                  a.nz - a.BZ - z0, b0, &s_bar);
+    };
+    if constexpr (kEarly) {
+        if (threadIdx.x == 0) issue_box(rpar);
+    }
     int ns[NS];
     bool live[NS];
     bool any = false;
@@ -631,7 +665,11 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
         if (!FORCE_ONLY && real && dn && brick == 0 && threadIdx.x == 0) carry_done(a, b);
         any = any || live[s];
     }
-    if (!any) return;  // block-uniform
+    if (!any) {  // block-uniform
+        if (kEarly && threadIdx.x == 0) stage_bar_wait(&s_bar);  // the copies land before the block leaves
+        return;
+    }
+    if (kEarly && threadIdx.x == 0 && (ns[0] & 1) != rpar) atomicOr(&a.status[sample_of(0)], 4);
     if (threadIdx.x == 0) s_ridx = FORCE_ONLY ? -1 : a.brick_ridx[brick];
     const int n_mine = (NS == 2 && threadIdx.x == 1) ? ns[NS - 1] : ns[0];  // the step of sample threadIdx.x
     if (threadIdx.x < NS) s_n[threadIdx.x] = n_mine;
@@ -665,21 +703,6 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
         s_pre[threadIdx.x][3] = vp.lo;
         s_cnt[threadIdx.x] = 0u;
     }
-    const int bxy = fdiv(brick, a.fd_nbx), bz = fdiv(bxy, a.fd_nby);
-    const int bx = brick - a.nbx * bxy, by = bxy - a.nby * bz;
-    const int x0 = kSlice * bx, y0 = a.BY * by, z0 = a.BZ * bz;
-    const size_t BN = (size_t)a.B * a.N;
-    const int Wy = a.BY + 2 * kHalo;
-    const int Zp = a.BZ + HZ;    // layers of each copy: upper (sub-lane 0) and reflected lower (sub-lane 1)
-    const int LB = RB * Wy, LK = RK * Wy;
-    // record copies on 128-byte boundaries (TMA destinations), then the kappa
-    // copies (KAPPA) and the parts' partial sums (Q > 1)
-    const int CP = (LB * Zp + 127) & ~127;
-    const int pad = (int)((0u - sm_addr(g_box)) & 127u);
-    const int oP = pad, oM = pad + CP;
-    const int okP = pad + 2 * CP, okM = okP + LK * Zp;
-    const int oPart = KAPPA ? okM + LK * Zp : okP;
-    float *s_part = (float *)((char *)g_box + oPart);  // [Q-1][wpb][16][6 NS]
 
     // The dirty bits of this thread's lane and part (byte `part` of the lane's
     // word holds the part's groups of 8 rounds from bit 0), read before the
@@ -699,15 +722,8 @@ __device__ __forceinline__ void step_block(const StepArgs &a, const int blk, con
     // cell at (x, y, z) of the reflected grid is (nx-1-x, ny-1-y, nz-1-z)).
     {
         const int par0 = ns[0] & 1;
-        if constexpr (NS == 1) {
-            if (threadIdx.x == 0) {
-                stage_bar_init(&s_bar);
-                stage_bar_expect(&s_bar, 2u * (uint32_t)(LB * Zp));
-                const int b0 = sample_of(0);
-                stage_box((char *)g_box + oP, &maps->rec[par0], x0 - kHalo, y0 - kHalo, z0, b0, &s_bar);
-                stage_box((char *)g_box + oM, &maps->ref[par0], a.nx - kSlice - kHalo - x0,
-                          a.ny - a.BY - kHalo - y0, a.nz - a.BZ - z0, b0, &s_bar);
-            }
+        if constexpr (NS == 1 && !kEarly) {
+            if (threadIdx.x == 0) issue_box(par0);
         }
         if constexpr (NS == 2 || KAPPA) {
             const int nbox = kWx * Wy * (a.BZ + 2 * HZ);

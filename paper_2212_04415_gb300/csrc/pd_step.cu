@@ -654,6 +654,7 @@ static StepArgs make_args(const pd_state *st) {
     a.ps2 = st->ps2;
     a.defer = 0;
     a.pendable = st->stencil && st->st_defer;
+    a.rec_off = st->rec_off;
     a.status = st->status;
     a.peak = st->peak;
     a.peak_step = st->peak_step;
@@ -965,6 +966,7 @@ static int build_state(pd_state *st, const int32_t *row_ptr, const int32_t *col)
     PD_CHECK_CUDA(cudaMemset(st->done, 0, 2 * (size_t)B * sizeof(int32_t)));
     PD_CHECK_CUDA(cudaMemset(st->step, 0, 2 * (size_t)B * sizeof(int32_t)));
     st->bk_par = 0;
+    st->rec_off = 0;
     // reaction bricks: those holding a prescribed DOF, plus brick 0
     {
         std::vector<uint8_t> hc((size_t)3 * N);
@@ -1219,6 +1221,7 @@ static int state_reset(pd_state *st, const float *s0, const double *s0d, const f
                                                   st->status, st->peak, st->peak_step,
                                                   st->ticket, 0);
     PD_CHECK_LAUNCH();
+    st->rec_off = st->bk_par;  // step 0 at the next launch's parity
     return PD_OK;
 }
 
@@ -1242,6 +1245,7 @@ extern "C" int pd_state_load(pd_state *st, const double *u, const double *v, con
                                                   st->status, st->peak, st->peak_step,
                                                   st->ticket, step);
     PD_CHECK_LAUNCH();
+    st->rec_off = st->bk_par ^ (step & 1);
     if (f64)
         k_load_u<true><<<blocks_for(NB), 256, 0, s>>>(st->N, st->B, u, v, st->u64, st->v64, st->vdf, st->step + st->bk_par * st->B,
                                                       st->rec[0], st->rec[1]);
@@ -1324,7 +1328,8 @@ extern "C" int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int
     PD_REQUIRE(max_steps >= 0, "max_steps must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
     const int chunk = 64;
-    if (!st->chunk_exec || st->chunk_max_steps != max_steps || st->chunk_par != st->bk_par) {
+    if (!st->chunk_exec || st->chunk_max_steps != max_steps || st->chunk_par != st->bk_par ||
+        st->chunk_rec_off != st->rec_off) {
         if (st->chunk_exec) {
             cudaGraphExecDestroy(st->chunk_exec);
             st->chunk_exec = nullptr;
@@ -1359,6 +1364,7 @@ extern "C" int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int
         st->chunk_steps = chunk;
         st->chunk_max_steps = max_steps;
         st->chunk_par = st->bk_par;
+        st->chunk_rec_off = st->rec_off;
     }
     k_run_init<<<blocks_for(st->B), 256, 0, s>>>(st->B, st->step + st->bk_par * st->B, st->done + st->bk_par * st->B,
                                                  max_steps);
@@ -1383,6 +1389,9 @@ extern "C" int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int
     for (int b = 0; b < st->B; ++b)
         if (status[b] & 2) {
             set_error("the staged box of a stencil step of sample %d did not arrive (bounded wait expired)", b);
+            return PD_ERR_CUDA;
+        } else if (status[b] & 4) {
+            set_error("sample %d was staged from the records of the wrong step parity", b);
             return PD_ERR_CUDA;
         } else if (status[b] & 1) {
             set_error("non-finite reaction in sample %d", b);
@@ -1541,6 +1550,9 @@ extern "C" int pd_run_to_peak_multi(pd_state *const *states, int32_t n_states, c
             if (status[i][b] & 2) {
                 set_error("the staged box of a stencil step of sample %d of state %d did not arrive (bounded wait "
                           "expired)", b, i);
+                return PD_ERR_CUDA;
+            } else if (status[i][b] & 4) {
+                set_error("sample %d of state %d was staged from the records of the wrong step parity", b, i);
                 return PD_ERR_CUDA;
             } else if (status[i][b] & 1) {
                 set_error("non-finite reaction in sample %d of state %d", b, i);
