@@ -46,11 +46,11 @@ L2_FLUSH_BYTES = 256 << 20
 # this program), reported only while the kernel's sources are the ones captured
 # (compared as code: comments and whitespace do not count).
 NCU_STEP_TRAFFIC = {
-    "bytes": 17_211_392 + 61_184,
+    "bytes": 18_028_288 + 0,
     "sources": {
-        "paper_2212_04415_gb300/csrc/pd_stencil_kernel.cuh": "73f952987c58b94b9474d36164be921e75d864f0036bd29c2d65a19320263d9d",
-        "paper_2212_04415_gb300/csrc/pd_stencil.cu": "b5a91b35d2556f49b4f93954eef05b6ddcc9f7ad51a480f97b9954877735cff5",
-        "paper_2212_04415_gb300/csrc/pd_device.cuh": "037f205b0d30834526582ee7b5b395405705edb13d1361c2cfde77c0327b08c7",
+        "paper_2212_04415_gb300/csrc/pd_stencil_kernel.cuh": "f2590149e80eea9b83c0bb4effc50c9c19a9f748032ea361927d03c7ad0212c3",
+        "paper_2212_04415_gb300/csrc/pd_stencil.cu": "e26b2a271f750ee7b22ef8def94652607dfad11d38f89755015c8d59a873e415",
+        "paper_2212_04415_gb300/csrc/pd_device.cuh": "f678545afa7ab7e5e73b3fc95e621bd4ed4eea985def02eb65dc1553616e808e",
     },
 }
 
@@ -294,7 +294,8 @@ def sweep_leg(pd, W, hbm, steps: int = 10, warmup: int = 3):
     """Size-effect sweep, batched (64 samples per launch): geometrically similar
     notched beams D = 50 ... 400 mm at dx = 2.5 mm (up to 1.79M nodes, 204M
     bonds per sample). The working set (up to ~70 GB) is far above L2, so
-    these launches show the step in the HBM regime. A bounded number of steps
+    these launches show the step in the HBM regime. Each size takes the
+    autotuned launch schedule (tuned before timing); a bounded number of steps
     from rest is timed per size (the first steps are elastic: few history
     writes)."""
     import torch
@@ -308,7 +309,8 @@ def sweep_leg(pd, W, hbm, steps: int = 10, warmup: int = 3):
         fld = pd.Field(g, 1, w.field)
         xi = pd.draw_xi(w.seed, 0, torch.arange(B, dtype=torch.int64, device="cuda"), w.field.n_modes)
         s0 = fld.sample(0, xi)
-        st = pd.State(g, row, col, w.mat, w.bc, batch=B)
+        sched, _ = pd.autotune(g, row, col, w.mat, w.bc, batch=B, trial_steps=3)  # before timing
+        st = pd.State(g, row, col, w.mat, w.bc, batch=B, schedule=sched)
         st.reset(s0)
         st.step(warmup, reaction=False)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -319,7 +321,8 @@ def sweep_leg(pd, W, hbm, steps: int = 10, warmup: int = 3):
         torch.cuda.synchronize()
         per = e0.elapsed_time(e1) * 1e-3 / steps
         alg = B * (nb * (4.0 + 4.0 / B) + g.n_nodes * 108.0)
-        out.append({"D_mm": D, "nodes": g.n_nodes, "bonds": nb, "samples_per_launch": B, "ms_per_step": 1e3 * per,
+        out.append({"D_mm": D, "nodes": g.n_nodes, "bonds": nb, "samples_per_launch": B, "schedule": list(sched),
+                    "ms_per_step": 1e3 * per,
                     "bond_updates_per_s": B * nb / per, "algorithmic_gbs": alg / per / 1e9,
                     "hbm_frac": alg / per / 1e9 / hbm})
         st.close()
@@ -353,7 +356,8 @@ def size_effect_leg(pd, W, hbm, sizes=(50.0, 100.0, 200.0, 400.0), max_steps: in
         fld = pd.Field(g, 1, w.field)
         xi = pd.draw_xi(w.seed, 0, torch.arange(B, dtype=torch.int64, device="cuda"), w.field.n_modes)
         s0 = fld.sample(0, xi)
-        st = pd.State(g, row, col, w.mat, w.bc, batch=B)
+        sched, _ = pd.autotune(g, row, col, w.mat, w.bc, batch=B, trial_steps=3)  # before timing
+        st = pd.State(g, row, col, w.mat, w.bc, batch=B, schedule=sched)
         st.reset(s0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -368,7 +372,7 @@ def size_effect_leg(pd, W, hbm, sizes=(50.0, 100.0, 200.0, 400.0), max_steps: in
         steps_max = int(nd.max())
         # history and node state of every sample-step taken, the index once per launch
         alg = float(nd.sum()) * (nb * 4.0 + g.n_nodes * 108.0) + steps_max * nb * 4.0
-        out.append({"D_mm": D, "nodes": g.n_nodes, "bonds": nb, "samples": B,
+        out.append({"D_mm": D, "nodes": g.n_nodes, "bonds": nb, "samples": B, "schedule": list(sched),
                     "sigma_N_mean_MPa": stats.fmean(sig), "sigma_N_std_MPa": stats.stdev(sig),
                     "peak_mean_N": float(pk.mean()), "peak_step_mean": float(ps.mean()),
                     "steps_mean": float(nd.mean()), "steps_max": steps_max, "wall_s": wall,

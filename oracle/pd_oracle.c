@@ -384,7 +384,11 @@ static void forces(const or_problem *p, const double *u, double *d, double *F,
             double cij = p->c;
             if (p->kappa) cij = p->c * 0.5 * (p->kappa[i] + p->kappa[j]);
             double f = cij * (1.0 - d[q]) * s;
-            for (int c = 0; c < 3; ++c) Fi[c] += f * V * y[c] / L;
+            /* A fully damaged bond carries no force (f = c (1 - d) s = 0, the
+             * bond law of Appendix A): its direction y / L is not needed, and
+             * it is undefined once the bond has collapsed to zero length. */
+            if (d[q] < 1.0)
+                for (int c = 0; c < 3; ++c) Fi[c] += f * V * y[c] / L;
         }
         for (int c = 0; c < 3; ++c) F[3 * i + c] = Fi[c];
         smn[i] = sm;

@@ -147,6 +147,10 @@ __device__ __forceinline__ float2 splat<float2>(float x) { return make_float2(x,
 template <class V>
 __device__ __forceinline__ V vsub(V a, V b) { return vfma(b, splat<V>(-1.0f), a); }
 
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float2 vmax(float2 a, float2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
+constexpr float kMinY2 = 1e-12f;
+
 __device__ __forceinline__ float neg(float a) { return -a; }
 __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
 
@@ -370,7 +374,12 @@ __device__ __forceinline__ void bond_kin(const Ctx &cx, const Rec<V> &r, int kx,
     const V wy = ky ? vadd(ey, splat<V>(2.0f * ky)) : ey;
     const V wz = kz ? vadd(ez, splat<V>(2.0f * kz)) : ez;
     const V num = vfma(ez, wz, vfma(ey, wy, vmul(ex, wx)));
-    const V y2 = vadd(num, splat<V>(KW2));
+    // |y|^2, kept at or above 1e-12 (cell units): the floor only acts on a
+    // bond shorter than a millionth of a cell. A broken bond compressed to
+    // zero length under a crushing load can reach |y|^2 <= 0 in FP32, where
+    // 1/|y| would be infinite and (1 - d) s / |y| = 0 x inf not a number;
+    // with the floor its force is exactly zero, as a broken bond's must be.
+    const V y2 = vmax(vadd(num, splat<V>(KW2)), splat<V>(kMinY2));
     rL = vrsqrt(y2);
     const V L = vmul(y2, rL);
     s = vmul(num, vrcp(vfma(L, splat<V>(KW), splat<V>(KW2))));

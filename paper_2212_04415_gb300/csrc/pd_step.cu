@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
                         }
                         double cv = a.cV;
                         if (KAPPA) cv = a.cV * 0.5 * (kap_i + (double)a.kappa[(size_t)b * a.N + j]);
-                        const double g = cv * (1.0 - d) * s / L;
+                        // a broken bond carries no force (its direction is undefined at L = 0)
+                        const double g = d < 1.0 ? cv * (1.0 - d) * s / L : 0.0;
                         Fx += g * yx;
                         Fy += g * yy;
                         Fz += g * yz;
@@ -246,7 +247,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_step(const StepArgs a) {
                                 }
                                 float cv = cVf;
                                 if (KAPPA) cv = cVf * 0.5f * (lo.w + lj.w);
-                                const float g = cv * (1.0f - d) * s * rL;
+                                // a broken bond carries no force (its direction is undefined at |y| = 0)
+                                const float g = d < 1.0f ? cv * (1.0f - d) * s * rL : 0.0f;
                                 px += g * yx;
                                 py += g * yy;
                                 pz += g * yz;

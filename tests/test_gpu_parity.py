@@ -106,6 +106,35 @@ def test_force_and_damage_parity(pd, prec, law, shape):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+def test_broken_bond_collapsed_to_zero_length(pd, prec):
+    """A broken bond (d = 1) squeezed to zero length carries no force on the
+    GPU either: the forces and damage stay finite and match the oracle's
+    (node j is placed on node i, as under a crushing load)."""
+    w = W.tiny_beam(16, 6, 4)
+    orow, ocol, s0, u, v, d = _random_case(w, 1, 41)
+    g = w.grid
+    i = 3 + g.nx * (2 + g.ny * 1)
+    j = i + 1
+    u[0][j] = u[0][i] - np.array([g.dx, 0.0, 0.0])
+    for a, b in ((i, j), (j, i)):
+        q = orow[a] + int(np.nonzero(ocol[orow[a]:orow[a + 1]] == b)[0][0])
+        d[0][q] = 1.0
+    row, col = pd.build_neighbours(g)
+    st = pd.State(g, row, col, w.mat, w.bc, batch=1, precision=prec)
+    st.reset(_dev(s0))
+    st.load(_dev(u), _dev(v), _dev(d), step=0)
+    F = st.force().cpu().numpy()[0]
+    dg = st.store()[2].cpu().numpy()[0]
+    st.close()
+    m = core.Model(w, orow, ocol, s0=s0[0].astype(np.float64))
+    Fo, do, _ = m.force(u[0], d[0])
+    assert np.all(np.isfinite(F)) and np.all(np.isfinite(Fo))
+    tol = 1e-10 if prec == 0 else 1e-5
+    assert np.abs(F - Fo).max() <= tol * np.abs(Fo).max()
+    assert np.abs(dg - do).max() <= tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_steps_from_random_state(pd, prec):
     w = W.tiny_beam(13, 7, 5)
     orow, ocol, s0, u, v, d = _random_case(w, 3, 33)

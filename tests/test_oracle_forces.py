@@ -140,3 +140,26 @@ def test_stable_dt_closed_form():
               for c in range(-3, 4) if 0 < a * a + b * b + c * c <= 9) / g.dx
     expect = 0.5 * math.sqrt(2 * w.mat.rho / (m.c * g.dx ** 3 * inv))
     assert abs(m.dt - expect) <= 1e-13 * expect
+
+
+def test_broken_bond_at_zero_length_carries_no_force():
+    """A fully damaged bond contributes nothing, even when it has collapsed to
+    zero length (its direction is undefined there): the forces stay finite and
+    equal those of the same configuration with the broken bond a hair apart."""
+    w = _tiny()
+    m = core.Model(w)
+    x = _coords(w.grid)
+    i = 2 + w.grid.nx * (2 + w.grid.ny * 2)     # interior node
+    j = i + 1                                   # its +x neighbour
+    d = np.zeros(m.nb)
+    for a, b in ((i, j), (j, i)):
+        q = m.row[a] + int(np.nonzero(m.col[m.row[a]:m.row[a + 1]] == b)[0][0])
+        d[q] = 1.0
+    u = np.zeros((m.n, 3))
+    u[j] = x[i] - x[j]                          # node j sits on node i
+    F, _, _ = m.force(u, d)
+    assert np.all(np.isfinite(F))
+    u2 = u.copy()
+    u2[j, 1] += 1e-9 * w.grid.dx                # the broken bond a hair apart
+    F2, _, _ = m.force(u2, d)
+    assert np.abs(F - F2).max() <= 1e-6 * np.abs(F2).max()
