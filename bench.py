@@ -567,8 +567,16 @@ def main():
         torch.cuda.synchronize()
         bs = e0.elapsed_time(e1) / 1e3
         bu = float(ndb.sum().item()) * nb
+        # algorithmic bytes of the whole batched run: history and node state of every
+        # sample-step taken, the index once per launch (as in the size-effect study)
+        hbm_b, kind_b = _peaks()
+        alg_b = float(ndb.sum().item()) * (nb * 4.0 + g.n_nodes * 108.0) + float(ndb.max().item()) * nb * 4.0
         batched = {"samples_per_launch": Bb, "value": bu / bs, "unit": METRIC, "samples_per_s": Bb / bs,
-                   "plain_samples_per_s": args.steps / dev_s, "ms": 1e3 * bs}
+                   "plain_samples_per_s": args.steps / dev_s, "ms": 1e3 * bs,
+                   "roofline": {"bound": "hbm", "achieved": alg_b / bs / 1e9, "peak": hbm_b, "unit": "GB/s",
+                                "frac": alg_b / bs / 1e9 / hbm_b, "peak_kind": kind_b,
+                                "note": "algorithmic bytes of the whole run to the peak (softening and the "
+                                        "host poll per 64-step chunk included) over its device time"}}
         stb.close()
 
     hbm, peak_kind = _peaks()

@@ -266,7 +266,11 @@ PD_API int pd_step(pd_state *st, int32_t n_steps, double *reaction, pd_stream st
  * R_n < Q/2 with Q > 0 and at least 100 steps after the peak.
  * Outputs (device): peak double[B], peak_step int32[B], n_done int32[B]
  * (steps executed). Host-synchronous (the host polls completion once per
- * chunk of captured steps). */
+ * chunk of captured steps). Errors after the run: PD_ERR_NAN if a sample's
+ * reaction became non-finite; PD_ERR_CUDA if a staged box of the stencil
+ * step did not arrive within its bounded wait, or if a sample was stepped at
+ * a step parity other than the one its state's last reset or load implies
+ * (both internal checks; the run's outputs are then not to be used). */
 PD_API int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int32_t *peak_step,
                    int32_t *n_done, pd_stream stream);
 

@@ -80,3 +80,50 @@ def test_mlmc_levels_of_one_sample(pd):
     assert res["levels"][1]["mean"] == pytest.approx(y[1], rel=1e-14)
     mean, var_b, _ = omlmc.level_stats(np.array([y[1]]))
     assert var_b == 0.0 and mean == pytest.approx(y[1], rel=1e-14)
+
+
+def test_run_to_peak_after_an_odd_number_of_steps(pd):
+    """A run to the peak that starts after three plain steps (odd step
+    parity, so the captured chunks start from the other record buffer) gives
+    the same peak, peak step, step count and final state as the
+    uninterrupted run; so does a second state loaded at an odd step."""
+    w = W.tiny_beam(16, 6, 4, n_steps=400)
+    g = w.grid
+    row, col = pd.build_neighbours(g)
+    s0 = _dev(W.lognormal_like_field(g.n_nodes, 2, 17))
+
+    def run(pre):
+        st = pd.State(g, row, col, w.mat, w.bc, batch=2)
+        st.reset(s0)
+        if pre:
+            st.step(pre)
+        out = [x.clone() for x in st.run_to_peak(w.n_steps)]
+        state = st.store()
+        st.close()
+        return out, state
+
+    (pk0, ps0, nd0), (u0, v0, d0) = run(0)
+    (pk3, ps3, nd3), (u3, v3, d3) = run(3)
+    assert torch.equal(pk0, pk3) and torch.equal(ps0, ps3) and torch.equal(nd0, nd3)
+    assert torch.equal(u0, u3) and torch.equal(v0, v3) and torch.equal(d0, d3)
+    assert int(nd0.max()) > 64  # several captured chunks
+
+    # a state loaded at step 7 from the 7-step state of the same run continues it bit for bit
+    st = pd.State(g, row, col, w.mat, w.bc, batch=2)
+    st.reset(s0)
+    st.step(7)
+    u7, v7, d7 = st.store()
+    st.close()
+    st2 = pd.State(g, row, col, w.mat, w.bc, batch=2)
+    st2.reset(s0)
+    st2.load(u7, v7, d7, step=7)
+    R_a = st2.step(40)
+    ua = st2.store()[0]
+    st2.close()
+    st = pd.State(g, row, col, w.mat, w.bc, batch=2)
+    st.reset(s0)
+    st.step(7)
+    R_b = st.step(40)
+    ub = st.store()[0]
+    st.close()
+    assert torch.equal(R_a, R_b) and torch.equal(ua, ub)
