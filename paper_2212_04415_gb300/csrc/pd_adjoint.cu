@@ -271,11 +271,17 @@ __global__ void k_sell_slots(long long len, const int32_t *q_of, const int32_t *
     dslot[x] = q >= 0 ? slot[q] : 0;
 }
 
-__global__ void k_gather_dmg(long long len, long long dlen, const int32_t *dslot, const float *dmg, float *out) {
-    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= len) return;
+// One block per slice of 32 nodes and sample, over all the slice's slots: the
+// slice's damage words lie in a few kilobytes of the stencil array (two lanes
+// of its nodes' warps), so they are read through L1 once instead of one
+// partly used sector per slot from L2.
+__global__ void k_gather_dmg(long long len, long long dlen, const long long *off, const int32_t *dslot,
+                             const float *dmg, float *out) {
+    const long long a0 = off[blockIdx.x], a1 = off[blockIdx.x + 1];
     const int b = blockIdx.y;
-    out[(size_t)b * len + x] = dmg[(size_t)b * dlen + dslot[x]];
+    const float *src = dmg + (size_t)b * dlen;
+    float *dst = out + (size_t)b * len;
+    for (long long x = a0 + threadIdx.x; x < a1; x += blockDim.x) dst[x] = __ldg(src + dslot[x]);
 }
 
 // The same from an FP64 CSR-order array (the generic layout's store).
@@ -499,6 +505,7 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
     DevBuf<float2> ld2;
     DevBuf<int32_t> slot, q_of, j_of, dslot;
     DevBuf<long long> sl_off;
+    long long nsl = 0;  // slices of 32 nodes (mixed path)
     long long SL = 0;  // sliced-ELL slots per sample
     const bool f32 = st->mat.precision == PD_PREC_MIXED;
     const long long BN = (long long)B * N;
@@ -515,7 +522,7 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
         // sliced ELL of the CSR rows (slice widths on the host)
         std::vector<int32_t> hrow(N + 1);
         PD_CHECK_CUDA(cudaMemcpy(hrow.data(), st->row_ptr, (N + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        const long long nsl = (N + 31) / 32;
+        nsl = (N + 31) / 32;
         std::vector<long long> hoff(nsl + 1, 0);
         for (long long sl = 0; sl < nsl; ++sl) {
             int w = 0;
@@ -628,7 +635,8 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
             PD_CHECK_LAUNCH();
         }
         if (st->stencil) {
-            k_gather_dmg<<<grid_sl, 256, 0, s>>>(SL, st->st_len, dslot.p, (const float *)st->dmg, d32);
+            k_gather_dmg<<<dim3((unsigned)nsl, (unsigned)B), 256, 0, s>>>(SL, st->st_len, sl_off.p, dslot.p,
+                                                                          (const float *)st->dmg, d32);
         } else {
             PD_TRY(pd_state_store(st, nullptr, nullptr, tr_d.p, stream));
             k_gather_csr<<<grid_sl, 256, 0, s>>>(SL, nb, q_of.p, tr_d.p, d32);
