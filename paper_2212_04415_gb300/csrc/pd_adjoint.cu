@@ -310,10 +310,15 @@ __device__ __forceinline__ void fold(float &s, float &c, float x) {
 // FP64 node sums. Capped at 64 registers (32 warps per SM; the kernel waits
 // on its gathers): measured on GB300 2.11 against 2.24 ms per adjoint step
 // with the compiler's 80.
-__global__ void __launch_bounds__(256, 4) k_adj_bonds_f32(const AdjArgs a, long long sl_len, const long long *off,
-                                                       const int32_t *j_of, const float4 *u4, const float *dprev,
-                                                       const float *dcur, const float4 *lF4, float2 *ld,
-                                                       double *lun, double *g_s0, double *g_k) {
+__global__ void __launch_bounds__(256, 4) k_adj_bonds_f32(const AdjArgs a, long long sl_len,
+                                                       const long long *__restrict__ off,
+                                                       const int32_t *__restrict__ j_of,
+                                                       const float4 *__restrict__ u4,
+                                                       const float *__restrict__ dprev,
+                                                       const float *__restrict__ dcur,
+                                                       const float4 *__restrict__ lF4, float2 *__restrict__ ld,
+                                                       double *__restrict__ lun, double *__restrict__ g_s0,
+                                                       double *__restrict__ g_k) {
     __shared__ float s_L0[64], s_iL0[64];
     if (threadIdx.x < 64) {
         s_L0[threadIdx.x] = a.L0q[threadIdx.x];
@@ -327,16 +332,18 @@ __global__ void __launch_bounds__(256, 4) k_adj_bonds_f32(const AdjArgs a, long 
     const float4 *ub = u4 + (size_t)b * a.N;
     const float4 *lb4 = lF4 + (size_t)b * a.N;
     const size_t db = (size_t)b * sl_len;
-    const int ci = a.coord[i];
+    const int32_t *__restrict__ coord = a.coord;
+    const int ci = coord[i];
     const float4 me = ub[i], ml = lb4[i];
     const long long base = off[i >> 5] + (i & 31);
     const int W = (int)((off[(i >> 5) + 1] - off[i >> 5]) >> 5);  // slots of the slice
     float S[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, Cc[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, P[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
     for (int p = 0; p < W; ++p) {
         const long long x = base + 32ll * p;
         const int j = j_of[x];
         if (j >= 0) {
-            const int cj = a.coord[j];
+            const int cj = coord[j];
             const int kx = (cj & 2047) - (ci & 2047), ky = ((cj >> 11) & 2047) - ((ci >> 11) & 2047),
                       kz = (cj >> 22) - (ci >> 22);
             const int q2 = kx * kx + ky * ky + kz * kz;
