@@ -297,7 +297,9 @@ PD_API int pd_run_to_peak(pd_state *st, int32_t max_steps, double *peak, int32_t
  * k 3N + (k + 1) n_b doubles and n_b doubles of damage adjoint, for
  * mixed-path states 16 k N + 4 (k + 1) S bytes of FP32 trajectory (S the
  * slots of a sliced-ELL copy of the rows, slices of 32 nodes padded to the
- * longest row, about n_b) and 8 S bytes of double-float damage adjoint.
+ * longest row, about n_b), 8 S bytes of double-float damage adjoint and S
+ * bytes marking the bonds whose damage grows in the run (only those carry a
+ * damage adjoint).
  * Arithmetic: FP64 for FP64-path states; for mixed-path states the bond terms
  * in FP32 on the FP32 trajectory (the forward path's own precision class),
  * the damage adjoint in double-float, the node sums in FP64. The states come

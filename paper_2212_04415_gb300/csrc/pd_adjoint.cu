@@ -293,6 +293,18 @@ __global__ void k_gather_csr(long long len, long long nb, const int32_t *q_of, c
     out[(size_t)b * len + x] = q >= 0 ? (float)csr[(size_t)b * nb + q] : 0.f;
 }
 
+// Slots (sliced-ELL order) of the bonds whose damage grows somewhere in the
+// run: damage never decreases, so a bond whose final damage equals its
+// initial one is never active, and its damage adjoint is never consumed.
+__global__ void k_grows(long long len, long long nb, const int32_t *q_of, const double *d_first,
+                        const double *d_last, uint8_t *grows) {
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= len) return;
+    const int b = blockIdx.y;
+    const int q = q_of[x];
+    grows[(size_t)b * len + x] = q >= 0 && d_last[(size_t)b * nb + q] > d_first[(size_t)b * nb + q];
+}
+
 // s + x accumulated with the rounding error carried in c (Knuth's TwoSum).
 __device__ __forceinline__ void fold(float &s, float &c, float x) {
     const float t = s + x;
@@ -316,7 +328,8 @@ __global__ void __launch_bounds__(256, 4) k_adj_bonds_f32(const AdjArgs a, long 
                                                        const float4 *__restrict__ u4,
                                                        const float *__restrict__ dprev,
                                                        const float *__restrict__ dcur,
-                                                       const float4 *__restrict__ lF4, float2 *__restrict__ ld,
+                                                       const float4 *__restrict__ lF4,
+                                                       const uint8_t *__restrict__ grows, float2 *__restrict__ ld,
                                                        double *__restrict__ lun, double *__restrict__ g_s0,
                                                        double *__restrict__ g_k) {
     __shared__ float s_L0[64], s_iL0[64];
@@ -369,8 +382,14 @@ __global__ void __launch_bounds__(256, 4) k_adj_bonds_f32(const AdjArgs a, long 
             const float cijV = a.kappa ? cV * 0.5f * (ml.w + lj.w) : cV;
             const float dp = dprev[db + x], dc = dcur[db + x];
             const bool active = dc > dp;
-            const float2 l0 = ld[db + x];
-            const df lamd = df_add(df{l0.x, l0.y}, df{cijV * h * ydl, 0.f});
+            // the damage adjoint of a bond that never grows in the run is never
+            // used: it is neither read nor written (a bond is active only if it grows)
+            const bool gw = grows[db + x] != 0;
+            df lamd = {0.f, 0.f};
+            if (gw) {
+                const float2 l0 = ld[db + x];
+                lamd = df_add(df{l0.x, l0.y}, df{cijV * h * ydl, 0.f});
+            }
             float dDds = 0.f, dDds0 = 0.f;
             if (active) law_derivs_f(a, s, s0, dDds, dDds0);
             const float lamdf = lamd.hi + lamd.lo;
@@ -381,7 +400,7 @@ __global__ void __launch_bounds__(256, 4) k_adj_bonds_f32(const AdjArgs a, long 
             for (int c = 0; c < 3; ++c) P[c] += cijV * om * (ydl * dhk * y[c] + h * dl[c]) - act * y[c];
             if (active) P[3] += 0.5f * lamdf * dDds0;
             P[4] += 0.5f * cV * (-om * h * ydl);
-            ld[db + x] = active ? make_float2(0.f, 0.f) : make_float2(lamd.hi, lamd.lo);
+            if (gw) ld[db + x] = active ? make_float2(0.f, 0.f) : make_float2(lamd.hi, lamd.lo);
         }
         if ((p & 7) == 7 || p + 1 == W) {
 #pragma unroll
@@ -512,6 +531,7 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
     DevBuf<float2> ld2;
     DevBuf<int32_t> slot, q_of, j_of, dslot;
     DevBuf<long long> sl_off;
+    DevBuf<uint8_t> grow8;  // mixed path: per sample and slot, the bond's damage grows in the run
     long long nsl = 0;  // slices of 32 nodes (mixed path)
     long long SL = 0;  // sliced-ELL slots per sample
     const bool f32 = st->mat.precision == PD_PREC_MIXED;
@@ -549,6 +569,7 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
         PD_TRY(dalloc(&tr_d32.p, (size_t)(k + 1) * B * SL));
         PD_TRY(dalloc(&lF4.p, BN));
         PD_TRY(dalloc(&ld2.p, (size_t)B * SL));
+        PD_TRY(dalloc(&grow8.p, (size_t)B * SL));
         if (st->stencil) {
             PD_TRY(dalloc(&slot.p, nb));
             PD_TRY(stencil_slot_table(st, slot.p, s));
@@ -579,6 +600,11 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
     }
     PD_TRY(pd_state_store(st, ck_u.p + (size_t)nseg * U3, ck_v.p + (size_t)nseg * U3, ck_d.p + (size_t)nseg * D1,
                           stream));
+    if (f32) {
+        k_grows<<<dim3((unsigned)((SL + 255) / 256), (unsigned)B), 256, 0, s>>>(SL, nb, q_of.p, ck_d.p,
+                                                                             ck_d.p + (size_t)nseg * D1, grow8.p);
+        PD_CHECK_LAUNCH();
+    }
 
     AdjArgs a;
     a.B = B;
@@ -675,7 +701,7 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
                 PD_CHECK_LAUNCH();
                 k_adj_bonds_f32<<<grid_nodes, 256, 0, s>>>(a, SL, sl_off.p, j_of.p, tr_u4.p + (size_t)m * BN,
                                                            tr_d32.p + (size_t)m * B * SL,
-                                                           tr_d32.p + (size_t)(m + 1) * B * SL, lF4.p, ld2.p, plun,
+                                                           tr_d32.p + (size_t)(m + 1) * B * SL, lF4.p, grow8.p, ld2.p, plun,
                                                            grad_s0, grad_kappa);
             } else {
                 k_adj_bonds<<<nblk_bond, 256, 0, s>>>(a, tr_u.p + (size_t)m * U3, tr_d.p + (size_t)m * D1,
