@@ -271,17 +271,24 @@ __global__ void k_sell_slots(long long len, const int32_t *q_of, const int32_t *
     dslot[x] = q >= 0 ? slot[q] : 0;
 }
 
+// Damage history of a slot over an adjoint run (k_grows).
+constexpr uint8_t kDmgZero = 0, kDmgGrows = 1, kDmgConst = 2;
+
 // One block per slice of 32 nodes and sample, over all the slice's slots: the
 // slice's damage words lie in a few kilobytes of the stencil array (two lanes
 // of its nodes' warps), so they are read through L1 once instead of one
-// partly used sector per slot from L2.
+// partly used sector per slot from L2. Only slots whose damage grows in the
+// run are gathered (code[] per sample and slot); the bond adjoint reads no
+// other slot of the trajectory.
 __global__ void k_gather_dmg(long long len, long long dlen, const long long *off, const int32_t *dslot,
-                             const float *dmg, float *out) {
+                             const uint8_t *code, const float *dmg, float *out) {
     const long long a0 = off[blockIdx.x], a1 = off[blockIdx.x + 1];
     const int b = blockIdx.y;
     const float *src = dmg + (size_t)b * dlen;
+    const uint8_t *cb = code + (size_t)b * len;
     float *dst = out + (size_t)b * len;
-    for (long long x = a0 + threadIdx.x; x < a1; x += blockDim.x) dst[x] = __ldg(src + dslot[x]);
+    for (long long x = a0 + threadIdx.x; x < a1; x += blockDim.x)
+        if (cb[x] == kDmgGrows) dst[x] = __ldg(src + dslot[x]);
 }
 
 // The same from an FP64 CSR-order array (the generic layout's store).
@@ -293,16 +300,24 @@ __global__ void k_gather_csr(long long len, long long nb, const int32_t *q_of, c
     out[(size_t)b * len + x] = q >= 0 ? (float)csr[(size_t)b * nb + q] : 0.f;
 }
 
-// Slots (sliced-ELL order) of the bonds whose damage grows somewhere in the
-// run: damage never decreases, so a bond whose final damage equals its
-// initial one is never active, and its damage adjoint is never consumed.
+// Damage history code of every slot (sliced-ELL order) over the run:
+// kDmgGrows if its damage grows somewhere in the run, else kDmgZero or
+// kDmgConst (its damage is the same at every step, zero or not). Damage
+// never decreases, so a bond whose final damage equals its initial one never
+// changes and is never active: its damage adjoint is never consumed, and its
+// damage at any step is its initial value (a padding slot is kDmgZero).
 __global__ void k_grows(long long len, long long nb, const int32_t *q_of, const double *d_first,
-                        const double *d_last, uint8_t *grows) {
+                        const double *d_last, uint8_t *code) {
     const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= len) return;
     const int b = blockIdx.y;
     const int q = q_of[x];
-    grows[(size_t)b * len + x] = q >= 0 && d_last[(size_t)b * nb + q] > d_first[(size_t)b * nb + q];
+    uint8_t c = kDmgZero;
+    if (q >= 0) {
+        const double d0 = d_first[(size_t)b * nb + q], d1 = d_last[(size_t)b * nb + q];
+        c = d1 > d0 ? kDmgGrows : (d0 != 0.0 ? kDmgConst : kDmgZero);
+    }
+    code[(size_t)b * len + x] = c;
 }
 
 // s + x accumulated with the rounding error carried in c (Knuth's TwoSum).
@@ -329,7 +344,10 @@ __global__ void __launch_bounds__(256, 4) k_adj_bonds_f32(const AdjArgs a, long 
                                                        const float *__restrict__ dprev,
                                                        const float *__restrict__ dcur,
                                                        const float4 *__restrict__ lF4,
-                                                       const uint8_t *__restrict__ grows, float2 *__restrict__ ld,
+                                                       const uint8_t *__restrict__ dcode,
+                                                       const int32_t *__restrict__ q_of,
+                                                       const double *__restrict__ d_first, long long nb,
+                                                       float2 *__restrict__ ld,
                                                        double *__restrict__ lun, double *__restrict__ g_s0,
                                                        double *__restrict__ g_k) {
     __shared__ float s_L0[64], s_iL0[64];
@@ -380,11 +398,20 @@ __global__ void __launch_bounds__(256, 4) k_adj_bonds_f32(const AdjArgs a, long 
             const float h = s * rL;
             const float s0 = 0.5f * (me.w + nj.w);
             const float cijV = a.kappa ? cV * 0.5f * (ml.w + lj.w) : cV;
-            const float dp = dprev[db + x], dc = dcur[db + x];
+            // damage at this step and the next: from the trajectory for a bond
+            // that grows in the run, else its constant value; the damage adjoint
+            // of a bond that never grows is never used, so it is neither read
+            // nor written (a bond is active only if it grows)
+            const uint8_t cd = dcode[db + x];
+            const bool gw = cd == kDmgGrows;
+            float dp = 0.f, dc = 0.f;
+            if (gw) {
+                dp = dprev[db + x];
+                dc = dcur[db + x];
+            } else if (cd == kDmgConst) {
+                dp = dc = (float)d_first[(size_t)b * nb + q_of[x]];
+            }
             const bool active = dc > dp;
-            // the damage adjoint of a bond that never grows in the run is never
-            // used: it is neither read nor written (a bond is active only if it grows)
-            const bool gw = grows[db + x] != 0;
             df lamd = {0.f, 0.f};
             if (gw) {
                 const float2 l0 = ld[db + x];
@@ -531,7 +558,7 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
     DevBuf<float2> ld2;
     DevBuf<int32_t> slot, q_of, j_of, dslot;
     DevBuf<long long> sl_off;
-    DevBuf<uint8_t> grow8;  // mixed path: per sample and slot, the bond's damage grows in the run
+    DevBuf<uint8_t> grow8;  // mixed path: per sample and slot, the damage history code (k_grows)
     long long nsl = 0;  // slices of 32 nodes (mixed path)
     long long SL = 0;  // sliced-ELL slots per sample
     const bool f32 = st->mat.precision == PD_PREC_MIXED;
@@ -669,7 +696,7 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
         }
         if (st->stencil) {
             k_gather_dmg<<<dim3((unsigned)nsl, (unsigned)B), 256, 0, s>>>(SL, st->st_len, sl_off.p, dslot.p,
-                                                                          (const float *)st->dmg, d32);
+                                                                          grow8.p, (const float *)st->dmg, d32);
         } else {
             PD_TRY(pd_state_store(st, nullptr, nullptr, tr_d.p, stream));
             k_gather_csr<<<grid_sl, 256, 0, s>>>(SL, nb, q_of.p, tr_d.p, d32);
@@ -701,8 +728,8 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
                 PD_CHECK_LAUNCH();
                 k_adj_bonds_f32<<<grid_nodes, 256, 0, s>>>(a, SL, sl_off.p, j_of.p, tr_u4.p + (size_t)m * BN,
                                                            tr_d32.p + (size_t)m * B * SL,
-                                                           tr_d32.p + (size_t)(m + 1) * B * SL, lF4.p, grow8.p, ld2.p, plun,
-                                                           grad_s0, grad_kappa);
+                                                           tr_d32.p + (size_t)(m + 1) * B * SL, lF4.p, grow8.p,
+                                                           q_of.p, ck_d.p, nb, ld2.p, plun, grad_s0, grad_kappa);
             } else {
                 k_adj_bonds<<<nblk_bond, 256, 0, s>>>(a, tr_u.p + (size_t)m * U3, tr_d.p + (size_t)m * D1,
                                                       tr_d.p + (size_t)(m + 1) * D1, lF.p, ld.p, plun, grad_s0,
