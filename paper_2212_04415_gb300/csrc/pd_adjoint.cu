@@ -249,16 +249,23 @@ __device__ __forceinline__ float rcp_ap(float x) {
 // slices of 32 consecutive nodes, slot-major inside a slice (slot p of node
 // 32 sl + lane at off[sl] + 32 p + lane), rows padded to the slice's longest.
 // Rows are sorted, so at a slot the interior nodes of a slice take the same
-// stencil offset and their neighbour gathers are contiguous.
-__global__ void k_sell_fill(long long N, const int32_t *row_ptr, const int32_t *col, const long long *off,
-                            int32_t *q_of, int32_t *j_of) {
+// stencil offset and their neighbour gathers are contiguous. Per slot: the
+// CSR position q_of, and the neighbour's grid offset k_of = (kx, ky, kz) as
+// three signed bytes (the neighbour is i + kx + nx (ky + ny kz); |k| < 128
+// cells, checked by the host), -1 for a padding slot.
+__global__ void k_sell_fill(long long N, const int32_t *row_ptr, const int32_t *col, const int32_t *coord,
+                            const long long *off, int32_t *q_of, int32_t *k_of) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const long long base = off[i >> 5] + (i & 31);
+    const int ci = coord[i];
     for (int q = row_ptr[i]; q < row_ptr[i + 1]; ++q) {
         const long long x = base + 32ll * (q - row_ptr[i]);
+        const int cj = coord[col[q]];
+        const int kx = (cj & 2047) - (ci & 2047), ky = ((cj >> 11) & 2047) - ((ci >> 11) & 2047),
+                  kz = (cj >> 22) - (ci >> 22);
         q_of[x] = q;
-        j_of[x] = col[q];
+        k_of[x] = (kx & 0xff) | ((ky & 0xff) << 8) | ((kz & 0xff) << 16);
     }
 }
 
@@ -287,8 +294,14 @@ __global__ void k_gather_dmg(long long len, long long dlen, const long long *off
     const float *src = dmg + (size_t)b * dlen;
     const uint8_t *cb = code + (size_t)b * len;
     float *dst = out + (size_t)b * len;
-    for (long long x = a0 + threadIdx.x; x < a1; x += blockDim.x)
-        if (cb[x] == kDmgGrows) dst[x] = __ldg(src + dslot[x]);
+    // four slots per thread (a slice holds 32 W slots and starts on a multiple of 32)
+    for (long long x = a0 + 4 * threadIdx.x; x < a1; x += 4 * blockDim.x) {
+        const uchar4 c = *(const uchar4 *)(cb + x);
+        if (c.x == kDmgGrows) dst[x] = __ldg(src + dslot[x]);
+        if (c.y == kDmgGrows) dst[x + 1] = __ldg(src + dslot[x + 1]);
+        if (c.z == kDmgGrows) dst[x + 2] = __ldg(src + dslot[x + 2]);
+        if (c.w == kDmgGrows) dst[x + 3] = __ldg(src + dslot[x + 3]);
+    }
 }
 
 // The same from an FP64 CSR-order array (the generic layout's store).
@@ -339,7 +352,7 @@ __device__ __forceinline__ void fold(float &s, float &c, float x) {
 // with the compiler's 80.
 __global__ void __launch_bounds__(256, 4) k_adj_bonds_f32(const AdjArgs a, long long sl_len,
                                                        const long long *__restrict__ off,
-                                                       const int32_t *__restrict__ j_of,
+                                                       const int32_t *__restrict__ k_of,
                                                        const float4 *__restrict__ u4,
                                                        const float *__restrict__ dprev,
                                                        const float *__restrict__ dcur,
@@ -363,8 +376,6 @@ __global__ void __launch_bounds__(256, 4) k_adj_bonds_f32(const AdjArgs a, long 
     const float4 *ub = u4 + (size_t)b * a.N;
     const float4 *lb4 = lF4 + (size_t)b * a.N;
     const size_t db = (size_t)b * sl_len;
-    const int32_t *__restrict__ coord = a.coord;
-    const int ci = coord[i];
     const float4 me = ub[i], ml = lb4[i];
     const long long base = off[i >> 5] + (i & 31);
     const int W = (int)((off[(i >> 5) + 1] - off[i >> 5]) >> 5);  // slots of the slice
@@ -372,11 +383,11 @@ __global__ void __launch_bounds__(256, 4) k_adj_bonds_f32(const AdjArgs a, long 
 #pragma unroll 2
     for (int p = 0; p < W; ++p) {
         const long long x = base + 32ll * p;
-        const int j = j_of[x];
-        if (j >= 0) {
-            const int cj = coord[j];
-            const int kx = (cj & 2047) - (ci & 2047), ky = ((cj >> 11) & 2047) - ((ci >> 11) & 2047),
-                      kz = (cj >> 22) - (ci >> 22);
+        const int kp = k_of[x];
+        if (kp != -1) {
+            const int kx = (int)(signed char)(kp & 0xff), ky = (int)(signed char)((kp >> 8) & 0xff),
+                      kz = (int)(signed char)((kp >> 16) & 0xff);
+            const int j = (int)i + kx + a.nx * (ky + a.ny * kz);
             const int q2 = kx * kx + ky * ky + kz * kz;
             const float L0 = q2 < 64 ? s_L0[q2] : sqrtf((float)q2) * dxf;
             const float iL0 = q2 < 64 ? s_iL0[q2] : 1.0f / L0;
@@ -556,7 +567,7 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
     DevBuf<float4> tr_u4, lF4;
     DevBuf<float> tr_d32;
     DevBuf<float2> ld2;
-    DevBuf<int32_t> slot, q_of, j_of, dslot;
+    DevBuf<int32_t> slot, q_of, k_of, dslot;
     DevBuf<long long> sl_off;
     DevBuf<uint8_t> grow8;  // mixed path: per sample and slot, the damage history code (k_grows)
     long long nsl = 0;  // slices of 32 nodes (mixed path)
@@ -573,6 +584,7 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
     PD_TRY(dalloc(&lF.p, U3));
     PD_TRY(dalloc(&rbuf.p, (size_t)B * k));
     if (f32) {
+        PD_REQUIRE(st->g.m_ratio < 127.0, "the mixed-path adjoint packs bond offsets in bytes: horizon below 127 cells");
         // sliced ELL of the CSR rows (slice widths on the host)
         std::vector<int32_t> hrow(N + 1);
         PD_CHECK_CUDA(cudaMemcpy(hrow.data(), st->row_ptr, (N + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -587,10 +599,11 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
         PD_TRY(dalloc(&sl_off.p, nsl + 1));
         PD_CHECK_CUDA(cudaMemcpy(sl_off.p, hoff.data(), (nsl + 1) * sizeof(long long), cudaMemcpyHostToDevice));
         PD_TRY(dalloc(&q_of.p, SL));
-        PD_TRY(dalloc(&j_of.p, SL));
+        PD_TRY(dalloc(&k_of.p, SL));
         PD_CHECK_CUDA(cudaMemsetAsync(q_of.p, 0xff, SL * sizeof(int32_t), s));
-        PD_CHECK_CUDA(cudaMemsetAsync(j_of.p, 0xff, SL * sizeof(int32_t), s));
-        k_sell_fill<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, st->row_ptr, st->col_csr, sl_off.p, q_of.p, j_of.p);
+        PD_CHECK_CUDA(cudaMemsetAsync(k_of.p, 0xff, SL * sizeof(int32_t), s));
+        k_sell_fill<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, st->row_ptr, st->col_csr, st->coord, sl_off.p,
+                                                                q_of.p, k_of.p);
         PD_CHECK_LAUNCH();
         PD_TRY(dalloc(&tr_u4.p, (size_t)k * BN));
         PD_TRY(dalloc(&tr_d32.p, (size_t)(k + 1) * B * SL));
@@ -726,7 +739,7 @@ extern "C" int pd_adjoint(pd_state *st, int32_t n_steps, int32_t ckpt_every, int
             if (f32) {
                 k_lF_to_f4<<<nblk_node, 256, 0, s>>>(BN, lF.p, kappa, lF4.p);
                 PD_CHECK_LAUNCH();
-                k_adj_bonds_f32<<<grid_nodes, 256, 0, s>>>(a, SL, sl_off.p, j_of.p, tr_u4.p + (size_t)m * BN,
+                k_adj_bonds_f32<<<grid_nodes, 256, 0, s>>>(a, SL, sl_off.p, k_of.p, tr_u4.p + (size_t)m * BN,
                                                            tr_d32.p + (size_t)m * B * SL,
                                                            tr_d32.p + (size_t)(m + 1) * B * SL, lF4.p, grow8.p,
                                                            q_of.p, ck_d.p, nb, ld2.p, plun, grad_s0, grad_kappa);

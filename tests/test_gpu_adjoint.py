@@ -298,3 +298,39 @@ def test_mixed_adjoint_midsize_through_the_peak(pd):
     assert er <= 1e-5
     assert ek <= 1e-4
     assert n_off <= g.n_nodes // 100 and es <= 1e-3
+
+
+def test_mixed_adjoint_from_a_damaged_state_matches_fp64(pd):
+    """The adjoint from a loaded state with partly damaged bonds: the mixed
+    path (which reads the damage of a bond that never grows in the run from
+    its initial value, and keeps a damage adjoint only for bonds that grow)
+    against the FP64 path (every bond's damage from its trajectory), within
+    the mixed path's bar."""
+    w = _case()
+    g = w.grid
+    B = 2
+    s0, kap = _fields(w, B, seed=3)
+    orow, ocol = core.neighbours(g)
+    i_idx = np.repeat(np.arange(g.n_nodes), np.diff(orow))
+    d = 0.5 * W.pair_damage(i_idx, ocol, 77, B)          # partly damaged bonds, none broken
+    u, v = W.random_state(g.n_nodes, B, 78, u_scale=2e-7)
+    row, col = pd.build_neighbours(g)
+    T, obs = 300, [299, 150, 260]
+    wts = torch.tensor([[1.0, 0.5, -0.3], [-0.7, 1.0, 0.2]], dtype=torch.float64, device="cuda")
+    s0d, kd = torch.tensor(s0, device="cuda"), torch.tensor(kap, device="cuda")
+    out = {}
+    for prec in (pd.PREC_FP64, pd.PREC_MIXED):
+        st = pd.State(g, row, col, w.mat, w.bc, batch=B, precision=prec)
+        st.reset(s0d, kd)
+        st.load(torch.tensor(u, device="cuda"), torch.tensor(v, device="cuda"), torch.tensor(d, device="cuda"), step=0)
+        gs, gk, _ = st.adjoint(T, obs, wts, s0d, kd, ckpt_every=64)
+        _, _, d_end = st.store()
+        out[prec] = (gs.cpu().numpy(), gk.cpu().numpy(), d_end.cpu().numpy())
+        st.close()
+    gs64, gk64, d64 = out[pd.PREC_FP64]
+    gsm, gkm, _ = out[pd.PREC_MIXED]
+    print("bonds with initial damage", int((d > 0).sum()), "grown in the run", int((d64 > d).sum()))
+    assert (d > 0).sum() > 100  # bonds of constant non-zero damage
+    for b in range(B):
+        assert np.abs(gsm[b] - gs64[b]).max() <= 1e-4 * np.abs(gs64[b]).max()
+        assert np.abs(gkm[b] - gk64[b]).max() <= 1e-4 * np.abs(gk64[b]).max()
