@@ -24,12 +24,14 @@
 //
 // The undirected bond's damage adjoint is kept in both directed slots (both
 // copies compute the same value), and the node sums are fixed xor trees, so
-// the gradient is deterministic. Arithmetic is FP64 throughout (the adjoint
-// is an offline gradient study; its states come from the state's own
-// forward path, FP64 or mixed). For mixed-path states the per-bond terms run
-// in FP32 (k_adj_bonds_f32) on an FP32 trajectory (node records u, s0 and the
-// damage in CSR order), with the carried damage adjoint in double-float and
-// double-float warp sums added to FP64 node sums.
+// the gradient is deterministic. For FP64-path states the arithmetic is FP64
+// throughout. For mixed-path states the per-bond terms run in FP32
+// (k_adj_bonds_f32) on an FP32 trajectory (node records u, s0 and, in
+// sliced-ELL order, the damage of the bonds whose damage grows in the run;
+// every other bond keeps its initial damage at every step), with the carried
+// damage adjoint in double-float for growing bonds only and compensated FP32
+// sums added to FP64 node sums. Both take their states from the state's own
+// forward path.
 #include <algorithm>
 #include <cmath>
 #include <vector>

@@ -63,12 +63,15 @@ def test_mlmc_estimate_against_oracle(pd):
         assert lv["sum_y"] == pytest.approx(y.sum(), rel=1e-12, abs=1e-12 * scale * n)
         assert lv["sum_y2"] == pytest.approx((y * y).sum(), rel=1e-12)
         mean, var_b, _ = omlmc.level_stats(of - oc)
-        assert abs(lv["mean"] - mean) <= 2e-3 * scale
+        # the level's own mean (a correction level's |Y_hat| is well below the
+        # peak load), floored at 1 % of the peak scale for a vanishing correction
+        print(f"level {l}: Y_hat {lv['mean']:.9g} vs {mean:.9g}")
+        assert abs(lv["mean"] - mean) <= 1e-3 * max(abs(mean), 1e-2 * scale)
         Yh.append(mean)
         V.append(var_b)
         assert lv["steps"] > 0 and lv["bond_updates"] > 0
     q, _ = omlmc.mlmc_estimate(Yh, V, a["n_samples"])
-    assert abs(res["q_ml"] - q) <= 2e-3 * abs(q)
+    assert abs(res["q_ml"] - q) <= 1e-3 * abs(q)
     # the estimator is the sum of the level means; its variance sum_l V_l / N_l
     assert res["q_ml"] == pytest.approx(sum(lv["mean"] for lv in res["levels"]), rel=1e-14)
     assert res["var_ml"] == pytest.approx(sum(lv["var"] / lv["n"] for lv in res["levels"]), rel=1e-14)
@@ -263,8 +266,9 @@ def test_plane_mlmc_against_oracle(pd):
         assert np.all(np.abs(qf - of) <= 1e-3 * np.abs(of))
         assert np.all(np.abs(qc - oc) <= 1e-3 * np.maximum(np.abs(oc), 1e-30))
         mean, var_b, _ = omlmc.level_stats(of - oc)
-        assert abs(res["levels"][l]["mean"] - mean) <= 2e-3 * np.abs(of).max()
+        print(f"plane level {l}: Y_hat {res['levels'][l]['mean']:.9g} vs {mean:.9g}")
+        assert abs(res["levels"][l]["mean"] - mean) <= 1e-3 * max(abs(mean), 1e-2 * np.abs(of).max())
         Yh.append(mean)
         V.append(var_b)
     q, _ = omlmc.mlmc_estimate(Yh, V, a["n_samples"])
-    assert abs(res["q_ml"] - q) <= 2e-3 * abs(q)
+    assert abs(res["q_ml"] - q) <= 1e-3 * abs(q)
