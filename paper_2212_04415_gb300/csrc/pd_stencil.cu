@@ -81,23 +81,47 @@ __global__ void k_stencil_reset(long long len, int B, const float *tmpl, float *
     dmg[t] = tmpl[t % len];
 }
 
+// Damage between CSR order (FP64) and the stencil layout. Loading (TO_STATE)
+// also sets the damage flags of the node's two lanes: a group of 8 rounds
+// whose loaded damage is not all zero (the template value of a present bond)
+// is marked, in the byte of the part of the half-stencil that owns it (q
+// parts; byte part of the lane's word, bit group - first group of the part).
+// A node's bonds lie in its own two lanes only, so each word has one writer.
 template <bool TO_STATE>
 __global__ void k_stencil_map(const int32_t *row_ptr, const int32_t *col, const int32_t *coord, long long N, int B,
                               long long nb, int nx, int ny, int BY, int BZ, int nbx, int nby, int wpb, int rounds,
-                              long long len, const int16_t *box, float *dmg, double *csr) {
+                              long long len, const int16_t *box, float *dmg, double *csr, uint32_t *dirty,
+                              int q) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N * B) return;
     const int b = (int)(t / N);
     const int i = (int)(t % N);
+    const int gpp = rounds / 8 / q;  // groups of 8 rounds per part
+    uint32_t w[2] = {0u, 0u};        // flags of sub-lanes 0 and 1
     for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
         const int code = code_of(coord, i, col[p], box);
         if (code < 0) continue;
         const long long e = (long long)b * len + slot_of(i, code, nx, ny, BY, BZ, nbx, nby, wpb, rounds);
-        const long long q = (long long)b * nb + p;
-        if (TO_STATE)
-            dmg[e] = (float)csr[q];
-        else
-            csr[q] = (double)dmg[e];
+        const long long qq = (long long)b * nb + p;
+        if (TO_STATE) {
+            const float d = (float)csr[qq];
+            dmg[e] = d;
+            if (d != 0.0f) {
+                const int g = (code >> 1) / 8, part = g / gpp;
+                w[code & 1] |= 1u << (8 * part + (g - part * gpp));
+            }
+        } else {
+            csr[qq] = (double)dmg[e];
+        }
+    }
+    if (TO_STATE) {
+        const int ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+        const long long brick = (ix / kSlice) + (long long)nbx * ((iy / BY) + (long long)nby * (iz / BZ));
+        const int row = (iy % BY) + BY * (iz % BZ);
+        const long long lane0 = (brick * wpb + (row >> 1)) * 32 + 8 * (row & 1) + (ix % kSlice);
+        const long long per_sample = len / rounds;  // lanes of a sample
+        dirty[(size_t)b * per_sample + lane0] = w[0];
+        dirty[(size_t)b * per_sample + lane0 + 16] = w[1];
     }
 }
 
@@ -328,20 +352,17 @@ int stencil_reset_damage(pd_state *st, cudaStream_t s) {
 
 int stencil_map_damage(const pd_state *st, double *csr, bool to_state, cudaStream_t s) {
     const long long NB = st->N * st->B;
-    if (to_state) {  // loaded damage: every group is read from the samples' own words
-        const int rounds = st->st_dim == 3 ? Sten<3>::kRounds : Sten<2>::kRounds;
-        PD_CHECK_CUDA(cudaMemsetAsync(st->st_dirty, 0xFF, (size_t)st->B * (st->st_len / rounds) * 4, s));
-    }
-    if (to_state)
+    const int rounds = st->st_dim == 3 ? Sten<3>::kRounds : Sten<2>::kRounds;
+    if (to_state)  // loaded damage, with the damage flags of every node's lanes
         k_stencil_map<true><<<blocks_of(NB), 256, 0, s>>>(st->row_ptr, st->col_csr, st->coord, st->N, st->B, st->nb,
                                                           st->g.nx, st->g.ny, st->by, st->bz, st->nbx, st->nby,
-                                                          st->st_wpb, st->st_dim == 3 ? Sten<3>::kRounds : Sten<2>::kRounds,
-                                                          st->st_len, st->st_box, (float *)st->dmg, csr);
+                                                          st->st_wpb, rounds, st->st_len, st->st_box, (float *)st->dmg,
+                                                          csr, (uint32_t *)st->st_dirty, st->st_q);
     else
         k_stencil_map<false><<<blocks_of(NB), 256, 0, s>>>(st->row_ptr, st->col_csr, st->coord, st->N, st->B, st->nb,
                                                            st->g.nx, st->g.ny, st->by, st->bz, st->nbx, st->nby,
-                                                           st->st_wpb, st->st_dim == 3 ? Sten<3>::kRounds : Sten<2>::kRounds,
-                                                          st->st_len, st->st_box, (float *)st->dmg, csr);
+                                                           st->st_wpb, rounds, st->st_len, st->st_box, (float *)st->dmg,
+                                                           csr, nullptr, st->st_q);
     PD_CHECK_LAUNCH();
     return PD_OK;
 }

@@ -51,7 +51,7 @@
 // it is read from the template, which stays in L2, instead of from the
 // sample's own words: the values are the same, and the DRAM stream of a
 // launch shrinks to the groups that are softening or broken. Reset clears the
-// bits; a state loaded with damage marks every group.
+// bits; loading damage marks the groups whose loaded damage is not all zero.
 //
 // A step's reaction is reduced in its own launch, or, for launches of a single
 // wave, by every block of the next launch before it steps (no serial tail at
