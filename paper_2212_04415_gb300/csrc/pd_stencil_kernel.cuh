@@ -392,36 +392,32 @@ __device__ __forceinline__ V bond_g(V d, V s, V rL) {
     return vmul(vfma(neg(d), s, s), rL);
 }
 
-// Offsets of the rounds of the positive half-stencil, for the fix-up path.
+// Offsets of the rounds of the positive half-stencil, for the fix-up path:
+// kx, ky, kz and |k|^2 in the bytes of one word (padding rounds: zero), and
+// |k| (the float the unrolled loop uses for the same round). The lanes of a
+// warp fix up different rounds, so the table is read through the read-only
+// data cache, which serves divergent addresses of one line together (the
+// constant bank serves them one address at a time).
+struct __align__(8) HalfEnt {
+    int k;
+    float kw;
+};
 struct HalfTab {
-    signed char k[64][4];  // kx, ky, kz, |k|^2 (padding rounds: zero)
+    HalfEnt e[64];
 };
 template <int DIM>
 __host__ __device__ constexpr HalfTab half_table() {
     HalfTab t{};
-    for (int m = 0; m < Sten<DIM>::kHalf; ++m) {
-        const I3 k = half_off<DIM>(m);
-        t.k[m][0] = (signed char)k.x;
-        t.k[m][1] = (signed char)k.y;
-        t.k[m][2] = (signed char)k.z;
-        t.k[m][3] = (signed char)(k.x * k.x + k.y * k.y + k.z * k.z);
+    for (int m = 0; m < 64; ++m) {
+        const I3 k = m < Sten<DIM>::kHalf ? half_off<DIM>(m) : I3{0, 0, 0};
+        const int q = k.x * k.x + k.y * k.y + k.z * k.z;
+        t.e[m].k = (int)((unsigned)(k.x & 0xFF) | ((unsigned)(k.y & 0xFF) << 8) | ((unsigned)(k.z & 0xFF) << 16) |
+                         ((unsigned)q << 24));
+        t.e[m].kw = knorm(q);
     }
     return t;
 }
-__constant__ HalfTab c_half[2] = {half_table<2>(), half_table<3>()};
-
-__device__ __forceinline__ float knorm_rt(int q) {
-    switch (q) {
-        case 1: return knorm(1);
-        case 2: return knorm(2);
-        case 3: return knorm(3);
-        case 4: return knorm(4);
-        case 5: return knorm(5);
-        case 6: return knorm(6);
-        case 8: return knorm(8);
-        default: return knorm(9);
-    }
-}
+__device__ const HalfTab g_half[2] = {half_table<2>(), half_table<3>()};
 
 // The fix-up of one bond (round m) whose stretch passed its elastic limit
 // this step: recompute it (the same operations as the unrolled loop, so the
@@ -435,20 +431,34 @@ struct FixOut {
     V dg, yx, yy, yz;
 };
 
+// Previous damage of round m, per sample of the lane (the sample's own words:
+// a group read from the template holds the same values).
+template <int NS>
+__device__ __forceinline__ typename Lane<NS>::V load_dold(int m, const BondCtx<NS> &cx) {
+    const float *slot0 = (const float *)(cx.dq0 + 32 * (m / 4)) + (m % 4);
+    if constexpr (NS == 1) {
+        return *slot0;
+    } else {
+        const float *slot1 = (const float *)(cx.dq1 + 32 * (m / 4)) + (m % 4);
+        return make_float2(*slot0, *slot1);
+    }
+}
+
 template <int DIM, int NS, int LAW, bool KAPPA>
-__device__ __forceinline__ FixOut<typename Lane<NS>::V> fix_one(int m, bool act, const BondCtx<NS> &cx, unsigned &dwn) {
+__device__ __forceinline__ FixOut<typename Lane<NS>::V> fix_one(int m, bool act, const BondCtx<NS> &cx, unsigned &dwn,
+                                                                typename Lane<NS>::V dold) {
     using V = typename Lane<NS>::V;
-    const signed char *k = c_half[DIM - 2].k[m];
-    const int kx = k[0], ky = k[1], kz = k[2], q = k[3];
+    const int2 e = __ldg(reinterpret_cast<const int2 *>(&g_half[DIM - 2].e[m]));
+    const int kx = (int)((unsigned)e.x << 24) >> 24, ky = (int)((unsigned)e.x << 16) >> 24;
+    const int kz = (int)((unsigned)e.x << 8) >> 24, q = (int)((unsigned)e.x >> 24);
     const Rec<V> r = load_rec<NS>(cx.rb + cx.lb * kz + 16 * kx + NS * kRowC * ky);
     FixOut<V> o;
     V rL, s;
-    bond_kin<V>(cx, r, kx, ky, kz, knorm_rt(q), (float)q, o.yx, o.yy, o.yz, rL, s);
+    bond_kin<V>(cx, r, kx, ky, kz, __int_as_float(e.y), (float)q, o.yx, o.yy, o.yz, rL, s);
     const V s0 = vadd(cx.h, r.h);
     float *slot0 = (float *)(cx.dq0 + 32 * (m / 4)) + (m % 4);
-    V dold, dnew;
+    V dnew;
     if constexpr (NS == 1) {
-        dold = *slot0;
         const float dl = s > s0 ? law_cold<LAW>(s, s0, cx.lc) : 0.f;
         const bool grow = act && dl > dold;
         dnew = grow ? dl : dold;
@@ -458,7 +468,6 @@ __device__ __forceinline__ FixOut<typename Lane<NS>::V> fix_one(int m, bool act,
         }
     } else {
         float *slot1 = (float *)(cx.dq1 + 32 * (m / 4)) + (m % 4);
-        dold = make_float2(*slot0, *slot1);
         const float dlx = s.x > s0.x ? law_cold<LAW>(s.x, s0.x, cx.lc) : 0.f;
         const float dly = s.y > s0.y ? law_cold<LAW>(s.y, s0.y, cx.lc) : 0.f;
         const bool gx = act && dlx > dold.x, gy = act && dly > dold.y;
@@ -494,8 +503,12 @@ __device__ __forceinline__ void fix_bonds(unsigned mask, int m0, const BondCtx<N
         const bool two = mask != 0u;
         const int j2 = two ? __ffs(mask) - 1 : j1;  // without a second bond: the first again, with no effect
         if (two) mask &= mask - 1;
-        const FixOut<V> a = fix_one<DIM, NS, LAW, KAPPA>(m0 + j1, true, cx, dwn);
-        const FixOut<V> b = fix_one<DIM, NS, LAW, KAPPA>(m0 + j2, two, cx, dwn);
+        // both damage words are read before either bond stores (the rounds
+        // differ, or the second bond changes nothing), so the two reads share
+        // one memory latency
+        const V da = load_dold<NS>(m0 + j1, cx), db = load_dold<NS>(m0 + j2, cx);
+        const FixOut<V> a = fix_one<DIM, NS, LAW, KAPPA>(m0 + j1, true, cx, dwn, da);
+        const FixOut<V> b = fix_one<DIM, NS, LAW, KAPPA>(m0 + j2, two, cx, dwn, db);
         px = vfma(a.dg, a.yx, px);
         py = vfma(a.dg, a.yy, py);
         pz = vfma(a.dg, a.yz, pz);
