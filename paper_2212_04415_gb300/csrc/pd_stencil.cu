@@ -386,9 +386,10 @@ bool stencil_pairable(const pd_state *s0, const pd_state *s1) {
 // stream is finishing (programmatic dependent launch): the kernel waits for it
 // (griddepcontrol.wait) before it reads anything, so only the launch and the
 // scheduling of its blocks overlap the previous step's tail. Single-wave
-// launches (one sample of a small mesh) are launched plainly: there the early
-// blocks took the free slots of some SMs and the step was slower (measured on
-// GB300, 28k-node beam, one sample: 15.9 -> 18.0 us per step).
+// launches (one sample of a small mesh) are launched plainly: there the
+// steps without softening gain (28k-node beam, one sample, GB300: 12.4 ->
+// 10.8 us) but the steps with a growing crack lose more, and whole runs to
+// the peak were slower (14.07 against 14.00 us per step).
 static cudaLaunchConfig_t pdl_config(unsigned grid, int threads, size_t smem, cudaStream_t s, bool pdl) {
     static const cudaLaunchAttribute attr = [] {
         cudaLaunchAttribute x{};
