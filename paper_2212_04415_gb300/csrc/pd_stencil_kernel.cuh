@@ -423,9 +423,9 @@ __device__ const HalfTab g_half[2] = {half_table<2>(), half_table<3>()};
 // this step: recompute it (the same operations as the unrolled loop, so the
 // same bits), apply the law, store the damage where it grew (only when act),
 // and return the correction of the force factor -- the unrolled loop formed
-// the lane's sums with the previous damage -- with the bond's direction (zero
-// where nothing grew). The two directed copies of a bond run the same
-// correction.
+// the lane's sums with the previous damage dold, which the caller loads --
+// with the bond's direction (zero where nothing grew). The two directed
+// copies of a bond run the same correction.
 template <class V>
 struct FixOut {
     V dg, yx, yy, yz;
